@@ -1,0 +1,324 @@
+"""Benchmark: Mcell-updates/s of the multi-material FV step on one GB300.
+
+Default workload: the 256^3 shock-bubble problem with Mie-Grueneisen water and
+an air bubble (shock 1e9 Pa at x = 0.2, bubble radius 0.15 at the centre), in
+mixed precision (the headline ``value``), with the plain FP64 path timed on
+the same grid next to it (``fp64``). A "step" is one full RK2 time step of the
+whole grid: both stages (MUSCL + HLLC + FIVER + level set), the phase update,
+and every tenth step the reinitialisation. The state (805 MB) is larger than
+L2, so no flush is needed between steps.
+
+--impl reference times the CPU oracle (the only reference: the paper ships no
+code) on a bounded sample of the same workload.
+
+Under torchrun each rank runs its own replica on its own GPU (the workload is
+independent grids: weak scaling, no collective on the data path); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-updates/s at 256^3 two-phase (mixed precision; FP64 alongside)"
+UNIT = "Mcell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid edge")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def setup(n):
+    from paper_2508_16387_gb300 import workloads as WL
+    return WL.shock_bubble(n=n, water=WL.WATER_MG, steps=500, name=f"shock_bubble_{n}^3_mg_water")
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def make_grid(M, s, precision, stream=None):
+    g = M.Grid(s.n, s.h, s.bc, s.eos, precision=precision, cfl=s.cfl, reinit_every=s.reinit_every,
+               reinit_iters=s.reinit_iters, stream=stream)
+    amb = s.prims_by_region[s.shock[1]]
+    r1, u1, _ = M.m2c_shock_state(s.eos[0], (amb[0], amb[1], amb[4]), s.shock[0])
+    g.set_prims(s.prims((r1, u1)), s.phi)
+    return g
+
+
+def launches_per_step(step_index, reinit_every, reinit_iters):
+    n = 8
+    if reinit_every > 0 and (step_index + 1) % reinit_every == 0 and reinit_iters > 0:
+        n += reinit_iters + (1 if reinit_iters == 1 else 0)
+    return n
+
+
+def time_steps(torch, g, steps, warmup, barrier=None):
+    """Runs warmup steps, then times exactly `steps` steps with CUDA events on the grid's stream,
+    recording the bulk stage kernel launches with the library's event pairs."""
+    stream = torch.cuda.current_stream()
+    g.step(warmup)
+    g.sync()
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
+    g.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kms, klaunch = g.profile_read()
+    g.profile(False)
+    g.sync()
+    return ms, kms, klaunch
+
+
+def e2e_run(torch, M, s, g, steps):
+    """End to end through the C-ABI with host buffers: every step uploads the state from
+    pinned host memory, advances one time step and downloads the state."""
+    nx, ny, nz = s.n
+    Wh = torch.empty((5, nz, ny, nx), dtype=torch.float64, pin_memory=True)
+    ph = torch.empty((nz, ny, nx), dtype=torch.float64, pin_memory=True)
+    g.download(Wh, ph)
+    W0 = Wh.clone()
+    p0 = ph.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        Wh.copy_(W0)
+        ph.copy_(p0)
+        g.upload(Wh, ph)
+        g.step(1)
+        g.download(Wh, ph)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nbytes = (Wh.numel() + ph.numel()) * 8
+    return dt, nbytes
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            P = json.load(f)
+        return P.get("hbm_gbs", 6800.0), "measured"
+    except OSError:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kind):
+    """Per-launch DRAM bytes of the bulk stage kernel from the committed ncu summary (or None)."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get(kind)
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline(seconds_hint=15.0, n=64, steps=3):
+    """The oracle, as it stands, on the 64^3 version of the same workload (bounded sample)."""
+    from oracle import oracle as O
+    s = setup(n)
+    g = O.Grid(n=s.n, h=s.h, eos=tuple(O.EOS(*e) for e in s.eos), bc=s.bc, cfl=s.cfl,
+               reinit_every=s.reinit_every, reinit_iters=s.reinit_iters)
+    amb = s.prims_by_region[s.shock[1]]
+    r1, u1, _ = O.shock_state(O.EOS(*s.eos[0]), (amb[0], amb[1], amb[4]), s.shock[0])
+    W = O.prims_to_cons(g, s.prims((r1, u1)), s.phi)
+    O.run(g, W, s.phi, 1)  # warm-up (page-in, thread start)
+    t0 = time.perf_counter()
+    O.run(g, W, s.phi, steps)
+    dt = time.perf_counter() - t0
+    return {"value": s.ncells * steps / dt / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{steps} oracle time steps of the {n}^3 version of the same MG shock-bubble setup "
+                      f"({dt:.1f} s wall)"}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    barrier = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = dist.barrier
+    from paper_2508_16387_gb300 import m2c as M
+    M.lib()
+    s = setup(args.n)
+    N = s.ncells
+    out = {}
+
+    g = make_grid(M, s, M.MIXED)
+    with ClockSampler(local) as clk:
+        ms, kms, kl = time_steps(torch, g, args.steps, args.warmup, barrier)
+    t_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * N * args.steps / (t_max * 1e-3) / 1e6
+    hbm, src = peaks()
+    avg = kms / max(kl, 1)
+    alg_bytes = 120.0 * N  # mean over stage 1 (96 B/cell) and stage 2 (144 B/cell)
+    achieved = alg_bytes / (avg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": ncu_traffic("mixed"),
+            "kernel": "k_stage<float,8> (bulk stage)", "peak_source": src,
+            "kernel_ms_avg": round(avg, 4), "kernel_share": round(kms / ms, 3) if ms > 0 else None}
+    launches = sum(launches_per_step(args.warmup + i, s.reinit_every, s.reinit_iters) for i in range(args.steps))
+    e2e = None
+    if not args.no_e2e:
+        sec, nbytes = e2e_run(torch, M, s, g, max(3, args.steps // 4))
+        e2e = {"value": round(N * max(3, args.steps // 4) / sec / 1e6, 2), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    del g
+    torch.cuda.empty_cache()
+    fp64 = None
+    if not args.no_fp64:
+        g64 = make_grid(M, s, M.FP64)
+        k64 = max(5, args.steps // 2)
+        ms64, kms64, kl64 = time_steps(torch, g64, k64, args.warmup, barrier)
+        avg64 = kms64 / max(kl64, 1)
+        fp64 = {"value": round(N * k64 / (ms64 * 1e-3) / 1e6, 2), "unit": UNIT, "steps": k64,
+                "ms_per_step": round(ms64 / k64, 3), "dtype": "f64",
+                "roofline": {"bound": "alu", "kernel": "k_stage<double,8> (bulk stage)",
+                             "kernel_ms_avg": round(avg64, 4),
+                             "hbm_frac": round(alg_bytes / (avg64 * 1e-3) / 1e9 / hbm, 4)}}
+        del g64
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+           "config": {"workload": s.name, "grid": list(s.n), "precision": "mixed", "cells": N,
+                      "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                      "l2": "state (805 MB) larger than L2, no flush"},
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64}
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out))
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    import numpy as np  # noqa: F401
+    n = 64
+    s = setup(n)
+    g = O.Grid(n=s.n, h=s.h, eos=tuple(O.EOS(*e) for e in s.eos), bc=s.bc, cfl=s.cfl,
+               reinit_every=s.reinit_every, reinit_iters=s.reinit_iters)
+    amb = s.prims_by_region[s.shock[1]]
+    r1, u1, _ = O.shock_state(O.EOS(*s.eos[0]), (amb[0], amb[1], amb[4]), s.shock[0])
+    W = O.prims_to_cons(g, s.prims((r1, u1)), s.phi)
+    phi = s.phi
+    r = O.run(g, W, phi, args.warmup)
+    W, phi = r.W, r.phi
+    t0 = time.perf_counter()
+    r = O.run(g, W, phi, args.steps, step0=args.warmup)
+    dt = time.perf_counter() - t0
+    value = s.ncells * args.steps / dt / 1e6
+    sample = (f"each step one oracle time step of the {n}^3 version of the 256^3 MG shock-bubble workload "
+              f"(same physics, same per-cell work)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": setup(args.n).name, "grid": [args.n] * 3, "precision": "f64 (oracle)",
+                   "sample_grid": [n] * 3},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

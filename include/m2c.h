@@ -1,0 +1,176 @@
+/*
+ * m2c.h -- C ABI of libm2cgpu.so, a GB300 (sm_103a) solver for the
+ * multi-material compressible flow step of M2C (arXiv 2508.16387).
+ *
+ * One call to m2c_step advances a Cartesian grid by whole time steps of the
+ * method of the paper's Sec. 4: cell-centred finite volumes (Sec. 4.2, Eq.
+ * NS_discretized with the viscous and source terms off), MUSCL reconstruction
+ * of the primitive variables with the modified van Albada limiter (App. D),
+ * the HLLC flux (App. C.4) on faces between cells of one material, the FIVER
+ * flux on faces where the level set changes sign (Sec. 4.2, exact
+ * two-material Riemann problem, Eq. 1DRiemannProblem), the second-order TVD
+ * Runge-Kutta scheme (Sec. 4.3), level-set advection (Sec. 3.5.1, Eq.
+ * levelset; third-order upwind finite differences, Sec. 4.4), periodic
+ * reinitialisation (Eq. reinit) and the phase update of Sec. 2.3 step (6).
+ *
+ * Conventions. SI units. A grid has nx*ny*nz cells of edge h; arrays are
+ * structure-of-arrays with x fastest: field f of cell (i,j,k) is at
+ * a[f*N + (k*ny + j)*nx + i], N = nx*ny*nz. The conserved state is
+ * W = (rho, rho u, rho v, rho w, rho E), E = e + |V|^2/2; primitive arrays are
+ * (rho, u, v, w, p). Material 1 is where phi < 0, material 0 elsewhere.
+ *
+ * Memory ownership. The caller owns all memory. Device arrays passed to the
+ * library are borrowed for the life of the context (or of the call, for the
+ * one-shot entry points); the library allocates no device memory except the
+ * small per-call staging buffers of m2c_solve_riemann and m2c_shock_state when
+ * they are given host pointers. All solver scratch lives in one caller-provided
+ * device workspace of m2c_workspace_bytes() bytes, 256-byte aligned.
+ *
+ * Errors. Every entry point returns an m2c_status; no exception crosses the
+ * ABI. Launches are asynchronous on the context's stream; errors raised on
+ * the device (non-physical state, Riemann non-convergence, list overflow) are
+ * latched in the workspace and returned by m2c_sync together with the first
+ * offending cell. m2c_last_error() gives a text for the last error of a
+ * context. Functions are not thread-safe on one context.
+ */
+#ifndef M2C_H
+#define M2C_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  M2C_OK = 0,
+  M2C_EINVAL = 1,    /* bad argument */
+  M2C_ENOMEM = 2,    /* workspace too small */
+  M2C_ECUDA = 3,     /* CUDA runtime error */
+  M2C_ENOCONV = 4,   /* Newton / bisection cap reached in the Riemann solver */
+  M2C_ENONPHYS = 5,  /* rho <= 0, c^2 <= 0, or a state outside the EOS domain */
+  M2C_EVACUUM = 6,   /* the Riemann problem has a vacuum solution (not built) */
+  M2C_ETIMEOUT = 7,  /* a bounded device wait ran out */
+  M2C_EOVERFLOW = 8  /* an interface work list exceeded its capacity */
+} m2c_status;
+
+/* Equations of state (Sec. 3.3 and App. B).
+ * M2C_EOS_SG: stiffened gas, NASG with b = e_c = 0: p = (gamma-1) rho e - gamma p_c;
+ *   params = {gamma, p_c}; p_c = 0 is a perfect gas.
+ * M2C_EOS_MG: Mie-Grueneisen (App. B.3): p = p_R(eta) + rho0 Gamma0 (e - e_R(eta)),
+ *   eta = 1 - rho0/rho; params = {rho0, c0, s, Gamma0, e0, eta_min}; eta_min = -inf
+ *   (or fewer than 6 params) turns the tensile cutoff off. */
+typedef enum { M2C_EOS_SG = 0, M2C_EOS_MG = 1 } m2c_eos_type;
+
+/* M2C_FP64: every operation in FP64. M2C_MIXED: reconstruction, HLLC and the
+ * level-set residual in FP32; the pressure from the conserved state, the
+ * Runge-Kutta accumulation of W and phi, and the exact Riemann solver in FP64. */
+typedef enum { M2C_FP64 = 0, M2C_MIXED = 1 } m2c_precision;
+
+/* Boundary conditions per side (x-, x+, y-, y+, z-, z+): transmissive
+ * (zero-gradient ghost values) or periodic (both sides of an axis). */
+typedef enum { M2C_BC_TRANSMISSIVE = 0, M2C_BC_PERIODIC = 1 } m2c_bc;
+
+typedef struct {
+  int type;          /* m2c_eos_type */
+  double params[6];
+} m2c_eos_desc;
+
+typedef struct m2c_ctx m2c_ctx;
+
+/* Counters of the last completed step, read by m2c_get_stats after m2c_sync. */
+typedef struct {
+  long interface_faces;  /* faces with different materials, stage 1 of the last step */
+  long interface_cells;  /* cells with at least one such face, stage 1 */
+  long flipped_cells;    /* cells that changed material in the last step */
+  double dt;             /* time step of the next step */
+} m2c_stats;
+
+/* Workspace bytes for an nx*ny*nz grid. */
+size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
+
+/* Creates a context on the calling thread's current CUDA device.
+ * lo: lower corner (only used to report coordinates), h > 0: cell edge,
+ * bc[6]: m2c_bc per side, workspace: device pointer of ws_bytes >=
+ * m2c_workspace_bytes(), stream: a cudaStream_t (NULL = legacy default stream).
+ * Defaults: CFL 0.5, reinitialisation every 10 steps with 5 iterations. */
+m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[3], double h, const int bc[6],
+                         int precision, void* workspace, size_t ws_bytes, void* stream);
+
+/* Material 0 (phi >= 0) or 1 (phi < 0) gets an EOS; nparams <= 6. */
+m2c_status m2c_set_eos(m2c_ctx* ctx, int material, int type, const double* params, int nparams);
+
+/* CFL number of dt = CFL h / max_cells sum_d (|V_d| + c) (the sum runs over the
+ * axes with more than one cell), and the reinitialisation schedule: after every
+ * reinit_every-th step, reinit_iters pseudo-time iterations (0 disables). */
+m2c_status m2c_set_scheme(m2c_ctx* ctx, double cfl, int reinit_every, int reinit_iters);
+
+/* Borrows the device arrays W (5N doubles) and phi (N doubles) as the state,
+ * sets time t and step counter step, and computes the first time step. */
+m2c_status m2c_set_state(m2c_ctx* ctx, double* W, double* phi, double t, long step);
+
+/* Fills the borrowed W from device primitive arrays prims (5N: rho, u, v, w, p)
+ * using the EOS of each cell's material (from the sign of phi). */
+m2c_status m2c_prims_to_state(m2c_ctx* ctx, const double* prims);
+
+/* Copies host arrays into / out of the borrowed state (pinned host memory gives
+ * asynchronous copies; m2c_download_state synchronises the stream). */
+m2c_status m2c_upload_state(m2c_ctx* ctx, const double* W_host, const double* phi_host);
+m2c_status m2c_download_state(m2c_ctx* ctx, double* W_host, double* phi_host);
+
+/* Enqueues nsteps time steps on the context's stream. */
+m2c_status m2c_step(m2c_ctx* ctx, int nsteps);
+
+/* Device bytes of the descriptor table of a batch of k contexts. */
+size_t m2c_batch_bytes(int k);
+
+/* Enqueues nsteps time steps of k contexts (one precision, one reinitialisation
+ * schedule: the first context's) on the first context's stream, with one launch
+ * per kernel for all contexts. batch_ws: caller's device buffer of
+ * m2c_batch_bytes(k) bytes, 256-byte aligned, borrowed until the steps complete. */
+m2c_status m2c_step_batch(m2c_ctx** ctxs, int k, int nsteps, void* batch_ws, size_t bytes);
+
+/* Writes the residual of one Runge-Kutta stage of the current state, without
+ * advancing it: R (5N) = dW/dt and L (N) = dphi/dt, device arrays. */
+m2c_status m2c_residual(m2c_ctx* ctx, double* R, double* L);
+
+/* Blocks until the stream is idle; returns the first latched device error,
+ * the time, the step counter and the offending cell (-1 if none). Any of the
+ * output pointers may be NULL. Clears the latched error. */
+m2c_status m2c_sync(m2c_ctx* ctx, double* t, long* steps, long* err_cell);
+
+m2c_status m2c_get_stats(m2c_ctx* ctx, m2c_stats* out);
+
+/* Batch of n exact two-material Riemann problems (Sec. 4.2, Eq.
+ * 1DRiemannProblem). L and R are SoA (rho[n], u[n], p[n]); out is SoA
+ * (p*[n], u*[n], rho*_L[n], rho*_R[n]); iters[n] and status[n] (may be NULL)
+ * get the iteration count and per-problem m2c_status. on_device = 1: all
+ * arrays are device pointers and the call is asynchronous on stream; 0: host
+ * arrays, the call stages them and blocks. Returns the first non-OK status of
+ * the batch (host arrays) or M2C_OK (device arrays; read status[]). */
+m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
+                             const double* R, double* out, int* iters, int* status, int on_device, void* stream);
+
+/* Post-shock state of a shock moving in +x into the state w = (rho, u, p) with
+ * pressure p1 behind it (the right-facing wave of the exact Riemann solver):
+ * out = (rho1, u1, shock speed). Host arrays; blocks. */
+m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]);
+
+/* Kernel timing: while enabled, m2c_step and m2c_step_batch record a CUDA event
+ * pair on the context's stream around every launch of the bulk stage kernel.
+ * m2c_profile_read synchronises the stream, returns the summed event time (ms)
+ * and the number of timed launches, and starts a new count. */
+m2c_status m2c_profile(m2c_ctx* ctx, int enable);
+m2c_status m2c_profile_read(m2c_ctx* ctx, double* total_ms, long* launches);
+
+/* Releases a context (the borrowed memory stays with the caller). */
+void m2c_destroy(m2c_ctx* ctx);
+
+const char* m2c_last_error(const m2c_ctx* ctx);
+const char* m2c_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* M2C_H */

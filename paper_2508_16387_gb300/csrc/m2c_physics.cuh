@@ -1,0 +1,428 @@
+// Device-side physics of the M2C finite-volume step (arXiv 2508.16387):
+// equations of state, the modified van Albada slope, the HLLC flux and the
+// exact two-material Riemann solver of the FIVER flux.
+//
+// Real type R is double on the FP64 path and float for the reconstruction and
+// HLLC of the mixed-precision path; the Riemann solver is FP64 on both paths.
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#include "m2c.h"
+
+namespace m2c {
+
+// ---------------------------------------------------------------------------
+// Equation of state parameters in device memory. SG: p = (g - 1) rho e - g pc
+// (NASG of Sec. 3.3 with b = e_c = 0). MG: App. B.3 with the compression,
+// tension and cutoff branches of the reference curves.
+// ---------------------------------------------------------------------------
+struct EosDev {
+  int type;  // M2C_EOS_SG or M2C_EOS_MG
+  int pad;
+  double g, pc, gm1, gpc, inv_gm1;                // SG
+  double rho0, c0, s, G0, e0, eta_min;            // MG
+  double K0, rg, inv_rg, inv_2rho0, eta_max, pmin;  // MG derived
+};
+
+__host__ inline EosDev make_eos_dev(int type, const double* prm) {
+  EosDev e{};
+  e.type = type;
+  if (type == M2C_EOS_SG) {
+    e.g = prm[0];
+    e.pc = prm[1];
+    e.gm1 = prm[0] - 1.0;
+    e.gpc = prm[0] * prm[1];
+    e.inv_gm1 = 1.0 / (prm[0] - 1.0);
+  } else {
+    e.rho0 = prm[0];
+    e.c0 = prm[1];
+    e.s = prm[2];
+    e.G0 = prm[3];
+    e.e0 = prm[4];
+    e.eta_min = prm[5];
+    e.K0 = prm[0] * prm[1] * prm[1];
+    e.rg = prm[0] * prm[3];
+    e.inv_rg = 1.0 / e.rg;
+    e.inv_2rho0 = 0.5 / prm[0];
+    e.eta_max = 1.0 / prm[2];
+    e.pmin = e.K0 * prm[5];
+  }
+  return e;
+}
+
+// Reference curves p_R, p_R', e_R, e_R' at strain eta (App. B.3); "p_H" in the
+// compression e_R is read as p_R.
+template <typename R>
+__device__ __forceinline__ void mg_ref(const EosDev& q, R eta, R& pR, R& dpR, R& eR, R& deR) {
+  const R K0 = (R)q.K0, rho0 = (R)q.rho0, e0 = (R)q.e0, h2 = (R)q.inv_2rho0;
+  if (eta > (R)0) {
+    R d = (R)1 - (R)q.s * eta;
+    R id = (R)1 / d;
+    R id2 = id * id;
+    pR = K0 * eta * id2;
+    dpR = K0 * ((R)1 + (R)q.s * eta) * id2 * id;
+    eR = pR * eta * h2 + e0;
+    deR = (dpR * eta + pR) * h2;
+  } else if (eta >= (R)q.eta_min) {
+    pR = K0 * eta;
+    dpR = K0;
+    eR = K0 * eta * eta * h2 + e0;
+    deR = K0 * eta / rho0;
+  } else {
+    R em = (R)q.eta_min, pm = (R)q.pmin;
+    pR = pm;
+    dpR = (R)0;
+    eR = K0 * em * em * h2 + e0 + pm / rho0 * (eta - em);
+    deR = pm / rho0;
+  }
+}
+
+// p(rho, e) given 1/rho; false if the state is outside the EOS domain.
+template <typename R>
+__device__ __forceinline__ bool eos_p(const EosDev& q, R rho, R inv_rho, R e, R& p) {
+  if (q.type == M2C_EOS_SG) {
+    p = (R)q.gm1 * rho * e - (R)q.gpc;
+    return true;
+  }
+  R eta = (R)1 - (R)q.rho0 * inv_rho;
+  if (!(eta < (R)q.eta_max)) return false;
+  R pR, dpR, eR, deR;
+  mg_ref(q, eta, pR, dpR, eR, deR);
+  p = pR + (R)q.rg * (e - eR);
+  return true;
+}
+
+// e(rho, p) and c^2(rho, p) together (App. B.3 and App. C.2: c^2 = dp/drho|_e + p/rho^2 dp/de|_rho).
+// False if rho <= 0, c^2 <= 0 or the state is outside the EOS domain.
+template <typename R>
+__device__ __forceinline__ bool eos_e_c2(const EosDev& q, R rho, R inv_rho, R p, R& e, R& c2) {
+  if (!(rho > (R)0)) return false;
+  if (q.type == M2C_EOS_SG) {
+    R pb = p + (R)q.pc;
+    e = (p + (R)q.gpc) * (R)q.inv_gm1 * inv_rho;
+    c2 = (R)q.g * pb * inv_rho;
+  } else {
+    R eta = (R)1 - (R)q.rho0 * inv_rho;
+    if (!(eta < (R)q.eta_max)) return false;
+    R pR, dpR, eR, deR;
+    mg_ref(q, eta, pR, dpR, eR, deR);
+    e = eR + (p - pR) * (R)q.inv_rg;
+    R ir2 = inv_rho * inv_rho;
+    c2 = ((dpR - (R)q.rg * deR) * (R)q.rho0 + p * (R)q.rg) * ir2;
+  }
+  return c2 > (R)0 && c2 < (R)INFINITY;
+}
+
+// ---------------------------------------------------------------------------
+// Modified van Albada slope (App. D, uniform grid A = B = 1, k = 2):
+// sigma = a b (a + b)/(a^2 + b^2) when a b > 0, else 0.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R va_slope(R a, R b) {
+  R ab = a * b;
+  if (!(ab > (R)0)) return (R)0;
+  return ab * (a + b) / (a * a + b * b);
+}
+
+// A reconstructed face state with its sound speed and total energy per mass.
+template <typename R>
+struct FaceState {
+  R rho, u, v, w, p, c, E;
+};
+
+template <int D, typename R>
+__device__ __forceinline__ R comp(const FaceState<R>& q) {
+  return D == 0 ? q.u : (D == 1 ? q.v : q.w);
+}
+
+// Physical flux F(W).e_d (Sec. 3.2, Eq. NSEquation_terms) of a face state.
+template <int D, typename R>
+__device__ __forceinline__ void phys_flux(const FaceState<R>& q, R F[5]) {
+  R un = comp<D>(q);
+  R m = q.rho * un;
+  F[0] = m;
+  F[1] = m * q.u;
+  F[2] = m * q.v;
+  F[3] = m * q.w;
+  F[1 + D] += q.p;
+  F[4] = (q.rho * q.E + q.p) * un;
+}
+
+// HLLC flux (App. C.4): Davis wave speeds S_L = min(u_L - c_L, u_R - c_R),
+// S_R = max(u_L + c_L, u_R + c_R), the contact speed S* as printed, and
+// F* = F_K + S_K (W*_K - W_K) with W*_K = rho_K (S_K - u_K)/(S_K - S*) [1, V*, E*_K],
+// V* normal = S*, tangential = side K's, E*_K = E_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K))).
+template <int D, typename R>
+__device__ __forceinline__ void hllc(const FaceState<R>& L, const FaceState<R>& Rt, R F[5]) {
+  const R uL = comp<D>(L), uR = comp<D>(Rt);
+  const R SL = fmin(uL - L.c, uR - Rt.c);
+  const R SR = fmax(uL + L.c, uR + Rt.c);
+  const R aL = L.rho * (SL - uL), aR = Rt.rho * (SR - uR);
+  const R Ss = (Rt.p - L.p + uL * aL - uR * aR) / (aL - aR);
+  if ((R)0 <= SL) {
+    phys_flux<D>(L, F);
+    return;
+  }
+  bool left;
+  if ((R)0 <= Ss) left = true;
+  else if ((R)0 <= SR) left = false;
+  else {
+    phys_flux<D>(Rt, F);
+    return;
+  }
+  const FaceState<R>& K = left ? L : Rt;
+  const R SK = left ? SL : SR;
+  const R uK = left ? uL : uR;
+  const R aK = left ? aL : aR;
+  phys_flux<D>(K, F);
+  const R fac = aK / (SK - Ss);
+  const R Es = K.E + (Ss - uK) * (Ss + K.p / aK);
+  R ws[5] = {fac, fac * K.u, fac * K.v, fac * K.w, fac * Es};
+  ws[1 + D] = fac * Ss;
+  const R wk[5] = {K.rho, K.rho * K.u, K.rho * K.v, K.rho * K.w, K.rho * K.E};
+#pragma unroll
+  for (int v = 0; v < 5; ++v) F[v] = F[v] + SK * (ws[v] - wk[v]);
+}
+
+// ---------------------------------------------------------------------------
+// Exact two-material Riemann problem (Sec. 4.2, Eq. 1DRiemannProblem with the
+// interface conditions of Sec. 3.5.1), FP64. Newton on p* from the PVRS guess,
+// stop when |dp| <= 1e-12 |p| and take one more step; 50 steps then bisection.
+// SG wave curves in closed form; MG shock from the Hugoniot root, MG
+// rarefaction by RK4 on 64 equal pressure substeps.
+// ---------------------------------------------------------------------------
+constexpr double kNewtonTol = 1e-12;
+constexpr int kNewtonCap = 50;
+constexpr int kBisectCap = 200;
+constexpr double kHugTol = 1e-14;
+constexpr int kHugCap = 100;
+constexpr int kRk4Steps = 64;
+
+struct Side {
+  double rho, u, p, c, e;
+};
+
+__device__ inline bool make_side(const EosDev& q, double rho, double u, double p, Side& K) {
+  if (!(rho > 0.0)) return false;
+  double e, c2;
+  if (!eos_e_c2<double>(q, rho, 1.0 / rho, p, e, c2)) return false;
+  K.rho = rho;
+  K.u = u;
+  K.p = p;
+  K.c = sqrt(c2);
+  K.e = e;
+  return true;
+}
+
+__device__ inline double eos_plow(const EosDev& q) {
+  if (q.type == M2C_EOS_SG) return -q.pc;
+  return isfinite(q.eta_min) ? q.pmin : -INFINITY;
+}
+
+__device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs) {
+  const double g = q.g, pb = p + q.pc, pbK = K.p + q.pc;
+  if (!(pb >= 0.0) || !(pbK > 0.0)) return M2C_ENONPHYS;
+  if (p > K.p) {
+    double A = 2.0 / ((g + 1.0) * K.rho);
+    double B = (g - 1.0) / (g + 1.0) * pbK;
+    double sq = sqrt(A / (pb + B));
+    f = (p - K.p) * sq;
+    df = sq * (1.0 - 0.5 * (p - K.p) / (pb + B));
+    double r = pb / pbK, gm = (g - 1.0) / (g + 1.0);
+    rs = K.rho * (r + gm) / (gm * r + 1.0);
+  } else {
+    double r = pb / pbK;
+    f = 2.0 * K.c / (g - 1.0) * (pow(r, (g - 1.0) / (2.0 * g)) - 1.0);
+    df = pow(r, -(g + 1.0) / (2.0 * g)) / (K.rho * K.c);
+    rs = K.rho * pow(r, 1.0 / g);
+  }
+  return M2C_OK;
+}
+
+// de/drho at constant p for MG
+__device__ inline bool mg_dedr(const EosDev& q, double rho, double& dedr) {
+  double eta = 1.0 - q.rho0 / rho;
+  if (!(eta < q.eta_max)) return false;
+  double pR, dpR, eR, deR;
+  mg_ref<double>(q, eta, pR, dpR, eR, deR);
+  dedr = (deR - dpR * q.inv_rg) * q.rho0 / (rho * rho);
+  return true;
+}
+
+// Density on the MG Hugoniot through K at pressure p (safeguarded Newton in a
+// closed bracket, one extra step after convergence) and d rho/dp along it.
+__device__ inline int mg_hugoniot(const EosDev& q, const Side& K, double p, double& rho_out, double& drdp) {
+  double lo = K.rho, hi = q.rho0 * q.s / (q.s - 1.0);
+  if (!(hi > lo)) return M2C_ENONPHYS;
+  double rho = K.rho + (p - K.p) / (K.c * K.c);
+  if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
+  bool extra = false, done = false;
+  for (int it = 0; it < kHugCap; ++it) {
+    double eta = 1.0 - q.rho0 / rho;
+    if (!(eta < q.eta_max)) return M2C_ENONPHYS;
+    double pR, dpR, eR, deR;
+    mg_ref<double>(q, eta, pR, dpR, eR, deR);
+    double e = eR + (p - pR) * q.inv_rg;
+    double dedr = (deR - dpR * q.inv_rg) * q.rho0 / (rho * rho);
+    double H = e - K.e - 0.5 * (p + K.p) * (1.0 / K.rho - 1.0 / rho);
+    double dH = dedr - 0.5 * (p + K.p) / (rho * rho);
+    if (H > 0.0) lo = rho; else hi = rho;
+    double rn = rho - H / dH;
+    if (!(rn >= lo && rn <= hi)) rn = 0.5 * (lo + hi);
+    bool conv = fabs(rn - rho) <= kHugTol * rn;
+    rho = rn;
+    if (extra) { done = true; break; }
+    if (conv) extra = true;
+  }
+  if (!done) return M2C_ENOCONV;
+  double dedr;
+  if (!mg_dedr(q, rho, dedr)) return M2C_ENONPHYS;
+  double Hp = q.inv_rg - 0.5 * (1.0 / K.rho - 1.0 / rho);
+  double Hr = dedr - 0.5 * (p + K.p) / (rho * rho);
+  rho_out = rho;
+  drdp = -Hp / Hr;
+  return M2C_OK;
+}
+
+__device__ inline int mg_rhs(const EosDev& q, double p, double rho, double& drho, double& dfv) {
+  double e, c2;
+  if (!eos_e_c2<double>(q, rho, 1.0 / rho, p, e, c2)) return M2C_ENONPHYS;
+  drho = 1.0 / c2;
+  dfv = 1.0 / (rho * sqrt(c2));
+  return M2C_OK;
+}
+
+__device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs) {
+  if (p == K.p) {
+    f = 0.0;
+    df = 1.0 / (K.rho * K.c);
+    rs = K.rho;
+    return M2C_OK;
+  }
+  if (p > K.p) {
+    double rho, drdp;
+    int st = mg_hugoniot(q, K, p, rho, drdp);
+    if (st) return st;
+    double dv = 1.0 / K.rho - 1.0 / rho;
+    double fv = sqrt((p - K.p) * dv);
+    f = fv;
+    df = (dv + (p - K.p) * drdp / (rho * rho)) / (2.0 * fv);
+    rs = rho;
+    return M2C_OK;
+  }
+  const double hs = (p - K.p) / kRk4Steps;
+  double rho = K.rho, fv = 0.0;
+  for (int i = 0; i < kRk4Steps; ++i) {
+    double pi = K.p + i * hs;
+    double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
+    int st = mg_rhs(q, pi, rho, k1r, k1f);
+    if (!st) st = mg_rhs(q, pi + 0.5 * hs, rho + 0.5 * hs * k1r, k2r, k2f);
+    if (!st) st = mg_rhs(q, pi + 0.5 * hs, rho + 0.5 * hs * k2r, k3r, k3f);
+    if (!st) st = mg_rhs(q, pi + hs, rho + hs * k3r, k4r, k4f);
+    if (st) return st;
+    rho = rho + hs / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
+    fv = fv + hs / 6.0 * (k1f + 2.0 * k2f + 2.0 * k3f + k4f);
+  }
+  double e, c2;
+  if (!eos_e_c2<double>(q, rho, 1.0 / rho, p, e, c2)) return M2C_ENONPHYS;
+  f = fv;
+  df = 1.0 / (rho * sqrt(c2));
+  rs = rho;
+  return M2C_OK;
+}
+
+__device__ inline int wave(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs) {
+  return q.type == M2C_EOS_SG ? wave_sg(q, K, p, f, df, rs) : wave_mg(q, K, p, f, df, rs);
+}
+
+__device__ inline int riemann_F(const EosDev& qL, const Side& L, const EosDev& qR, const Side& Rs, double p,
+                                double& F, double& dF) {
+  double fL, dfL, rL, fR, dfR, rR;
+  int st = wave(qL, L, p, fL, dfL, rL);
+  if (!st) st = wave(qR, Rs, p, fR, dfR, rR);
+  if (st) return st;
+  F = fL + fR + (Rs.u - L.u);
+  dF = dfL + dfR;
+  return M2C_OK;
+}
+
+struct RiemannOut {
+  double p, u, rhoL, rhoR;
+};
+
+// Solves the 1D problem between (rho, u, p) states; returns a status and the
+// Newton/bisection iteration count.
+__device__ inline int riemann_solve(const EosDev& qL, double rl, double ul, double pl, const EosDev& qR, double rr,
+                                    double ur, double pr, RiemannOut& out, int& iters) {
+  Side L, Rs;
+  iters = 0;
+  if (!make_side(qL, rl, ul, pl, L) || !make_side(qR, rr, ur, pr, Rs)) return M2C_ENONPHYS;
+  const double plow = fmax(eos_plow(qL), eos_plow(qR));
+  double F, dF;
+  int st;
+  if (isfinite(plow)) {
+    st = riemann_F(qL, L, qR, Rs, plow, F, dF);
+    if (st) return st;
+    if (F >= 0.0) return M2C_EVACUUM;
+  }
+  double p = 0.5 * (L.p + Rs.p) - 0.125 * (Rs.u - L.u) * (L.rho + Rs.rho) * (L.c + Rs.c);
+  if (!(p > plow)) {
+    double gap = fmin(L.p, Rs.p) - plow;
+    if (!(gap > 0.0)) gap = fmax(L.p, Rs.p) - plow;
+    p = plow + 1e-3 * gap;
+  }
+  int it;
+  bool conv = false, extra = false;
+  for (it = 1; it <= kNewtonCap; ++it) {
+    st = riemann_F(qL, L, qR, Rs, p, F, dF);
+    if (st) return st;
+    double pn = p - F / dF;
+    if (!(pn > plow)) pn = 0.5 * (p + plow);
+    bool small = fabs(pn - p) <= kNewtonTol * fabs(pn);
+    p = pn;
+    if (extra) { conv = true; break; }
+    if (small) extra = true;
+  }
+  if (!conv) {
+    double a = plow, b = fmax(L.p, Rs.p);
+    if (!isfinite(a)) {
+      a = fmin(L.p, Rs.p);
+      for (int k = 0; k < kBisectCap; ++k) {
+        st = riemann_F(qL, L, qR, Rs, a, F, dF);
+        if (st) return st;
+        if (F < 0.0) break;
+        a = a - 2.0 * fabs(a) - 1.0;
+      }
+    }
+    for (int k = 0; k < kBisectCap; ++k) {
+      st = riemann_F(qL, L, qR, Rs, b, F, dF);
+      if (st) return st;
+      if (F > 0.0) break;
+      b = 2.0 * b + fabs(b) + 1.0;
+    }
+    bool ok = false;
+    for (int k = 0; k < kBisectCap; ++k) {
+      double m = 0.5 * (a + b);
+      st = riemann_F(qL, L, qR, Rs, m, F, dF);
+      if (st) return st;
+      if (F < 0.0) a = m; else b = m;
+      ++it;
+      if (b - a <= 1e-14 * fmax(fabs(a), fabs(b))) { ok = true; break; }
+    }
+    if (!ok) return M2C_ENOCONV;
+    p = 0.5 * (a + b);
+  }
+  double fL, dfL, rL, fR, dfR, rR;
+  st = wave(qL, L, p, fL, dfL, rL);
+  if (!st) st = wave(qR, Rs, p, fR, dfR, rR);
+  if (st) return st;
+  out.p = p;
+  out.u = 0.5 * (L.u + Rs.u) + 0.5 * (fR - fL);
+  out.rhoL = rL;
+  out.rhoR = rR;
+  iters = it;
+  return M2C_OK;
+}
+
+}  // namespace m2c

@@ -1,0 +1,1429 @@
+// libm2cgpu: GB300 (sm_103a) kernels and C-ABI of the multi-material
+// finite-volume step of M2C (arXiv 2508.16387), declared in include/m2c.h.
+//
+// One time step (Sec. 2.3 steps (1)-(6), RK2 of Sec. 4.3) is eight launches:
+//   stage 1: k_stage (bulk) -> k_fiver (interface faces) -> k_finish (interface cells)
+//   stage 2: k_stage        -> k_fiver                  -> k_finish
+//   [k_reinit x iterations, every reinit_every steps] -> k_phase_fix -> k_end_step
+// The bulk kernel marches a 32 x TY column tile along z: a plane of primitive
+// states with a two-cell halo in shared memory, a register window of planes
+// along z, MUSCL face states and HLLC fluxes per face computed once, the
+// residual sum, the level-set residual and the Runge-Kutta update fused in
+// the same pass. Faces whose two cells have different materials are not
+// solved there: they are compacted by warp ballot into a work list and solved
+// packed by k_fiver (exact Riemann problem, FP64), and the cells touching them
+// are finished by k_finish. The time step is reduced on the device (max of
+// the wave-speed sum, atomically, in the kernels that write the new state).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "m2c_kernels.cuh"
+
+namespace m2c {
+
+// ---------------------------------------------------------------------------
+// Conservative -> primitive
+// ---------------------------------------------------------------------------
+
+// FP64 path: u = (rho u)/rho, e = (rho E - rho|V|^2/2)/rho, p = p(rho, e).
+// Mixed path: the same with FP32 velocities and kinetic energy; rho e and, for
+// the stiffened gas, the pressure (a difference of large numbers when p_c is
+// large) in FP64, then rounded to FP32.
+template <typename R>
+__device__ __forceinline__ bool cons_to_prim(const EosDev& q, const double* __restrict__ W, long long N, long long c,
+                                             R P[5]) {
+  const double rho = W[c], m1 = W[N + c], m2 = W[2 * N + c], m3 = W[3 * N + c], E = W[4 * N + c];
+  if constexpr (sizeof(R) == 8) {
+    const double inv = 1.0 / rho;
+    const double u = m1 * inv, v = m2 * inv, w = m3 * inv;
+    const double ke = 0.5 * ((m1 * u + m2 * v) + m3 * w);
+    const double e = (E - ke) * inv;
+    double p = 0.0;
+    const bool ok = eos_p<double>(q, rho, inv, e, p);
+    P[0] = rho; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
+    return ok && rho > 0.0;
+  } else {
+    const float rf = (float)rho;
+    const float inv = 1.0f / rf;
+    const float f1 = (float)m1, f2 = (float)m2, f3 = (float)m3;
+    const float u = f1 * inv, v = f2 * inv, w = f3 * inv;
+    const float ke = 0.5f * ((f1 * u + f2 * v) + f3 * w);
+    const double rhoe = E - (double)ke;
+    float p = 0.0f;
+    bool ok = true;
+    if (q.type == M2C_EOS_SG) {
+      p = (float)(q.gm1 * rhoe - q.gpc);
+    } else {
+      ok = eos_p<float>(q, rf, inv, (float)rhoe * inv, p);
+    }
+    P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
+    return ok && rho > 0.0;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ bool make_face(const EosDev& q, R rho, R u, R v, R w, R p, FaceState<R>& F) {
+  R e = (R)0, c2 = (R)0;
+  const bool ok = eos_e_c2<R>(q, rho, (R)1 / rho, p, e, c2);
+  F.rho = rho; F.u = u; F.v = v; F.w = w; F.p = p;
+  F.c = sqrt(c2);
+  F.E = e + (R)0.5 * ((u * u + v * v) + w * w);
+  return ok;
+}
+
+// MUSCL face states of one cell along one axis: q -+ sigma/2 with the modified
+// van Albada slope (App. D). same = both stencil neighbours have the cell's
+// material (otherwise first order, Reading R11); a non-admissible face state
+// makes the whole axis first order (Reading R12). bad: even the cell state is
+// not admissible.
+template <typename R>
+__device__ __forceinline__ void cell_faces(const EosDev& q, const R Pm[5], const R P[5], const R Pp[5], bool same,
+                                           FaceState<R>& Qm, FaceState<R>& Qp, bool& bad) {
+  if (same) {
+    R s[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s[v] = va_slope<R>(P[v] - Pm[v], Pp[v] - P[v]);
+    const R hf = (R)0.5;
+    const bool okm = make_face<R>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2], P[3] - hf * s[3],
+                                  P[4] - hf * s[4], Qm);
+    const bool okp = make_face<R>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2], P[3] + hf * s[3],
+                                  P[4] + hf * s[4], Qp);
+    if (okm && okp) return;
+  }
+  if (!make_face<R>(q, P[0], P[1], P[2], P[3], P[4], Qm)) bad = true;
+  Qp = Qm;
+}
+
+// Wave-speed sum of a state, sum over the axes with more than one cell of
+// |V_d| + c (the CFL reading of the design notes).
+__device__ __forceinline__ double wave_sum(const Grid& g, const EosDev& q, const double* W, long long N, long long c,
+                                           bool& ok) {
+  double P[5];
+  ok = cons_to_prim<double>(q, W, N, c, P);
+  double e, c2;
+  ok = ok && eos_e_c2<double>(q, P[0], 1.0 / P[0], P[4], e, c2);
+  const double cs = sqrt(c2);
+  double lam = 0.0;
+  if (g.active[0]) lam = lam + (fabs(P[1]) + cs);
+  if (g.active[1]) lam = lam + (fabs(P[2]) + cs);
+  if (g.active[2]) lam = lam + (fabs(P[3]) + cs);
+  return lam;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block max of a positive double, then one atomic max on its bit pattern
+// (positive doubles order like their bit patterns).
+__device__ __forceinline__ void block_max_to(double v, unsigned long long* dst, double* s_red) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) s_red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double x = lane < nw ? s_red[lane] : 0.0;
+    x = warp_max(x);
+    if (lane == 0 && x > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(x));
+  }
+}
+
+__device__ __forceinline__ int find_grid(const long long* __restrict__ tile_begin, int ngrid, long long tile) {
+  int lo = 0, hi = ngrid - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_begin[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Bulk stage kernel
+// ---------------------------------------------------------------------------
+
+template <typename R, int TY>
+struct StageSmem {
+  static constexpr int TX = 32, HX = TX + 4, HY = TY + 4;
+  static constexpr size_t q_off = 0;
+  static constexpr size_t phi_off = q_off + sizeof(R) * 5 * HY * HX;
+  static constexpr size_t xs_off = phi_off + sizeof(R) * HY * HX;
+  static constexpr size_t ys_off = xs_off + sizeof(FaceState<R>) * TY * (TX + 2) * 2;
+  static constexpr size_t fx_off = ys_off + sizeof(FaceState<R>) * (TY + 2) * TX * 2;
+  static constexpr size_t fy_off = fx_off + sizeof(R) * 5 * TY * (TX + 1);
+  static constexpr size_t id_off = fy_off + sizeof(R) * 5 * (TY + 1) * TX;
+  static constexpr size_t eos_off = (id_off + HY * HX + 15) / 16 * 16;
+  static constexpr size_t bytes = eos_off + sizeof(EosDev) * 2;
+};
+
+template <typename R, int TY>
+__global__ void __launch_bounds__(32 * TY)
+k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, int mode) {
+  constexpr int TX = 32, NT = TX * TY, HX = TX + 4, HY = TY + 4;
+  using SM = StageSmem<R, TY>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  R* s_q = reinterpret_cast<R*>(smem + SM::q_off);                         // [5][HY][HX]
+  R* s_phi = reinterpret_cast<R*>(smem + SM::phi_off);                     // [HY][HX]
+  FaceState<R>* s_xs = reinterpret_cast<FaceState<R>*>(smem + SM::xs_off);  // [TY][TX+2][2]
+  FaceState<R>* s_ys = reinterpret_cast<FaceState<R>*>(smem + SM::ys_off);  // [TY+2][TX][2]
+  R* s_fx = reinterpret_cast<R*>(smem + SM::fx_off);                       // [5][TY][TX+1]
+  R* s_fy = reinterpret_cast<R*>(smem + SM::fy_off);                       // [5][TY+1][TX]
+  uint8_t* s_id = smem + SM::id_off;                                       // [HY][HX]
+  EosDev* s_eos = reinterpret_cast<EosDev*>(smem + SM::eos_off);
+  __shared__ double s_dt;
+  __shared__ double s_red[32];
+
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  const long long tile = blockIdx.x;
+  const int gidx = find_grid(tile_begin, ngrid, tile);
+  const Grid& G = grids[gidx];
+  const int nx = G.nx, ny = G.ny, nz = G.nz;
+  const long long N = G.N;
+  long long t = tile - tile_begin[gidx];
+  const int bx = (int)(t % G.tiles_x);
+  t /= G.tiles_x;
+  const int by = (int)(t % G.tiles_y);
+  const int bz = (int)(t / G.tiles_y);
+  const int x0 = bx * TX, y0 = by * TY, k0 = bz * G.tz, k1 = min(k0 + G.tz, nz);
+  const R ih = (R)G.inv_h;
+  const R i6h = (R)(1.0 / (6.0 * G.h));
+  const double* __restrict__ Ws = mode == kStage2 ? G.W1 : G.W;
+  const double* __restrict__ phis = mode == kStage2 ? G.phi1 : G.phi;
+  Ctrl* ctrl = G.ctrl;
+  const int slot = mode == kStage2 ? 1 : 0;
+  const long long step = ctrl->step;
+
+  if (tid < 2) s_eos[tid] = G.eos[tid];
+  if (tid == 0) s_dt = mode == kResidual ? 0.0 : lam_to_dt(G, ctrl->lam[step & 1]);
+  __syncthreads();
+  const double dt = s_dt;
+
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool own_xy = gx < nx && gy < ny;
+
+  // material at the start of the step and the stage state of one cell
+  auto load = [&](int i, int j, int k, R P[5], R& ph, int& idv) {
+    const long long c = cell_of(G, i, j, k);
+    const double phd = phis[c];
+    idv = mode == kStage2 ? (G.id[c] & 1) : (phd < 0.0 ? 1 : 0);
+    ph = (R)phd;
+    if (!cons_to_prim<R>(s_eos[idv], Ws, N, c, P)) latch_error(ctrl, M2C_ENONPHYS, c);
+  };
+
+  // ---- warm-up of the z window: planes k0-2 .. k0+1
+  R Pa[5], P0[5], P1[5], P2[5];
+  R ph[5];
+  int ida, idm, id0, id1, id2;
+  FaceState<R> QzP, Qtmp, QzM1, QzP1;
+  R Fzm[5], Fzp[5];
+  bool bad = false;
+  {
+    R Pb[5];
+    int idb;
+    load(gx, gy, k0 - 2, Pb, ph[0], idb);
+    load(gx, gy, k0 - 1, Pa, ph[1], ida);
+    load(gx, gy, k0, P0, ph[2], id0);
+    load(gx, gy, k0 + 1, P1, ph[3], id1);
+    FaceState<R> QaP, Q0M;
+    cell_faces<R>(s_eos[ida], Pb, Pa, P0, idb == ida && id0 == ida, Qtmp, QaP, bad);
+    cell_faces<R>(s_eos[id0], Pa, P0, P1, ida == id0 && id1 == id0, Q0M, QzP, bad);
+    if (ida == id0) {
+      hllc<2, R>(QaP, Q0M, Fzm);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fzm[v] = (R)0;
+    }
+    idm = ida;
+  }
+
+  double lam_max = 0.0;
+  const int nhalo = 4 * (TX + TY);
+
+  for (int k = k0; k < k1; ++k) {
+    // ---- own column: plane k+2, z face states of cell k+1, z flux of face k+1/2
+    load(gx, gy, k + 2, P2, ph[4], id2);
+    cell_faces<R>(s_eos[id1], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad);
+    if (id0 == id1) {
+      hllc<2, R>(QzP, QzM1, Fzp);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fzp[v] = (R)0;
+    }
+    // ---- plane k into shared memory: own cells and the two-cell halo (no corners)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s_q[(v * HY + ty + 2) * HX + tx + 2] = P0[v];
+    s_phi[(ty + 2) * HX + tx + 2] = ph[2];
+    s_id[(ty + 2) * HX + tx + 2] = (uint8_t)id0;
+    for (int hsel = tid; hsel < nhalo; hsel += NT) {
+      int hx, hy;
+      if (hsel < 4 * TY) {
+        const int c4 = hsel / TY, r = hsel % TY;
+        hx = c4 < 2 ? c4 : TX + c4;
+        hy = r + 2;
+      } else {
+        const int h2 = hsel - 4 * TY;
+        const int c4 = h2 / TX, col = h2 % TX;
+        hy = c4 < 2 ? c4 : TY + c4;
+        hx = col + 2;
+      }
+      R Ph[5], phh;
+      int idh;
+      load(x0 + hx - 2, y0 + hy - 2, k, Ph, phh, idh);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s_q[(v * HY + hy) * HX + hx] = Ph[v];
+      s_phi[hy * HX + hx] = phh;
+      s_id[hy * HX + hx] = (uint8_t)idh;
+    }
+    __syncthreads();
+
+    // ---- MUSCL face states along x (cells x = -1 .. TX) and y (cells y = -1 .. TY)
+    for (int i = tid; i < (TX + 2) * TY; i += NT) {
+      const int xs = i % (TX + 2), row = i / (TX + 2);
+      const int hx = xs + 1, hy = row + 2;
+      R Pm[5], P[5], Pp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        Pm[v] = s_q[(v * HY + hy) * HX + hx - 1];
+        P[v] = s_q[(v * HY + hy) * HX + hx];
+        Pp[v] = s_q[(v * HY + hy) * HX + hx + 1];
+      }
+      const int ic = s_id[hy * HX + hx];
+      const bool same = s_id[hy * HX + hx - 1] == ic && s_id[hy * HX + hx + 1] == ic;
+      bool b = false;
+      cell_faces<R>(s_eos[ic], Pm, P, Pp, same, s_xs[(row * (TX + 2) + xs) * 2 + 0],
+                    s_xs[(row * (TX + 2) + xs) * 2 + 1], b);
+      if (b) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, x0 + xs - 1, y0 + row, k));
+    }
+    for (int i = tid; i < TX * (TY + 2); i += NT) {
+      const int x = i % TX, ys = i / TX;
+      const int hx = x + 2, hy = ys + 1;
+      R Pm[5], P[5], Pp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        Pm[v] = s_q[(v * HY + hy - 1) * HX + hx];
+        P[v] = s_q[(v * HY + hy) * HX + hx];
+        Pp[v] = s_q[(v * HY + hy + 1) * HX + hx];
+      }
+      const int ic = s_id[hy * HX + hx];
+      const bool same = s_id[(hy - 1) * HX + hx] == ic && s_id[(hy + 1) * HX + hx] == ic;
+      bool b = false;
+      cell_faces<R>(s_eos[ic], Pm, P, Pp, same, s_ys[(ys * TX + x) * 2 + 0], s_ys[(ys * TX + x) * 2 + 1], b);
+      if (b) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, x0 + x, y0 + ys - 1, k));
+    }
+    __syncthreads();
+
+    // ---- HLLC on every x face (f between cells f-1 and f) and y face of the tile
+    for (int i = tid; i < (TX + 1) * TY; i += NT) {
+      const int f = i % (TX + 1), row = i / (TX + 1);
+      R F[5];
+      const int il = s_id[(row + 2) * HX + f + 1], ir = s_id[(row + 2) * HX + f + 2];
+      if (il == ir) {
+        hllc<0, R>(s_xs[(row * (TX + 2) + f) * 2 + 1], s_xs[(row * (TX + 2) + f + 1) * 2 + 0], F);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[v] = (R)0;
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s_fx[(v * TY + row) * (TX + 1) + f] = F[v];
+    }
+    for (int i = tid; i < TX * (TY + 1); i += NT) {
+      const int x = i % TX, f = i / TX;
+      R F[5];
+      const int il = s_id[(f + 1) * HX + x + 2], ir = s_id[(f + 2) * HX + x + 2];
+      if (il == ir) {
+        hllc<1, R>(s_ys[(f * TX + x) * 2 + 1], s_ys[((f + 1) * TX + x) * 2 + 0], F);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[v] = (R)0;
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s_fy[(v * (TY + 1) + f) * TX + x] = F[v];
+    }
+    __syncthreads();
+
+    // ---- per cell: residual, level set, Runge-Kutta update, work lists
+    {
+      const int hxc = tx + 2, hyc = ty + 2;
+      const int idxm = s_id[hyc * HX + hxc - 1], idxp = s_id[hyc * HX + hxc + 1];
+      const int idym = s_id[(hyc - 1) * HX + hxc], idyp = s_id[(hyc + 1) * HX + hxc];
+      const bool inside = own_xy;
+      const bool is_if = inside && (idxm != id0 || idxp != id0 || idym != id0 || idyp != id0 || idm != id0 ||
+                                    id1 != id0);
+      R res[5];
+      R Fxm[5], Fxp[5], Fym[5], Fyp[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        Fxm[v] = s_fx[(v * TY + ty) * (TX + 1) + tx];
+        Fxp[v] = s_fx[(v * TY + ty) * (TX + 1) + tx + 1];
+        Fym[v] = s_fy[(v * (TY + 1) + ty) * TX + tx];
+        Fyp[v] = s_fy[(v * (TY + 1) + ty + 1) * TX + tx];
+        res[v] = ((Fxm[v] - Fxp[v]) * ih + (Fym[v] - Fyp[v]) * ih) + (Fzm[v] - Fzp[v]) * ih;
+      }
+      // level-set residual -((u phi_x + v phi_y) + w phi_z), third-order upwind-biased (Sec. 4.4)
+      const R u = P0[1], vv = P0[2], w = P0[3];
+      const R* prow = s_phi + hyc * HX + hxc;
+      R Dx, Dy, Dz;
+      if (u >= (R)0) Dx = (((R)2 * prow[1] + (R)3 * prow[0]) - (R)6 * prow[-1] + prow[-2]) * i6h;
+      else Dx = ((-prow[2] + (R)6 * prow[1]) - (R)3 * prow[0] - (R)2 * prow[-1]) * i6h;
+      if (vv >= (R)0) Dy = (((R)2 * prow[HX] + (R)3 * prow[0]) - (R)6 * prow[-HX] + prow[-2 * HX]) * i6h;
+      else Dy = ((-prow[2 * HX] + (R)6 * prow[HX]) - (R)3 * prow[0] - (R)2 * prow[-HX]) * i6h;
+      if (w >= (R)0) Dz = (((R)2 * ph[3] + (R)3 * ph[2]) - (R)6 * ph[1] + ph[0]) * i6h;
+      else Dz = ((-ph[4] + (R)6 * ph[3]) - (R)3 * ph[2] - (R)2 * ph[1]) * i6h;
+      const R Lphi = -((u * Dx + vv * Dy) + w * Dz);
+
+      const long long c = ((long long)k * ny + (inside ? gy : 0)) * nx + (inside ? gx : 0);
+      bool flip = false;
+      if (inside) {
+        if (mode == kResidual) {
+          if (!is_if) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) G.resR[v * N + c] = (double)res[v];
+          }
+          G.resL[c] = (double)Lphi;
+          G.id[c] = (uint8_t)id0;
+        } else if (mode == kStage1) {
+          G.phi1[c] = G.phi[c] + dt * (double)Lphi;
+          G.id[c] = (uint8_t)id0;
+          if (!is_if) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) G.W1[v * N + c] = G.W[v * N + c] + dt * (double)res[v];
+          }
+        } else {
+          const double pn = 0.5 * (G.phi[c] + (G.phi1[c] + dt * (double)Lphi));
+          G.phi[c] = pn;
+          flip = (pn < 0.0) != (id0 == 1);
+          if (!is_if) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * (double)res[v]));
+            if (!flip) {
+              bool ok;
+              const double lam = wave_sum(G, s_eos[id0], G.W, N, c, ok);
+              if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
+              lam_max = fmax(lam_max, lam);
+            }
+          }
+        }
+      }
+      // ---- work lists: warp ballot, one atomic per warp
+      const unsigned lane = tid & 31;
+      const unsigned lt = (1u << lane) - 1u;
+      {
+        const unsigned m = __ballot_sync(0xffffffffu, is_if);
+        if (m) {
+          int base = 0;
+          const int leader = __ffs(m) - 1;
+          if ((int)lane == leader) base = atomicAdd(&ctrl->ncell[slot], __popc(m));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (is_if) {
+            const int s = base + __popc(m & lt);
+            if (s < G.cell_cap) {
+              IfCell* e = G.cells + s;
+              e->cell = c;
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                e->F[0][v] = (double)Fxm[v];
+                e->F[1][v] = (double)Fxp[v];
+                e->F[2][v] = (double)Fym[v];
+                e->F[3][v] = (double)Fyp[v];
+                e->F[4][v] = (double)Fzm[v];
+                e->F[5][v] = (double)Fzp[v];
+              }
+              G.cell_slot[c] = s;
+            } else {
+              latch_error(ctrl, M2C_EOVERFLOW, c);
+            }
+          }
+        }
+      }
+      {
+        const bool fx = inside && idxp != id0, fy = inside && idyp != id0, fz = inside && id1 != id0;
+        const int nf = (int)fx + (int)fy + (int)fz;
+        int incl = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if ((int)lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+          int base = 0;
+          if (lane == 31) base = atomicAdd(&ctrl->nface[slot], total);
+          base = __shfl_sync(0xffffffffu, base, 31);
+          int s = base + incl - nf;
+          const bool fl[3] = {fx, fy, fz};
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            if (fl[d]) {
+              if (s < G.face_cap) {
+                G.faces[s].cell = c;
+                G.faces[s].dir = d;
+              } else {
+                latch_error(ctrl, M2C_EOVERFLOW, c);
+              }
+              ++s;
+            }
+          }
+        }
+      }
+      if (mode == kStage2) {
+        const unsigned m = __ballot_sync(0xffffffffu, flip);
+        if (m) {
+          int base = 0;
+          const int leader = __ffs(m) - 1;
+          if ((int)lane == leader) base = atomicAdd(&ctrl->nflip, __popc(m));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (flip) {
+            const int s = base + __popc(m & lt);
+            if (s < G.flip_cap) G.flips[s] = c;
+            else latch_error(ctrl, M2C_EOVERFLOW, c);
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- shift the z window
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      P0[v] = P1[v];
+      P1[v] = P2[v];
+      Fzm[v] = Fzp[v];
+    }
+    ph[0] = ph[1]; ph[1] = ph[2]; ph[2] = ph[3]; ph[3] = ph[4];
+    idm = id0; id0 = id1; id1 = id2;
+    QzP = QzP1;
+  }
+  if (bad) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, gx, gy, k0));
+  if (mode == kStage2) block_max_to(lam_max, &ctrl->lam[(step + 1) & 1], s_red);
+}
+
+// ---------------------------------------------------------------------------
+// FIVER on the packed interface faces (Sec. 4.2): exact two-material Riemann
+// problem on the normal projections of the two cell states (their face states
+// are the cell states, Reading R11), star states with each side's tangential
+// velocity (Reading R8), F_ij = Phi(W_ij, W*_ij; EOS_i) and
+// F_ji = Phi(W*_ji, W_ji; EOS_j) (Reading R16), FP64.
+// ---------------------------------------------------------------------------
+
+template <int D>
+__device__ __forceinline__ void fiver_fluxes(const FaceState<double>& A, const FaceState<double>& SA,
+                                             const FaceState<double>& SB, const FaceState<double>& B, double Fa[5],
+                                             double Fb[5]) {
+  hllc<D, double>(A, SA, Fa);
+  hllc<D, double>(SB, B, Fb);
+}
+
+__global__ void __launch_bounds__(128) k_fiver(const Grid* __restrict__ grids, int mode) {
+  const Grid& G = grids[blockIdx.y];
+  Ctrl* ctrl = G.ctrl;
+  const int slot = mode == kStage2 ? 1 : 0;
+  const int n = min(ctrl->nface[slot], G.face_cap);
+  const double* __restrict__ Ws = mode == kStage2 ? G.W1 : G.W;
+  const long long N = G.N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const IfFace f = G.faces[i];
+    const long long ca = f.cell;
+    const int ix = (int)(ca % G.nx), iy = (int)((ca / G.nx) % G.ny), iz = (int)(ca / ((long long)G.nx * G.ny));
+    const int d = f.dir;
+    const long long cb = cell_of(G, ix + (d == 0), iy + (d == 1), iz + (d == 2));
+    const int ia = G.id[ca] & 1, ib = G.id[cb] & 1;
+    const EosDev& qa = G.eos[ia];
+    const EosDev& qb = G.eos[ib];
+    double Pa[5], Pb[5];
+    bool ok = cons_to_prim<double>(qa, Ws, N, ca, Pa);
+    ok = cons_to_prim<double>(qb, Ws, N, cb, Pb) && ok;
+    double Fa[5] = {0, 0, 0, 0, 0}, Fb[5] = {0, 0, 0, 0, 0};
+    RiemannOut rs;
+    int its = 0;
+    int st = ok ? riemann_solve(qa, Pa[0], Pa[1 + d], Pa[4], qb, Pb[0], Pb[1 + d], Pb[4], rs, its) : M2C_ENONPHYS;
+    if (st == M2C_OK) {
+      FaceState<double> A, SA, SB, B;
+      double Sa[5] = {rs.rhoL, Pa[1], Pa[2], Pa[3], rs.p};
+      double Sb[5] = {rs.rhoR, Pb[1], Pb[2], Pb[3], rs.p};
+      Sa[1 + d] = rs.u;
+      Sb[1 + d] = rs.u;
+      bool okf = make_face<double>(qa, Pa[0], Pa[1], Pa[2], Pa[3], Pa[4], A);
+      okf = make_face<double>(qa, Sa[0], Sa[1], Sa[2], Sa[3], Sa[4], SA) && okf;
+      okf = make_face<double>(qb, Sb[0], Sb[1], Sb[2], Sb[3], Sb[4], SB) && okf;
+      okf = make_face<double>(qb, Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], B) && okf;
+      if (!okf) st = M2C_ENONPHYS;
+      if (d == 0) fiver_fluxes<0>(A, SA, SB, B, Fa, Fb);
+      else if (d == 1) fiver_fluxes<1>(A, SA, SB, B, Fa, Fb);
+      else fiver_fluxes<2>(A, SA, SB, B, Fa, Fb);
+    }
+    if (st != M2C_OK) {
+      latch_error(ctrl, st, ca);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fa[v] = Fb[v] = 0.0;
+    }
+    // a slot is trusted only if it is inside this stage's list and points back
+    // at the cell (an overflowed list leaves slots unwritten; the error is latched)
+    const int ncl = min(ctrl->ncell[slot], G.cell_cap);
+    const int sa = G.cell_slot[ca], sb = G.cell_slot[cb];
+    const bool oka = sa >= 0 && sa < ncl && G.cells[sa].cell == ca;
+    const bool okb = sb >= 0 && sb < ncl && G.cells[sb].cell == cb;
+    if (!oka || !okb) latch_error(ctrl, M2C_EOVERFLOW, ca);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      if (oka) G.cells[sa].F[2 * d + 1][v] = Fa[v];
+      if (okb) G.cells[sb].F[2 * d][v] = Fb[v];
+    }
+  }
+}
+
+// Interface cells: residual from the six stored face fluxes in the fixed
+// association ((x) + (y)) + (z), then the stage update.
+__global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, int mode) {
+  __shared__ double s_red[32];
+  const Grid& G = grids[blockIdx.y];
+  Ctrl* ctrl = G.ctrl;
+  const int slot = mode == kStage2 ? 1 : 0;
+  const int n = min(ctrl->ncell[slot], G.cell_cap);
+  const long long N = G.N;
+  const long long step = ctrl->step;
+  const double dt = mode == kResidual ? 0.0 : lam_to_dt(G, ctrl->lam[step & 1]);
+  const double ih = G.inv_h;
+  double lam_max = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const IfCell& e = G.cells[i];
+    const long long c = e.cell;
+    double res[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      res[v] = ((e.F[0][v] - e.F[1][v]) * ih + (e.F[2][v] - e.F[3][v]) * ih) + (e.F[4][v] - e.F[5][v]) * ih;
+    if (mode == kResidual) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) G.resR[v * N + c] = res[v];
+    } else if (mode == kStage1) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) G.W1[v * N + c] = G.W[v * N + c] + dt * res[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * res[v]));
+      const int id0 = G.id[c] & 1;
+      const bool flip = (G.phi[c] < 0.0) != (id0 == 1);
+      if (!flip) {
+        bool ok;
+        const double lam = wave_sum(G, G.eos[id0], G.W, N, c, ok);
+        if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
+        lam_max = fmax(lam_max, lam);
+      }
+    }
+  }
+  if (mode == kStage2) block_max_to(lam_max, &ctrl->lam[(step + 1) & 1], s_red);
+}
+
+// ---------------------------------------------------------------------------
+// Reinitialisation (Eq. reinit, Sec. 4.4): one Jacobi iteration
+// phi' = phi - dtau S(phi0) (G(phi) - 1), Godunov upwind |grad phi|,
+// S = phi0/sqrt(phi0^2 + h^2), dtau = h/2, first-layer cells fixed.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, const double* __restrict__ src,
+                                                double* __restrict__ dst, int first_iter) {
+  const Grid& G = grids[blockIdx.y];
+  const double* __restrict__ phi0 = G.phi;
+  const long long N = G.N;
+  const double h = G.h, ih = G.inv_h, dtau = 0.5 * G.h;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % G.nx), j = (int)((c / G.nx) % G.ny), k = (int)(c / ((long long)G.nx * G.ny));
+    const long long nb[6] = {cell_of(G, i - 1, j, k), cell_of(G, i + 1, j, k), cell_of(G, i, j - 1, k),
+                             cell_of(G, i, j + 1, k), cell_of(G, i, j, k - 1), cell_of(G, i, j, k + 1)};
+    const double p0 = phi0[c];
+    bool first;
+    if (first_iter) {
+      const bool s0 = p0 < 0.0;
+      first = false;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) first = first || ((phi0[nb[q]] < 0.0) != s0);
+      G.id[c] = (uint8_t)((G.id[c] & 1) | (first ? 2 : 0));
+    } else {
+      first = (G.id[c] & 2) != 0;
+    }
+    const double cur = src[c];
+    if (first) {
+      dst[c] = cur;
+      continue;
+    }
+    double G2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double a = (cur - src[nb[2 * d]]) * ih;
+      const double b = (src[nb[2 * d + 1]] - cur) * ih;
+      double x, y;
+      if (p0 >= 0.0) {
+        x = fmax(a, 0.0);
+        y = fmin(b, 0.0);
+      } else {
+        x = fmin(a, 0.0);
+        y = fmax(b, 0.0);
+      }
+      G2[d] = fmax(x * x, y * y);
+    }
+    const double Gn = sqrt((G2[0] + G2[1]) + G2[2]);
+    const double S = p0 / sqrt(p0 * p0 + h * h);
+    dst[c] = cur - dtau * S * (Gn - 1.0);
+  }
+}
+
+__global__ void k_copy(const Grid* __restrict__ grids, const double* __restrict__ src, double* __restrict__ dst) {
+  const Grid& G = grids[blockIdx.y];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x)
+    dst[c] = src[c];
+}
+
+// ---------------------------------------------------------------------------
+// Phase update (Sec. 2.3 step (6)): a cell whose material changed takes the
+// mean primitive state of its face neighbours that were and are of its new
+// material, else of its 26-neighbourhood, converted with the new EOS.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grids) {
+  __shared__ double s_red[32];
+  const Grid& G = grids[blockIdx.y];
+  Ctrl* ctrl = G.ctrl;
+  const int n = min(ctrl->nflip, G.flip_cap);
+  const long long N = G.N;
+  double lam_max = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const long long c = G.flips[t];
+    const int i = (int)(c % G.nx), j = (int)((c / G.nx) % G.ny), k = (int)(c / ((long long)G.nx * G.ny));
+    const int m = (G.phi[c] < 0.0) ? 1 : 0;
+    const EosDev& q = G.eos[m];
+    double sum[5] = {0, 0, 0, 0, 0};
+    int cnt = 0;
+    auto take = [&](long long nb) {
+      const int old_id = G.id[nb] & 1;
+      const int new_id = G.phi[nb] < 0.0 ? 1 : 0;
+      if (old_id == m && new_id == m) {
+        double P[5];
+        if (!cons_to_prim<double>(q, G.W, N, nb, P)) latch_error(ctrl, M2C_ENONPHYS, nb);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sum[v] = sum[v] + P[v];
+        ++cnt;
+      }
+    };
+    take(cell_of(G, i - 1, j, k));
+    take(cell_of(G, i + 1, j, k));
+    take(cell_of(G, i, j - 1, k));
+    take(cell_of(G, i, j + 1, k));
+    take(cell_of(G, i, j, k - 1));
+    take(cell_of(G, i, j, k + 1));
+    if (cnt == 0) {
+      for (int dk = -1; dk <= 1; ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di)
+            if (di || dj || dk) take(cell_of(G, i + di, j + dj, k + dk));
+    }
+    if (cnt == 0) {
+      latch_error(ctrl, M2C_ENONPHYS, c);
+      continue;
+    }
+    double P[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) P[v] = sum[v] / cnt;
+    double e, c2;
+    if (!eos_e_c2<double>(q, P[0], 1.0 / P[0], P[4], e, c2)) latch_error(ctrl, M2C_ENONPHYS, c);
+    G.W[c] = P[0];
+    G.W[N + c] = P[0] * P[1];
+    G.W[2 * N + c] = P[0] * P[2];
+    G.W[3 * N + c] = P[0] * P[3];
+    G.W[4 * N + c] = P[0] * e + 0.5 * P[0] * ((P[1] * P[1] + P[2] * P[2]) + P[3] * P[3]);
+    bool ok;
+    const double lam = wave_sum(G, q, G.W, N, c, ok);
+    lam_max = fmax(lam_max, lam);
+  }
+  block_max_to(lam_max, &ctrl->lam[(ctrl->step + 1) & 1], s_red);
+}
+
+// End of a step: advance t and the step counter, keep the counters of the
+// step for m2c_get_stats and reset the work lists for the next step.
+__global__ void k_end_step(const Grid* __restrict__ grids, int ngrid) {
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= ngrid) return;
+  const Grid& G = grids[gi];
+  Ctrl* c = G.ctrl;
+  const long long s = c->step;
+  const double dt = lam_to_dt(G, c->lam[s & 1]);
+  c->t = c->t + dt;
+  c->stat_faces = c->nface[0];
+  c->stat_cells = c->ncell[0];
+  c->stat_flips = c->nflip;
+  c->nface[0] = c->nface[1] = 0;
+  c->ncell[0] = c->ncell[1] = 0;
+  c->nflip = 0;
+  c->lam[s & 1] = 0ull;  // slot of step s + 2
+  c->step = s + 1;
+  c->stat_dt = lam_to_dt(G, c->lam[(s + 1) & 1]);
+}
+
+// Wave-speed maximum of the current state (first time step).
+__global__ void __launch_bounds__(256) k_lam_init(const Grid* __restrict__ grids) {
+  __shared__ double s_red[32];
+  const Grid& G = grids[blockIdx.y];
+  double lam_max = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x) {
+    const int m = G.phi[c] < 0.0 ? 1 : 0;
+    bool ok;
+    const double lam = wave_sum(G, G.eos[m], G.W, G.N, c, ok);
+    if (!ok) latch_error(G.ctrl, M2C_ENONPHYS, c);
+    lam_max = fmax(lam_max, lam);
+  }
+  block_max_to(lam_max, &G.ctrl->lam[G.ctrl->step & 1], s_red);
+}
+
+__global__ void k_prims_to_state(const Grid* __restrict__ grids, const double* __restrict__ prims) {
+  const Grid& G = grids[0];
+  const long long N = G.N;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int m = G.phi[c] < 0.0 ? 1 : 0;
+    const double rho = prims[c], u = prims[N + c], v = prims[2 * N + c], w = prims[3 * N + c], p = prims[4 * N + c];
+    double e, c2;
+    if (!eos_e_c2<double>(G.eos[m], rho, 1.0 / rho, p, e, c2)) latch_error(G.ctrl, M2C_ENONPHYS, c);
+    G.W[c] = rho;
+    G.W[N + c] = rho * u;
+    G.W[2 * N + c] = rho * v;
+    G.W[3 * N + c] = rho * w;
+    G.W[4 * N + c] = rho * e + 0.5 * rho * ((u * u + v * v) + w * w);
+  }
+}
+
+__global__ void k_riemann_batch(int n, EosDev qL, const double* __restrict__ L, EosDev qR,
+                                const double* __restrict__ Rr, double* __restrict__ out, int* __restrict__ iters,
+                                int* __restrict__ status) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    RiemannOut o;
+    int its = 0;
+    const int st = riemann_solve(qL, L[i], L[n + i], L[2 * n + i], qR, Rr[i], Rr[n + i], Rr[2 * n + i], o, its);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    out[i] = st ? nan : o.p;
+    out[n + i] = st ? nan : o.u;
+    out[2 * n + i] = st ? nan : o.rhoL;
+    out[3 * n + i] = st ? nan : o.rhoR;
+    if (iters) iters[i] = its;
+    if (status) status[i] = st;
+  }
+}
+
+// Post-shock state from the right-facing wave curve of the Riemann solver.
+__global__ void k_shock_state(EosDev q, double rho, double u, double p, double p1, double* out, int* status) {
+  Side K;
+  if (!make_side(q, rho, u, p, K) || !(p1 > p)) {
+    *status = M2C_EINVAL;
+    return;
+  }
+  double f, df, rs;
+  const int st = wave(q, K, p1, f, df, rs);
+  *status = st;
+  if (st) return;
+  out[0] = rs;
+  out[1] = K.u + f;
+  out[2] = (rs * out[1] - K.rho * K.u) / (rs - K.rho);
+}
+
+}  // namespace m2c
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+using namespace m2c;
+
+struct m2c_ctx {
+  Grid host;            // host copy of the device descriptor
+  Grid* dev_grid;       // in the workspace
+  long long* dev_tiles; // tile_begin[2] in the workspace
+  cudaStream_t stream;
+  int ty;               // tile rows of the bulk kernel
+  int reinit_every, reinit_iters;
+  long long host_step;
+  bool has_state, eos_set[2], dirty, lam_valid;
+  bool profiling;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pairs around bulk stage launches
+  size_t ev_used;
+  std::string err;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t grid, tiles, ctrl, W1, phi1, phiC, id, slot, faces, cells, flips, total;
+  int face_cap, cell_cap, flip_cap;
+};
+
+Layout layout_for(long long N) {
+  Layout L{};
+  L.face_cap = (int)std::min<long long>(std::max<long long>(4096, N / 4), 1ll << 30);
+  L.cell_cap = (int)std::min<long long>(std::max<long long>(2048, N / 8), 1ll << 30);
+  L.flip_cap = (int)std::min<long long>(std::max<long long>(1024, N / 16), 1ll << 30);
+  size_t o = 0;
+  L.grid = o; o = align_up(o + sizeof(Grid));
+  L.tiles = o; o = align_up(o + 2 * sizeof(long long));
+  L.ctrl = o; o = align_up(o + sizeof(Ctrl));
+  L.W1 = o; o = align_up(o + sizeof(double) * 5 * N);
+  L.phi1 = o; o = align_up(o + sizeof(double) * N);
+  L.phiC = o; o = align_up(o + sizeof(double) * N);
+  L.id = o; o = align_up(o + N);
+  L.slot = o; o = align_up(o + sizeof(int) * N);
+  L.faces = o; o = align_up(o + sizeof(IfFace) * (size_t)L.face_cap);
+  L.cells = o; o = align_up(o + sizeof(IfCell) * (size_t)L.cell_cap);
+  L.flips = o; o = align_up(o + sizeof(long long) * (size_t)L.flip_cap);
+  L.total = o;
+  return L;
+}
+
+m2c_status set_err(m2c_ctx* c, m2c_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+m2c_status cuda_check(m2c_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return M2C_OK;
+  return set_err(c, M2C_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename R, int TY>
+void stage_smem_setup() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_stage<R, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<R, TY>::bytes);
+  done = true;
+}
+
+template <typename R, int TY>
+cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
+                           cudaStream_t s) {
+  stage_smem_setup<R, TY>();
+  k_stage<R, TY><<<(unsigned)ntiles, 32 * TY, StageSmem<R, TY>::bytes, s>>>(grids, tiles, ngrid, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stage(int prec, int ty, const Grid* grids, const long long* tiles, int ngrid, long long ntiles,
+                         int mode, cudaStream_t s) {
+  if (prec == M2C_FP64) {
+    if (ty == 4) return launch_stage_t<double, 4>(grids, tiles, ngrid, ntiles, mode, s);
+    return launch_stage_t<double, 8>(grids, tiles, ngrid, ntiles, mode, s);
+  }
+  if (ty == 4) return launch_stage_t<float, 4>(grids, tiles, ngrid, ntiles, mode, s);
+  return launch_stage_t<float, 8>(grids, tiles, ngrid, ntiles, mode, s);
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+void set_tiling(Grid& g, int ty, int tz) {
+  g.tiles_x = (g.nx + 31) / 32;
+  g.tiles_y = (g.ny + ty - 1) / ty;
+  g.tz = std::max(1, std::min(tz, g.nz));
+  g.tiles_z = (g.nz + g.tz - 1) / g.tz;
+}
+
+long long ntiles_of(const Grid& g) { return (long long)g.tiles_x * g.tiles_y * g.tiles_z; }
+
+m2c_status push_grid(m2c_ctx* c) {
+  long long tiles[2] = {0, ntiles_of(c->host)};
+  cudaError_t e = cudaMemcpyAsync(c->dev_grid, &c->host, sizeof(Grid), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->dev_tiles, tiles, sizeof(tiles), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  c->dirty = false;
+  return cuda_check(c, e, "descriptor upload");
+}
+
+// Default tile z-chunk: long enough to amortise the z warm-up, short enough
+// to give every SM several blocks.
+int default_tz(const Grid& g, int ty) {
+  const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + ty - 1) / ty);
+  const long long want = 4ll * sm_count();
+  int tz = g.nz;
+  while (tz > 8 && cols * ((g.nz + tz - 1) / tz) < want) tz = (tz + 1) / 2;
+  return tz;
+}
+
+// Enqueues one time step for ngrid grids described at dev_grids.
+struct StageEvents {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev;
+  size_t* used;
+};
+
+cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s) {
+  if (!pe) return cudaSuccess;
+  if (start) {
+    if (*pe->used == pe->ev->size()) {
+      cudaEvent_t a, b;
+      cudaError_t e = cudaEventCreate(&a);
+      if (e == cudaSuccess) e = cudaEventCreate(&b);
+      if (e != cudaSuccess) return e;
+      pe->ev->push_back({a, b});
+    }
+    return cudaEventRecord((*pe->ev)[*pe->used].first, s);
+  }
+  cudaError_t e = cudaEventRecord((*pe->ev)[*pe->used].second, s);
+  ++*pe->used;
+  return e;
+}
+
+cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int ngrid, long long ntiles, int prec,
+                         int ty, bool reinit, int reinit_iters, const std::vector<Grid>& hosts, cudaStream_t s,
+                         StageEvents* pe = nullptr) {
+  cudaError_t e;
+  const dim3 lg((unsigned)(2 * sm_count()), (unsigned)ngrid);
+  for (int stage = 0; stage < 2; ++stage) {
+    const int mode = stage == 0 ? kStage1 : kStage2;
+    if ((e = record_pair(pe, true, s)) != cudaSuccess) return e;
+    e = launch_stage(prec, ty, dev_grids, dev_tiles, ngrid, ntiles, mode, s);
+    if (e != cudaSuccess) return e;
+    if ((e = record_pair(pe, false, s)) != cudaSuccess) return e;
+    k_fiver<<<lg, 128, 0, s>>>(dev_grids, mode);
+    k_finish<<<lg, 128, 0, s>>>(dev_grids, mode);
+  }
+  if (reinit && reinit_iters > 0) {
+    // phi0 = state phi; iterate through phi1 and phiC and end in phi. A single
+    // iteration goes through phi1 and a copy back.
+    // the per-grid buffers differ, so each iteration is launched per grid
+    for (int gi = 0; gi < ngrid; ++gi) {
+      const Grid& g = hosts[gi];
+      const Grid* dg = dev_grids + gi;
+      const dim3 r1((unsigned)std::min<long long>((g.N + 255) / 256, 8ll * sm_count()), 1);
+      for (int it = 1; it <= reinit_iters; ++it) {
+        const double* src = it == 1 ? g.phi : ((it % 2 == 0) ? g.phi1 : g.phiC);
+        double* dst = (it % 2 == 1) ? g.phi1 : g.phiC;
+        if (it == reinit_iters && it > 1) dst = g.phi;
+        k_reinit<<<r1, 256, 0, s>>>(dg, src, dst, it == 1);
+      }
+      if (reinit_iters == 1) k_copy<<<r1, 256, 0, s>>>(dg, g.phi1, g.phi);
+    }
+  }
+  k_phase_fix<<<lg, 128, 0, s>>>(dev_grids);
+  k_end_step<<<(ngrid + 63) / 64, 64, 0, s>>>(dev_grids, ngrid);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Wave-speed maximum of the current state for the next step's time step.
+static cudaError_t ensure_lam(m2c_ctx* c) {
+  cudaError_t e = cudaMemsetAsync(&c->host.ctrl->lam[0], 0, 2 * sizeof(unsigned long long), c->stream);
+  if (e != cudaSuccess) return e;
+  const dim3 g((unsigned)std::min<long long>((c->host.N + 255) / 256, 8ll * sm_count()), 1);
+  k_lam_init<<<g, 256, 0, c->stream>>>(c->dev_grid);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) c->lam_valid = true;
+  return e;
+}
+
+namespace {
+
+double lam_to_dt_host(const Grid& g, unsigned long long bits) {
+  double lam;
+  std::memcpy(&lam, &bits, sizeof(lam));
+  return lam > 0.0 ? g.cfl * g.h / lam : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* m2c_status_string(int s) {
+  switch (s) {
+    case M2C_OK: return "ok";
+    case M2C_EINVAL: return "invalid argument";
+    case M2C_ENOMEM: return "workspace too small";
+    case M2C_ECUDA: return "CUDA error";
+    case M2C_ENOCONV: return "Riemann solver did not converge";
+    case M2C_ENONPHYS: return "non-physical state";
+    case M2C_EVACUUM: return "vacuum in the Riemann problem";
+    case M2C_ETIMEOUT: return "device wait timed out";
+    case M2C_EOVERFLOW: return "interface work list overflow";
+    default: return "unknown status";
+  }
+}
+
+size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision) {
+  (void)precision;
+  if (nx < 1 || ny < 1 || nz < 1) return 0;
+  return layout_for((long long)nx * ny * nz).total;
+}
+
+m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[3], double h, const int bc[6],
+                         int precision, void* workspace, size_t ws_bytes, void* stream) {
+  (void)lo;
+  if (!out) return M2C_EINVAL;
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !workspace) return M2C_EINVAL;
+  if (precision != M2C_FP64 && precision != M2C_MIXED) return M2C_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    for (int s = 0; s < 2; ++s)
+      if (bc[2 * a + s] != M2C_BC_TRANSMISSIVE && bc[2 * a + s] != M2C_BC_PERIODIC) return M2C_EINVAL;
+    if ((bc[2 * a] == M2C_BC_PERIODIC) != (bc[2 * a + 1] == M2C_BC_PERIODIC)) return M2C_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return M2C_EINVAL;
+  const long long N = (long long)nx * ny * nz;
+  const Layout L = layout_for(N);
+  if (ws_bytes < L.total) return M2C_ENOMEM;
+  m2c_ctx* c = new (std::nothrow) m2c_ctx();
+  if (!c) return M2C_ENOMEM;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  Grid& g = c->host;
+  std::memset(&g, 0, sizeof(g));
+  g.nx = nx; g.ny = ny; g.nz = nz; g.N = N;
+  for (int s = 0; s < 6; ++s) g.bc[s] = bc[s];
+  g.active[0] = nx > 1; g.active[1] = ny > 1; g.active[2] = nz > 1;
+  g.prec = precision;
+  g.h = h; g.inv_h = 1.0 / h; g.cfl = 0.5;
+  g.W1 = reinterpret_cast<double*>(ws + L.W1);
+  g.phi1 = reinterpret_cast<double*>(ws + L.phi1);
+  g.phiC = reinterpret_cast<double*>(ws + L.phiC);
+  g.id = ws + L.id;
+  g.cell_slot = reinterpret_cast<int*>(ws + L.slot);
+  g.faces = reinterpret_cast<IfFace*>(ws + L.faces);
+  g.cells = reinterpret_cast<IfCell*>(ws + L.cells);
+  g.flips = reinterpret_cast<long long*>(ws + L.flips);
+  g.face_cap = L.face_cap; g.cell_cap = L.cell_cap; g.flip_cap = L.flip_cap;
+  g.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  c->dev_grid = reinterpret_cast<Grid*>(ws + L.grid);
+  c->dev_tiles = reinterpret_cast<long long*>(ws + L.tiles);
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->ty = 8;
+  if (const char* e = std::getenv("M2C_TILE_TY")) c->ty = std::atoi(e) == 4 ? 4 : 8;
+  set_tiling(g, c->ty, default_tz(g, c->ty));
+  if (const char* e = std::getenv("M2C_TILE_TZ")) set_tiling(g, c->ty, std::max(1, std::atoi(e)));
+  c->reinit_every = 10;
+  c->reinit_iters = 5;
+  c->host_step = 0;
+  c->has_state = false;
+  c->eos_set[0] = c->eos_set[1] = false;
+  c->lam_valid = false;
+  c->profiling = false;
+  c->ev_used = 0;
+  cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(Ctrl), c->stream);
+  if (e != cudaSuccess) {
+    delete c;
+    return M2C_ECUDA;
+  }
+  m2c_status st = push_grid(c);
+  if (st != M2C_OK) {
+    delete c;
+    return st;
+  }
+  *out = c;
+  return M2C_OK;
+}
+
+m2c_status m2c_set_eos(m2c_ctx* c, int material, int type, const double* params, int nparams) {
+  if (!c) return M2C_EINVAL;
+  if (material < 0 || material > 1 || !params) return set_err(c, M2C_EINVAL, "bad material or params");
+  double prm[6] = {0, 0, 0, 0, 0, -INFINITY};
+  if (type == M2C_EOS_SG) {
+    if (nparams < 2 || !(params[0] > 1.0)) return set_err(c, M2C_EINVAL, "SG needs gamma > 1 and p_c");
+    prm[0] = params[0];
+    prm[1] = params[1];
+  } else if (type == M2C_EOS_MG) {
+    if (nparams < 4 || nparams > 6) return set_err(c, M2C_EINVAL, "MG needs 4 to 6 params");
+    for (int i = 0; i < nparams; ++i) prm[i] = params[i];
+    if (!(prm[0] > 0.0) || !(prm[1] > 0.0) || !(prm[2] > 1.0) || !(prm[3] > 0.0))
+      return set_err(c, M2C_EINVAL, "MG needs rho0, c0 > 0, s > 1, Gamma0 > 0");
+  } else {
+    return set_err(c, M2C_EINVAL, "unknown EOS type");
+  }
+  c->host.eos[material] = make_eos_dev(type, prm);
+  c->eos_set[material] = true;
+  return push_grid(c);
+}
+
+m2c_status m2c_set_scheme(m2c_ctx* c, double cfl, int reinit_every, int reinit_iters) {
+  if (!c) return M2C_EINVAL;
+  if (!(cfl > 0.0) || reinit_every < 0 || reinit_iters < 0) return set_err(c, M2C_EINVAL, "bad scheme parameters");
+  c->host.cfl = cfl;
+  c->reinit_every = reinit_every;
+  c->reinit_iters = reinit_iters;
+  return push_grid(c);
+}
+
+m2c_status m2c_set_state(m2c_ctx* c, double* W, double* phi, double t, long step) {
+  if (!c) return M2C_EINVAL;
+  if (!W || !phi) return set_err(c, M2C_EINVAL, "null state");
+  if (!c->eos_set[0] || !c->eos_set[1]) return set_err(c, M2C_EINVAL, "set both EOS first");
+  c->host.W = W;
+  c->host.phi = phi;
+  m2c_status st = push_grid(c);
+  if (st) return st;
+  Ctrl init;
+  std::memset(&init, 0, sizeof(init));
+  init.t = t;
+  init.step = step;
+  init.err_cell = -1;
+  cudaError_t e = cudaMemcpyAsync(c->host.ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "set_state");
+  c->host_step = step;
+  c->has_state = true;
+  c->lam_valid = false;  // the first time step is reduced at the next m2c_step
+  e = cudaStreamSynchronize(c->stream);
+  return cuda_check(c, e, "set_state");
+}
+
+m2c_status m2c_prims_to_state(m2c_ctx* c, const double* prims) {
+  if (!c || !prims) return M2C_EINVAL;
+  if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first (W and phi buffers)");
+  const dim3 g((unsigned)std::min<long long>((c->host.N + 255) / 256, 8ll * sm_count()), 1);
+  k_prims_to_state<<<g, 256, 0, c->stream>>>(c->dev_grid, prims);
+  c->lam_valid = false;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_check(c, e, "prims_to_state");
+}
+
+m2c_status m2c_upload_state(m2c_ctx* c, const double* W_host, const double* phi_host) {
+  if (!c || !W_host || !phi_host) return M2C_EINVAL;
+  if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first");
+  const size_t N = (size_t)c->host.N;
+  cudaError_t e = cudaMemcpyAsync(c->host.W, W_host, 5 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->host.phi, phi_host, N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  c->lam_valid = false;
+  return cuda_check(c, e, "upload_state");
+}
+
+m2c_status m2c_download_state(m2c_ctx* c, double* W_host, double* phi_host) {
+  if (!c || !W_host || !phi_host) return M2C_EINVAL;
+  if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first");
+  const size_t N = (size_t)c->host.N;
+  cudaError_t e = cudaMemcpyAsync(W_host, c->host.W, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(phi_host, c->host.phi, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_check(c, e, "download_state");
+}
+
+m2c_status m2c_step(m2c_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return M2C_EINVAL;
+  if (!c->has_state) return set_err(c, M2C_EINVAL, "no state");
+  if (!c->lam_valid && nsteps > 0) {
+    cudaError_t e = ensure_lam(c);
+    if (e != cudaSuccess) return cuda_check(c, e, "first time step");
+  }
+  std::vector<Grid> hosts(1, c->host);
+  for (int n = 0; n < nsteps; ++n) {
+    const bool re = c->reinit_every > 0 && (c->host_step + 1) % c->reinit_every == 0;
+    StageEvents pe{&c->ev, &c->ev_used};
+    cudaError_t e = enqueue_step(c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), c->host.prec, c->ty, re,
+                                 c->reinit_iters, hosts, c->stream, c->profiling ? &pe : nullptr);
+    if (e != cudaSuccess) return cuda_check(c, e, "step launch");
+    ++c->host_step;
+  }
+  return M2C_OK;
+}
+
+size_t m2c_batch_bytes(int k) {
+  if (k < 1) return 0;
+  return align_up(sizeof(Grid) * (size_t)k) + align_up(sizeof(long long) * (size_t)(k + 1));
+}
+
+m2c_status m2c_step_batch(m2c_ctx** v, int k, int nsteps, void* batch_ws, size_t bytes) {
+  if (!v || k < 1 || nsteps < 0 || !batch_ws) return M2C_EINVAL;
+  if (bytes < m2c_batch_bytes(k) || reinterpret_cast<uintptr_t>(batch_ws) % kAlign) return M2C_EINVAL;
+  m2c_ctx* c0 = v[0];
+  if (!c0) return M2C_EINVAL;
+  for (int i = 0; i < k; ++i) {
+    if (!v[i] || !v[i]->has_state) return set_err(c0, M2C_EINVAL, "context without state");
+    if (v[i]->host.prec != c0->host.prec) return set_err(c0, M2C_EINVAL, "mixed precisions in one batch");
+  }
+  for (int i = 0; i < k; ++i) {
+    if (!v[i]->lam_valid && nsteps > 0) {
+      cudaError_t e0 = ensure_lam(v[i]);
+      if (e0 != cudaSuccess) return cuda_check(c0, e0, "first time step");
+      cudaStreamSynchronize(v[i]->stream);
+    }
+  }
+  Grid* dev = static_cast<Grid*>(batch_ws);
+  long long* dtiles = reinterpret_cast<long long*>(static_cast<unsigned char*>(batch_ws) + align_up(sizeof(Grid) * (size_t)k));
+  std::vector<Grid> hosts(k);
+  std::vector<long long> tiles(k + 1, 0);
+  for (int i = 0; i < k; ++i) {
+    hosts[i] = v[i]->host;
+    set_tiling(hosts[i], c0->ty, default_tz(hosts[i], c0->ty));
+    tiles[i + 1] = tiles[i] + ntiles_of(hosts[i]);
+  }
+  cudaError_t e = cudaMemcpyAsync(dev, hosts.data(), sizeof(Grid) * k, cudaMemcpyHostToDevice, c0->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dtiles, tiles.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, c0->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c0->stream);
+  if (e != cudaSuccess) return cuda_check(c0, e, "batch descriptors");
+  for (int n = 0; n < nsteps; ++n) {
+    const bool re = c0->reinit_every > 0 && (c0->host_step + 1) % c0->reinit_every == 0;
+    StageEvents pe{&c0->ev, &c0->ev_used};
+    e = enqueue_step(dev, dtiles, k, tiles[k], c0->host.prec, c0->ty, re, c0->reinit_iters, hosts, c0->stream,
+                     c0->profiling ? &pe : nullptr);
+    if (e != cudaSuccess) return cuda_check(c0, e, "batch step launch");
+    for (int i = 0; i < k; ++i) ++v[i]->host_step;
+  }
+  return M2C_OK;
+}
+
+m2c_status m2c_residual(m2c_ctx* c, double* R, double* L) {
+  if (!c || !R || !L) return M2C_EINVAL;
+  if (!c->has_state) return set_err(c, M2C_EINVAL, "no state");
+  c->host.resR = R;
+  c->host.resL = L;
+  m2c_status st = push_grid(c);
+  if (st) return st;
+  cudaError_t e = launch_stage(c->host.prec, c->ty, c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), kResidual,
+                               c->stream);
+  if (e == cudaSuccess) {
+    const dim3 lg((unsigned)(2 * sm_count()), 1);
+    k_fiver<<<lg, 128, 0, c->stream>>>(c->dev_grid, kResidual);
+    k_finish<<<lg, 128, 0, c->stream>>>(c->dev_grid, kResidual);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->host.ctrl->nface[0], 0, 2 * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->host.ctrl->ncell[0], 0, 2 * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_check(c, e, "residual");
+}
+
+m2c_status m2c_sync(m2c_ctx* c, double* t, long* steps, long* err_cell) {
+  if (!c) return M2C_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "sync");
+  Ctrl h;
+  e = cudaMemcpy(&h, c->host.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_check(c, e, "sync");
+  if (t) *t = h.t;
+  if (steps) *steps = (long)h.step;
+  if (err_cell) *err_cell = h.err ? (long)h.err_cell : -1;
+  if (h.err) {
+    const int zero[1] = {0};
+    cudaMemcpy(&c->host.ctrl->err, zero, sizeof(int), cudaMemcpyHostToDevice);
+    return set_err(c, (m2c_status)h.err, std::string("device: ") + m2c_status_string(h.err) + " at cell " +
+                                             std::to_string(h.err_cell));
+  }
+  return M2C_OK;
+}
+
+m2c_status m2c_get_stats(m2c_ctx* c, m2c_stats* out) {
+  if (!c || !out) return M2C_EINVAL;
+  Ctrl h;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, c->host.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_check(c, e, "get_stats");
+  out->interface_faces = (long)h.stat_faces;
+  out->interface_cells = (long)h.stat_cells;
+  out->flipped_cells = (long)h.stat_flips;
+  out->dt = h.step == 0 ? lam_to_dt_host(c->host, h.lam[0]) : h.stat_dt;
+  return M2C_OK;
+}
+
+m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
+                             const double* R, double* out, int* iters, int* status, int on_device, void* stream) {
+  if (n < 0 || !eosL || !eosR || !L || !R || !out) return M2C_EINVAL;
+  if (n == 0) return M2C_OK;
+  double pl[6] = {0, 0, 0, 0, 0, -INFINITY}, pr[6] = {0, 0, 0, 0, 0, -INFINITY};
+  for (int i = 0; i < 6; ++i) {
+    pl[i] = eosL->params[i];
+    pr[i] = eosR->params[i];
+  }
+  const EosDev qL = make_eos_dev(eosL->type, pl), qR = make_eos_dev(eosR->type, pr);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int threads = 128;
+  const int blocks = (int)std::min<long long>((n + threads - 1) / threads, 4ll * sm_count());
+  if (on_device) {
+    k_riemann_batch<<<blocks, threads, 0, s>>>(n, qL, L, qR, R, out, iters, status);
+    return cudaGetLastError() == cudaSuccess ? M2C_OK : M2C_ECUDA;
+  }
+  double *dL = nullptr, *dR = nullptr, *dO = nullptr;
+  int *dI = nullptr, *dS = nullptr;
+  m2c_status st = M2C_OK;
+  if (cudaMalloc(&dL, sizeof(double) * 3 * n) != cudaSuccess || cudaMalloc(&dR, sizeof(double) * 3 * n) != cudaSuccess ||
+      cudaMalloc(&dO, sizeof(double) * 4 * n) != cudaSuccess || cudaMalloc(&dI, sizeof(int) * n) != cudaSuccess ||
+      cudaMalloc(&dS, sizeof(int) * n) != cudaSuccess) {
+    st = M2C_ECUDA;
+  } else {
+    cudaMemcpyAsync(dL, L, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dR, R, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
+    k_riemann_batch<<<blocks, threads, 0, s>>>(n, qL, dL, qR, dR, dO, dI, dS);
+    std::vector<int> hs(n);
+    cudaMemcpyAsync(out, dO, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hs.data(), dS, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+    if (iters) cudaMemcpyAsync(iters, dI, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = M2C_ECUDA;
+    if (status) std::memcpy(status, hs.data(), sizeof(int) * n);
+    if (st == M2C_OK)
+      for (int i = 0; i < n; ++i)
+        if (hs[i]) { st = (m2c_status)hs[i]; break; }
+  }
+  cudaFree(dL); cudaFree(dR); cudaFree(dO); cudaFree(dI); cudaFree(dS);
+  return st;
+}
+
+m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]) {
+  if (!eos || !w || !out) return M2C_EINVAL;
+  double prm[6];
+  for (int i = 0; i < 6; ++i) prm[i] = eos->params[i];
+  const EosDev q = make_eos_dev(eos->type, prm);
+  double* d = nullptr;
+  if (cudaMalloc(&d, 4 * sizeof(double)) != cudaSuccess) return M2C_ECUDA;
+  int* ds = reinterpret_cast<int*>(d + 3);
+  k_shock_state<<<1, 1>>>(q, w[0], w[1], w[2], p1, d, ds);
+  double h[4];
+  cudaError_t e = cudaMemcpy(h, d, 4 * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return M2C_ECUDA;
+  int st;
+  std::memcpy(&st, &h[3], sizeof(int));
+  if (st) return (m2c_status)st;
+  out[0] = h[0]; out[1] = h[1]; out[2] = h[2];
+  return M2C_OK;
+}
+
+m2c_status m2c_profile(m2c_ctx* c, int enable) {
+  if (!c) return M2C_EINVAL;
+  c->profiling = enable != 0;
+  c->ev_used = 0;
+  return M2C_OK;
+}
+
+m2c_status m2c_profile_read(m2c_ctx* c, double* total_ms, long* launches) {
+  if (!c || !total_ms || !launches) return M2C_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "profile_read");
+  double sum = 0.0;
+  for (size_t i = 0; i < c->ev_used; ++i) {
+    float ms = 0.0f;
+    e = cudaEventElapsedTime(&ms, c->ev[i].first, c->ev[i].second);
+    if (e != cudaSuccess) return cuda_check(c, e, "profile_read");
+    sum += ms;
+  }
+  *total_ms = sum;
+  *launches = (long)c->ev_used;
+  c->ev_used = 0;
+  return M2C_OK;
+}
+
+void m2c_destroy(m2c_ctx* c) {
+  if (!c) return;
+  for (auto& p : c->ev) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  delete c;
+}
+
+const char* m2c_last_error(const m2c_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

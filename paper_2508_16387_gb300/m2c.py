@@ -1,0 +1,292 @@
+"""Thin ctypes binding of libm2cgpu.so (include/m2c.h).
+
+The functions named like the C entry points marshal arguments only; every
+step of the solver runs in the library's CUDA kernels. ``Grid`` is a small
+convenience owner of the torch device tensors a context borrows (state,
+workspace). Loading fails with an error if the library is missing: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libm2cgpu.so")
+
+M2C_OK = 0
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENONPHYS", 6: "EVACUUM",
+          7: "ETIMEOUT", 8: "EOVERFLOW"}
+EOS_SG, EOS_MG = 0, 1
+FP64, MIXED = 0, 1
+BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
+
+
+class M2CError(RuntimeError):
+    def __init__(self, code: int, where: str, text: str = ""):
+        super().__init__(f"{where}: {STATUS.get(code, code)} {text}".strip())
+        self.code = code
+
+
+class EosDesc(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("params", ctypes.c_double * 6)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("interface_faces", ctypes.c_long), ("interface_cells", ctypes.c_long),
+                ("flipped_cells", ctypes.c_long), ("dt", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        p, i, d, z, L_ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_long
+        L.m2c_workspace_bytes.restype = z
+        L.m2c_workspace_bytes.argtypes = [i, i, i, i]
+        L.m2c_batch_bytes.restype = z
+        L.m2c_batch_bytes.argtypes = [i]
+        L.m2c_init_grid.argtypes = [ctypes.POINTER(p), i, i, i, p, d, p, i, p, z, p]
+        L.m2c_set_eos.argtypes = [p, i, i, p, i]
+        L.m2c_set_scheme.argtypes = [p, d, i, i]
+        L.m2c_set_state.argtypes = [p, p, p, d, L_]
+        L.m2c_prims_to_state.argtypes = [p, p]
+        L.m2c_upload_state.argtypes = [p, p, p]
+        L.m2c_download_state.argtypes = [p, p, p]
+        L.m2c_step.argtypes = [p, i]
+        L.m2c_step_batch.argtypes = [p, i, i, p, z]
+        L.m2c_residual.argtypes = [p, p, p]
+        L.m2c_sync.argtypes = [p, p, p, p]
+        L.m2c_get_stats.argtypes = [p, ctypes.POINTER(Stats)]
+        L.m2c_solve_riemann.argtypes = [i, ctypes.POINTER(EosDesc), p, ctypes.POINTER(EosDesc), p, p, p, p, i, p]
+        L.m2c_shock_state.argtypes = [ctypes.POINTER(EosDesc), p, d, p]
+        L.m2c_profile.argtypes = [p, i]
+        L.m2c_profile_read.argtypes = [p, ctypes.POINTER(d), ctypes.POINTER(L_)]
+        L.m2c_destroy.argtypes = [p]
+        L.m2c_destroy.restype = None
+        L.m2c_last_error.argtypes = [p]
+        L.m2c_last_error.restype = ctypes.c_char_p
+        L.m2c_status_string.argtypes = [i]
+        L.m2c_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str, ctx=None):
+    if code != M2C_OK:
+        text = ""
+        if ctx is not None:
+            text = lib().m2c_last_error(ctx).decode()
+        raise M2CError(code, where, text)
+
+
+def eos_desc(eos) -> EosDesc:
+    """eos = (type, params) as in workloads.py."""
+    t, prm = eos
+    e = EosDesc()
+    e.type = t
+    vals = list(prm) + [0.0] * (6 - len(prm))
+    if t == EOS_MG and len(prm) < 6:
+        vals[5] = -math.inf
+    for k in range(6):
+        e.params[k] = vals[k]
+    return e
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- C entry points
+
+def m2c_workspace_bytes(nx, ny, nz, precision=FP64) -> int:
+    return lib().m2c_workspace_bytes(nx, ny, nz, precision)
+
+
+def m2c_batch_bytes(k) -> int:
+    return lib().m2c_batch_bytes(k)
+
+
+def m2c_solve_riemann(eosL, L, eosR, R, stream=None):
+    """Batch Riemann solve on device tensors L, R of shape (3, n) float64 (rho, u, p).
+    Returns (out (4, n): p*, u*, rho*_L, rho*_R; iters (n,); status (n,))."""
+    import torch
+    n = L.shape[1]
+    out = torch.empty((4, n), dtype=torch.float64, device=L.device)
+    iters = torch.zeros(n, dtype=torch.int32, device=L.device)
+    status = torch.zeros(n, dtype=torch.int32, device=L.device)
+    eL, eR = eos_desc(eosL), eos_desc(eosR)
+    code = lib().m2c_solve_riemann(n, ctypes.byref(eL), _ptr(L.contiguous()), ctypes.byref(eR),
+                                   _ptr(R.contiguous()), _ptr(out), _ptr(iters), _ptr(status), 1,
+                                   _stream_handle(stream))
+    _check(code, "m2c_solve_riemann")
+    return out, iters, status
+
+
+def m2c_solve_riemann_host(eosL, L, eosR, R):
+    """Host-array variant: L, R numpy (3, n); returns (code, out (4, n), iters, status)."""
+    import numpy as np
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    n = L.shape[1]
+    out = np.zeros((4, n))
+    iters = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    eL, eR = eos_desc(eosL), eos_desc(eosR)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    code = lib().m2c_solve_riemann(n, ctypes.byref(eL), vp(L), ctypes.byref(eR), vp(R), vp(out), vp(iters),
+                                   vp(status), 0, None)
+    return code, out, iters, status
+
+
+def m2c_shock_state(eos, w, p1):
+    import numpy as np
+    e = eos_desc(eos)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros(3)
+    _check(lib().m2c_shock_state(ctypes.byref(e), w.ctypes.data_as(ctypes.c_void_p), p1,
+                                 out.ctypes.data_as(ctypes.c_void_p)), "m2c_shock_state")
+    return tuple(out)
+
+
+@dataclass
+class StepStats:
+    interface_faces: int
+    interface_cells: int
+    flipped_cells: int
+    dt: float
+
+
+class Grid:
+    """A context with its borrowed device state and workspace (torch tensors)."""
+
+    def __init__(self, n, h, bc, eos, precision=FP64, cfl=0.5, reinit_every=10, reinit_iters=5,
+                 device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.n = tuple(n)
+        nx, ny, nz = self.n
+        self.N = nx * ny * nz
+        self.h = h
+        self.precision = precision
+        self.device = torch.device(device)
+        self.stream = stream
+        wsb = m2c_workspace_bytes(nx, ny, nz, precision)
+        self.workspace = torch.empty(wsb + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws_ptr = ctypes.c_void_p(self.workspace.data_ptr() + off)
+        self.W = torch.zeros((5, nz, ny, nx), dtype=torch.float64, device=self.device)
+        self.phi = torch.zeros((nz, ny, nx), dtype=torch.float64, device=self.device)
+        bcs = (ctypes.c_int * 6)(*bc)
+        lo = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+        ctx = ctypes.c_void_p()
+        code = lib().m2c_init_grid(ctypes.byref(ctx), nx, ny, nz, lo, h, bcs, precision, self._ws_ptr, wsb,
+                                   _stream_handle(stream))
+        _check(code, "m2c_init_grid")
+        self.ctx = ctx
+        for m in (0, 1):
+            t, prm = eos[m]
+            arr = (ctypes.c_double * 6)(*(list(prm) + [0.0] * (6 - len(prm))))
+            _check(lib().m2c_set_eos(ctx, m, t, arr, len(prm)), "m2c_set_eos", ctx)
+        _check(lib().m2c_set_scheme(ctx, cfl, reinit_every, reinit_iters), "m2c_set_scheme", ctx)
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and _lib is not None:
+            _lib.m2c_destroy(ctx)
+            self.ctx = None
+
+    # -- state
+    def set_state(self, W=None, phi=None, t=0.0, step=0):
+        torch = self.torch
+        if W is not None:
+            self.W.copy_(torch.as_tensor(W, dtype=torch.float64))
+        if phi is not None:
+            self.phi.copy_(torch.as_tensor(phi, dtype=torch.float64))
+        _check(lib().m2c_set_state(self.ctx, _ptr(self.W), _ptr(self.phi), t, step), "m2c_set_state", self.ctx)
+
+    def set_prims(self, prims, phi, t=0.0, step=0):
+        """State from primitive fields (5, nz, ny, nx) and phi, converted on the device."""
+        torch = self.torch
+        self.phi.copy_(torch.as_tensor(phi, dtype=torch.float64))
+        _check(lib().m2c_set_state(self.ctx, _ptr(self.W), _ptr(self.phi), t, step), "m2c_set_state", self.ctx)
+        P = torch.as_tensor(prims, dtype=torch.float64).to(self.device).contiguous()
+        _check(lib().m2c_prims_to_state(self.ctx, _ptr(P)), "m2c_prims_to_state", self.ctx)
+
+    def upload(self, W_host, phi_host):
+        _check(lib().m2c_upload_state(self.ctx, _ptr(W_host), _ptr(phi_host)), "m2c_upload_state", self.ctx)
+
+    def download(self, W_host, phi_host):
+        _check(lib().m2c_download_state(self.ctx, _ptr(W_host), _ptr(phi_host)), "m2c_download_state", self.ctx)
+
+    # -- stepping
+    def step(self, nsteps=1):
+        _check(lib().m2c_step(self.ctx, nsteps), "m2c_step", self.ctx)
+
+    def sync(self):
+        t = ctypes.c_double()
+        s = ctypes.c_long()
+        e = ctypes.c_long()
+        code = lib().m2c_sync(self.ctx, ctypes.byref(t), ctypes.byref(s), ctypes.byref(e))
+        if code != M2C_OK:
+            raise M2CError(code, "m2c_sync", lib().m2c_last_error(self.ctx).decode())
+        return t.value, s.value
+
+    def sync_status(self):
+        t = ctypes.c_double()
+        s = ctypes.c_long()
+        e = ctypes.c_long()
+        code = lib().m2c_sync(self.ctx, ctypes.byref(t), ctypes.byref(s), ctypes.byref(e))
+        return code, e.value
+
+    def stats(self) -> StepStats:
+        st = Stats()
+        _check(lib().m2c_get_stats(self.ctx, ctypes.byref(st)), "m2c_get_stats", self.ctx)
+        return StepStats(st.interface_faces, st.interface_cells, st.flipped_cells, st.dt)
+
+    def profile(self, enable=True):
+        _check(lib().m2c_profile(self.ctx, 1 if enable else 0), "m2c_profile", self.ctx)
+
+    def profile_read(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_long()
+        _check(lib().m2c_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)), "m2c_profile_read", self.ctx)
+        return ms.value, n.value
+
+    def residual(self):
+        torch = self.torch
+        nx, ny, nz = self.n
+        R = torch.zeros((5, nz, ny, nx), dtype=torch.float64, device=self.device)
+        L = torch.zeros((nz, ny, nx), dtype=torch.float64, device=self.device)
+        _check(lib().m2c_residual(self.ctx, _ptr(R), _ptr(L)), "m2c_residual", self.ctx)
+        return R, L
+
+
+def m2c_step_batch(grids, nsteps, batch_ws=None):
+    """Steps several Grid objects together (one launch per kernel for all)."""
+    import torch
+    k = len(grids)
+    nb = m2c_batch_bytes(k)
+    if batch_ws is None:
+        batch_ws = torch.empty(nb + 256, dtype=torch.uint8, device=grids[0].device)
+    off = (-batch_ws.data_ptr()) % 256
+    arr = (ctypes.c_void_p * k)(*[g.ctx.value for g in grids])
+    code = lib().m2c_step_batch(arr, k, nsteps, ctypes.c_void_p(batch_ws.data_ptr() + off), nb)
+    _check(code, "m2c_step_batch", grids[0].ctx)
+    return batch_ws
