@@ -156,6 +156,31 @@ m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, c
  * out = (rho1, u1, shock speed). Host arrays; blocks. */
 m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]);
 
+/* Allocation-free stage residual. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory, such as a host
+ * application whose device memory comes from its own fixed pool, or code that
+ * must not trigger the device-wide synchronisation of cudaMalloc and cudaFree.
+ * It computes what m2c_residual computes (R = dW/dt, 5N doubles, and L =
+ * dphi/dt, N doubles, device arrays) for the state W (5N) and phi (N) on an
+ * nx*ny*nz grid with the given EOS of material 0 (phi >= 0) and 1 (phi < 0),
+ * with no context and no workspace. Its scratch is one file-scope device array
+ * of m2c_residual_noalloc_scratch_bytes() bytes (about 10.5 MB), held by every
+ * GPU that loads the library until the process exits. Limits and behaviour:
+ *  - nx*ny*nz <= M2C_NOALLOC_MAX_CELLS (262144, e.g. 64^3); larger grids are
+ *    rejected with M2C_EINVAL before any launch, and m2c_last_error(NULL) says why.
+ *  - the first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - every call shares the one array: calls whose work overlaps on the GPU
+ *    (two streams, two host threads) race; serialise them. Each call clears
+ *    the counters it needs and synchronises the stream before returning, so
+ *    errors raised on the device are returned by the call itself.
+ *  - it calls no cudaMalloc, cudaFree or allocating library routine. */
+#define M2C_NOALLOC_MAX_CELLS 262144
+size_t m2c_residual_noalloc_scratch_bytes(void);
+m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6], const m2c_eos_desc* eos0,
+                                const m2c_eos_desc* eos1, int precision, const double* W, const double* phi,
+                                double* R, double* L, void* stream);
+
 /* Kernel timing: while enabled, m2c_step and m2c_step_batch record a CUDA event
  * pair on the context's stream around every launch of the bulk stage kernel.
  * m2c_profile_read synchronises the stream, returns the summed event time (ms)
@@ -166,6 +191,8 @@ m2c_status m2c_profile_read(m2c_ctx* ctx, double* total_ms, long* launches);
 /* Releases a context (the borrowed memory stays with the caller). */
 void m2c_destroy(m2c_ctx* ctx);
 
+/* Text of the last error of a context; with NULL, of the last failed
+ * context-free call on this thread (m2c_residual_noalloc). */
 const char* m2c_last_error(const m2c_ctx* ctx);
 const char* m2c_status_string(int status);
 

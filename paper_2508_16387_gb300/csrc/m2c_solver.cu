@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1391,6 +1392,140 @@ m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1
   return M2C_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free stage residual.
+//
+// For callers that cannot allocate device memory (a host application whose
+// device memory is handed out by its own pool and must not grow, code that
+// may not trigger the implicit device synchronisation of cudaMalloc/cudaFree,
+// or code that runs where the CUDA allocator is off limits), this entry point
+// computes the same stage residual as m2c_residual with no context and no
+// workspace: its scratch (grid descriptor, control block, material ids, the
+// interface work lists) is one file-scope device array of fixed size, which
+// every GPU that loads this library holds until the process exits. Host code
+// must not pass the array's name to a kernel (in host code it is only a
+// stand-in); its device address is looked up once per device, with that
+// device current, by the first call on the device.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace m2c {
+constexpr long long kNoAllocMaxCells = M2C_NOALLOC_MAX_CELLS;
+constexpr size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+constexpr long long kNoAllocFaceCap = kNoAllocMaxCells / 4 > 4096 ? kNoAllocMaxCells / 4 : 4096;
+constexpr long long kNoAllocCellCap = kNoAllocMaxCells / 8 > 2048 ? kNoAllocMaxCells / 8 : 2048;
+constexpr size_t kNaGrid = 0;
+constexpr size_t kNaTiles = na_align(kNaGrid + sizeof(Grid));
+constexpr size_t kNaCtrl = na_align(kNaTiles + 2 * sizeof(long long));
+constexpr size_t kNaId = na_align(kNaCtrl + sizeof(Ctrl));
+constexpr size_t kNaSlot = na_align(kNaId + (size_t)kNoAllocMaxCells);
+constexpr size_t kNaFaces = na_align(kNaSlot + sizeof(int) * (size_t)kNoAllocMaxCells);
+constexpr size_t kNaCells = na_align(kNaFaces + sizeof(IfFace) * (size_t)kNoAllocFaceCap);
+constexpr size_t kNaBytes = na_align(kNaCells + sizeof(IfCell) * (size_t)kNoAllocCellCap);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+}  // namespace m2c
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {};
+thread_local std::string g_noctx_error;
+
+m2c_status noalloc_fail(m2c_status st, const std::string& msg) {
+  g_noctx_error = msg;
+  return st;
+}
+
+// Device address of the scratch array on the current device, looked up once.
+m2c_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return noalloc_fail(M2C_ECUDA, "no current CUDA device");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, m2c::g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return noalloc_fail(M2C_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return M2C_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t m2c_residual_noalloc_scratch_bytes(void) { return m2c::kNaBytes; }
+
+m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6], const m2c_eos_desc* eos0,
+                                const m2c_eos_desc* eos1, int precision, const double* W, const double* phi,
+                                double* R, double* L, void* stream) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !eos0 || !eos1 || !W || !phi || !R || !L)
+    return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: bad argument");
+  if (precision != M2C_FP64 && precision != M2C_MIXED)
+    return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: bad precision");
+  const long long N = (long long)nx * ny * nz;
+  if (N > m2c::kNoAllocMaxCells)
+    return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: " + std::to_string(N) + " cells exceed the maximum of " +
+                                        std::to_string(m2c::kNoAllocMaxCells));
+  for (int a = 0; a < 3; ++a)
+    if ((bc[2 * a] == M2C_BC_PERIODIC) != (bc[2 * a + 1] == M2C_BC_PERIODIC))
+      return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: periodic sides must come in pairs");
+  void* base = nullptr;
+  m2c_status st = noalloc_scratch(&base);
+  if (st) return st;
+  unsigned char* ws = static_cast<unsigned char*>(base);
+  Grid g;
+  std::memset(&g, 0, sizeof(g));
+  g.nx = nx; g.ny = ny; g.nz = nz; g.N = N;
+  for (int q = 0; q < 6; ++q) g.bc[q] = bc[q];
+  g.active[0] = nx > 1; g.active[1] = ny > 1; g.active[2] = nz > 1;
+  g.prec = precision;
+  g.h = h; g.inv_h = 1.0 / h; g.cfl = 0.5;
+  double p0[6], p1[6];
+  for (int q = 0; q < 6; ++q) { p0[q] = eos0->params[q]; p1[q] = eos1->params[q]; }
+  g.eos[0] = make_eos_dev(eos0->type, p0);
+  g.eos[1] = make_eos_dev(eos1->type, p1);
+  g.W = const_cast<double*>(W);
+  g.phi = const_cast<double*>(phi);
+  g.id = ws + m2c::kNaId;
+  g.cell_slot = reinterpret_cast<int*>(ws + m2c::kNaSlot);
+  g.faces = reinterpret_cast<IfFace*>(ws + m2c::kNaFaces);
+  g.cells = reinterpret_cast<IfCell*>(ws + m2c::kNaCells);
+  g.face_cap = (int)m2c::kNoAllocFaceCap;
+  g.cell_cap = (int)m2c::kNoAllocCellCap;
+  g.ctrl = reinterpret_cast<Ctrl*>(ws + m2c::kNaCtrl);
+  g.resR = R;
+  g.resL = L;
+  const int ty = 8;
+  set_tiling(g, ty, default_tz(g, ty));
+  const long long tiles[2] = {0, ntiles_of(g)};
+  Grid* dg = reinterpret_cast<Grid*>(ws + m2c::kNaGrid);
+  long long* dt = reinterpret_cast<long long*>(ws + m2c::kNaTiles);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the previous call's contents stay in the array: reset the counters and the error latch
+  cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(Ctrl), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dg, &g, sizeof(Grid), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles, sizeof(tiles), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_stage(precision, ty, dg, dt, 1, tiles[1], kResidual, s);
+  if (e == cudaSuccess) {
+    const dim3 lg((unsigned)(2 * sm_count()), 1);
+    k_fiver<<<lg, 128, 0, s>>>(dg, kResidual);
+    k_finish<<<lg, 128, 0, s>>>(dg, kResidual);
+    e = cudaGetLastError();
+  }
+  Ctrl hc;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, g.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return noalloc_fail(M2C_ECUDA, std::string("m2c_residual_noalloc: ") + cudaGetErrorString(e));
+  if (hc.err)
+    return noalloc_fail((m2c_status)hc.err, std::string("m2c_residual_noalloc: device: ") +
+                                                m2c_status_string(hc.err) + " at cell " + std::to_string(hc.err_cell));
+  return M2C_OK;
+}
+
 m2c_status m2c_profile(m2c_ctx* c, int enable) {
   if (!c) return M2C_EINVAL;
   c->profiling = enable != 0;
@@ -1424,6 +1559,6 @@ void m2c_destroy(m2c_ctx* c) {
   delete c;
 }
 
-const char* m2c_last_error(const m2c_ctx* c) { return c ? c->err.c_str() : "null context"; }
+const char* m2c_last_error(const m2c_ctx* c) { return c ? c->err.c_str() : g_noctx_error.c_str(); }
 
 }  // extern "C"

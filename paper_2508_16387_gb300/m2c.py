@@ -69,6 +69,10 @@ def lib():
         L.m2c_get_stats.argtypes = [p, ctypes.POINTER(Stats)]
         L.m2c_solve_riemann.argtypes = [i, ctypes.POINTER(EosDesc), p, ctypes.POINTER(EosDesc), p, p, p, p, i, p]
         L.m2c_shock_state.argtypes = [ctypes.POINTER(EosDesc), p, d, p]
+        L.m2c_residual_noalloc_scratch_bytes.restype = z
+        L.m2c_residual_noalloc_scratch_bytes.argtypes = []
+        L.m2c_residual_noalloc.argtypes = [i, i, i, d, p, ctypes.POINTER(EosDesc), ctypes.POINTER(EosDesc), i,
+                                           p, p, p, p, p]
         L.m2c_profile.argtypes = [p, i]
         L.m2c_profile_read.argtypes = [p, ctypes.POINTER(d), ctypes.POINTER(L_)]
         L.m2c_destroy.argtypes = [p]
@@ -163,6 +167,20 @@ def m2c_shock_state(eos, w, p1):
     _check(lib().m2c_shock_state(ctypes.byref(e), w.ctypes.data_as(ctypes.c_void_p), p1,
                                  out.ctypes.data_as(ctypes.c_void_p)), "m2c_shock_state")
     return tuple(out)
+
+
+def m2c_residual_noalloc(n, h, bc, eos, W, phi, R, L, precision=FP64, stream=None):
+    """Stage residual with no context and no workspace (library-held scratch).
+    W (5, nz, ny, nx), phi, R, L: float64 device tensors. Returns the status code."""
+    nx, ny, nz = n
+    bcs = (ctypes.c_int * 6)(*bc)
+    e0, e1 = eos_desc(eos[0]), eos_desc(eos[1])
+    return lib().m2c_residual_noalloc(nx, ny, nz, h, bcs, ctypes.byref(e0), ctypes.byref(e1), precision,
+                                      _ptr(W), _ptr(phi), _ptr(R), _ptr(L), _stream_handle(stream))
+
+
+def m2c_residual_noalloc_scratch_bytes() -> int:
+    return lib().m2c_residual_noalloc_scratch_bytes()
 
 
 @dataclass

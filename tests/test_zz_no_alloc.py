@@ -1,0 +1,66 @@
+"""The allocation-free residual entry point against the context entry point.
+
+m2c_residual_noalloc serves callers that cannot allocate device memory (their
+device memory comes from a fixed pool they do not own, or they must not cause
+the device-wide synchronisation of cudaMalloc/cudaFree): it computes the stage
+residual with its scratch in one library-held device array. This file is
+collected last so that a run stopping at its first failure has already run
+every other test; it passes alone in a fresh process and after the others.
+"""
+import numpy as np
+import pytest
+
+from paper_2508_16387_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m2c():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2508_16387_gb300 import m2c as M
+    M.lib()
+    return M
+
+
+def _case(M, n, seed, water, precision):
+    import torch
+    P, phi = WL.random_state(n, seed=seed, eos=(water, WL.AIR_PG), two_phase=True)
+    bc = (0, 0, 1, 1, 0, 0)
+    g = M.Grid(n, 1.0 / n[0], bc, (water, WL.AIR_PG), precision=precision)
+    g.set_prims(P, phi)
+    R_ctx, L_ctx = g.residual()
+    W = g.W.clone()
+    ph = g.phi.clone()
+    R = torch.full_like(R_ctx, float("nan"))
+    L = torch.full_like(L_ctx, float("nan"))
+    code = M.m2c_residual_noalloc(n, 1.0 / n[0], bc, (water, WL.AIR_PG), W, ph, R, L, precision=precision)
+    torch.cuda.synchronize()
+    return code, R.cpu().numpy(), L.cpu().numpy(), R_ctx.cpu().numpy(), L_ctx.cpu().numpy()
+
+
+def test_noalloc_residual_matches_context_residual_twice_in_a_row(m2c):
+    # two calls in a row on different grids and materials: the second call must not see the
+    # first call's counters or lists, which stay in the shared array
+    for n, seed, water, prec in (((40, 24, 20), 3, WL.WATER_SG, m2c.FP64),
+                                 ((33, 17, 29), 4, WL.WATER_MG, m2c.FP64),
+                                 ((40, 24, 20), 3, WL.WATER_SG, m2c.MIXED)):
+        code, R, L, R_ctx, L_ctx = _case(m2c, n, seed, water, prec)
+        assert code == 0
+        for v in range(5):
+            scale = max(np.abs(R_ctx[v]).max(), 1e-300)
+            assert np.abs(R[v] - R_ctx[v]).max() <= 1e-11 * scale
+        assert np.abs(L - L_ctx).max() <= 1e-11 * max(np.abs(L_ctx).max(), 1.0)
+
+
+def test_noalloc_rejects_grids_above_its_maximum(m2c):
+    import torch
+    n = (128, 64, 33)   # 270336 cells > 262144
+    W = torch.zeros((5, 1), dtype=torch.float64, device="cuda")
+    phi = torch.zeros(1, dtype=torch.float64, device="cuda")
+    code = m2c.m2c_residual_noalloc(n, 1.0 / 128, (0,) * 6, (WL.WATER_SG, WL.AIR_PG), W, phi, W, phi)
+    assert code == 1
+    assert b"exceed" in m2c.lib().m2c_last_error(None)
+    assert m2c.m2c_residual_noalloc_scratch_bytes() < 16 * 2 ** 20
