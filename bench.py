@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"], help="precision of the headline run")
     return ap.parse_args()
 
 
@@ -198,8 +199,8 @@ def ncu_traffic(kind):
         return None
 
 
-def cpu_baseline(seconds_hint=15.0, n=64, steps=3):
-    """The oracle, as it stands, on the 64^3 version of the same workload (bounded sample)."""
+def cpu_baseline(n=128, steps=2):
+    """The oracle, as it stands, on the 128^3 version of the same workload (bounded sample)."""
     from oracle import oracle as O
     s = setup(n)
     g = O.Grid(n=s.n, h=s.h, eos=tuple(O.EOS(*e) for e in s.eos), bc=s.bc, cfl=s.cfl,
@@ -231,7 +232,7 @@ def run_ours(args):
     N = s.ncells
     out = {}
 
-    g = make_grid(M, s, M.MIXED)
+    g = make_grid(M, s, M.MIXED if args.prec == "mixed" else M.FP64)
     with ClockSampler(local) as clk:
         ms, kms, kl = time_steps(torch, g, args.steps, args.warmup, barrier)
     t_max = ms
@@ -273,8 +274,9 @@ def run_ours(args):
         return
     out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-           "config": {"workload": s.name, "grid": list(s.n), "precision": "mixed", "cells": N,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64 (mixed)" if args.prec == "mixed" else "f64", "data": "synthetic",
+           "config": {"workload": s.name, "grid": list(s.n), "precision": args.prec, "cells": N,
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                       "l2": "state (805 MB) larger than L2, no flush"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64}

@@ -44,7 +44,8 @@
 #define BISECT_CAP 200
 #define HUGONIOT_TOL 1e-14
 #define HUGONIOT_CAP 100
-#define RK4_SUBSTEPS 64
+#define RK4_SUBSTEPS 64      /* substeps of a rarefaction spanning at least RK4_SPAN_FRAC * K0 */
+#define RK4_SPAN_FRAC 0.05
 
 typedef struct {
   int type;
@@ -261,9 +262,21 @@ static int mg_isentrope_rhs(const or_eos_t* q, double p, double rho, double* drh
   return OR_OK;
 }
 
+/* Substeps of the RK4 isentrope integration over [p, p_K] (Reading R6): 64 equal
+ * substeps when the interval spans at least 5% of the reference bulk modulus
+ * K0 = rho0 c0^2, proportionally fewer (at least one) for weaker waves, so the
+ * substep length never exceeds 0.05 K0 / 64. */
+static int rk4_substeps(const or_eos_t* q, double dp) {
+  double K0 = q->prm[0] * q->prm[1] * q->prm[1];
+  double n = ceil(RK4_SUBSTEPS * fabs(dp) / (RK4_SPAN_FRAC * K0));
+  if (!(n >= 1.0)) n = 1.0;
+  if (n > RK4_SUBSTEPS) n = RK4_SUBSTEPS;
+  return (int)n;
+}
+
 /* MG wave curve. Shock: f = sqrt((p - p_K)(1/rho_K - 1/rho_H(p))). Rarefaction:
  * f = integral from p_K to p of dp/(rho c) along the isentrope, integrated
- * together with rho by classical RK4 on 64 equal substeps in p (Reading R6). */
+ * together with rho by classical RK4 on equal substeps in p (Reading R6). */
 static int wave_mg(const or_eos_t* q, const side_t* K, double p, double* f, double* df, double* rs) {
   if (p == K->p) {
     *f = 0.0;
@@ -282,9 +295,10 @@ static int wave_mg(const or_eos_t* q, const side_t* K, double p, double* f, doub
     *rs = rho;
     return OR_OK;
   }
-  double hs = (p - K->p) / RK4_SUBSTEPS;
+  int ns = rk4_substeps(q, p - K->p);
+  double hs = (p - K->p) / ns;
   double rho = K->rho, fv = 0.0;
-  for (int i = 0; i < RK4_SUBSTEPS; ++i) {
+  for (int i = 0; i < ns; ++i) {
     double pi = K->p + i * hs;
     double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
     int st = mg_isentrope_rhs(q, pi, rho, &k1r, &k1f);

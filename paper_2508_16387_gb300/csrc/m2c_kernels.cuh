@@ -49,7 +49,8 @@ struct Grid {
   int active[3];    // axis has more than one cell
   int prec;         // m2c_precision
   double h, inv_h, cfl;
-  EosDev eos[2];
+  EosDev eos[2];          // FP64 parameters (material 0: phi >= 0, 1: phi < 0)
+  EosP<float> eosf[2];    // the same rounded once to FP32, for the mixed-precision kernels
   double* W;        // state W^n (caller's), updated in place by stage 2
   double* phi;      // level set (caller's)
   double* W1;       // stage-1 state

@@ -17,60 +17,68 @@ namespace m2c {
 // (NASG of Sec. 3.3 with b = e_c = 0). MG: App. B.3 with the compression,
 // tension and cutoff branches of the reference curves.
 // ---------------------------------------------------------------------------
-struct EosDev {
+template <typename R>
+struct EosP {
   int type;  // M2C_EOS_SG or M2C_EOS_MG
   int pad;
-  double g, pc, gm1, gpc, inv_gm1;                // SG
-  double rho0, c0, s, G0, e0, eta_min;            // MG
-  double K0, rg, inv_rg, inv_2rho0, eta_max, pmin;  // MG derived
+  R g, pc, gm1, gpc, inv_gm1;                // SG
+  R rho0, c0, s, G0, e0, eta_min;            // MG
+  R K0, rg, inv_rg, inv_2rho0, eta_max, pmin, rk4_span;  // MG derived
 };
+using EosDev = EosP<double>;
 
-__host__ inline EosDev make_eos_dev(int type, const double* prm) {
-  EosDev e{};
+// Parameters computed in FP64 and rounded once to R.
+template <typename R>
+__host__ inline EosP<R> make_eos(int type, const double* prm) {
+  EosP<R> e{};
   e.type = type;
   if (type == M2C_EOS_SG) {
-    e.g = prm[0];
-    e.pc = prm[1];
-    e.gm1 = prm[0] - 1.0;
-    e.gpc = prm[0] * prm[1];
-    e.inv_gm1 = 1.0 / (prm[0] - 1.0);
+    e.g = (R)prm[0];
+    e.pc = (R)prm[1];
+    e.gm1 = (R)(prm[0] - 1.0);
+    e.gpc = (R)(prm[0] * prm[1]);
+    e.inv_gm1 = (R)(1.0 / (prm[0] - 1.0));
   } else {
-    e.rho0 = prm[0];
-    e.c0 = prm[1];
-    e.s = prm[2];
-    e.G0 = prm[3];
-    e.e0 = prm[4];
-    e.eta_min = prm[5];
-    e.K0 = prm[0] * prm[1] * prm[1];
-    e.rg = prm[0] * prm[3];
-    e.inv_rg = 1.0 / e.rg;
-    e.inv_2rho0 = 0.5 / prm[0];
-    e.eta_max = 1.0 / prm[2];
-    e.pmin = e.K0 * prm[5];
+    const double K0 = prm[0] * prm[1] * prm[1], rg = prm[0] * prm[3];
+    e.rho0 = (R)prm[0];
+    e.c0 = (R)prm[1];
+    e.s = (R)prm[2];
+    e.G0 = (R)prm[3];
+    e.e0 = (R)prm[4];
+    e.eta_min = (R)prm[5];
+    e.K0 = (R)K0;
+    e.rg = (R)rg;
+    e.inv_rg = (R)(1.0 / rg);
+    e.inv_2rho0 = (R)(0.5 / prm[0]);
+    e.eta_max = (R)(1.0 / prm[2]);
+    e.pmin = (R)(K0 * prm[5]);
+    e.rk4_span = (R)(0.05 * K0);
   }
   return e;
 }
 
+__host__ inline EosDev make_eos_dev(int type, const double* prm) { return make_eos<double>(type, prm); }
+
 // Reference curves p_R, p_R', e_R, e_R' at strain eta (App. B.3); "p_H" in the
 // compression e_R is read as p_R.
 template <typename R>
-__device__ __forceinline__ void mg_ref(const EosDev& q, R eta, R& pR, R& dpR, R& eR, R& deR) {
-  const R K0 = (R)q.K0, rho0 = (R)q.rho0, e0 = (R)q.e0, h2 = (R)q.inv_2rho0;
+__device__ __forceinline__ void mg_ref(const EosP<R>& q, R eta, R& pR, R& dpR, R& eR, R& deR) {
+  const R K0 = q.K0, rho0 = q.rho0, e0 = q.e0, h2 = q.inv_2rho0;
   if (eta > (R)0) {
-    R d = (R)1 - (R)q.s * eta;
+    R d = (R)1 - q.s * eta;
     R id = (R)1 / d;
     R id2 = id * id;
     pR = K0 * eta * id2;
-    dpR = K0 * ((R)1 + (R)q.s * eta) * id2 * id;
+    dpR = K0 * ((R)1 + q.s * eta) * id2 * id;
     eR = pR * eta * h2 + e0;
     deR = (dpR * eta + pR) * h2;
-  } else if (eta >= (R)q.eta_min) {
+  } else if (eta >= q.eta_min) {
     pR = K0 * eta;
     dpR = K0;
     eR = K0 * eta * eta * h2 + e0;
     deR = K0 * eta / rho0;
   } else {
-    R em = (R)q.eta_min, pm = (R)q.pmin;
+    R em = q.eta_min, pm = q.pmin;
     pR = pm;
     dpR = (R)0;
     eR = K0 * em * em * h2 + e0 + pm / rho0 * (eta - em);
@@ -80,36 +88,36 @@ __device__ __forceinline__ void mg_ref(const EosDev& q, R eta, R& pR, R& dpR, R&
 
 // p(rho, e) given 1/rho; false if the state is outside the EOS domain.
 template <typename R>
-__device__ __forceinline__ bool eos_p(const EosDev& q, R rho, R inv_rho, R e, R& p) {
+__device__ __forceinline__ bool eos_p(const EosP<R>& q, R rho, R inv_rho, R e, R& p) {
   if (q.type == M2C_EOS_SG) {
-    p = (R)q.gm1 * rho * e - (R)q.gpc;
+    p = q.gm1 * rho * e - q.gpc;
     return true;
   }
-  R eta = (R)1 - (R)q.rho0 * inv_rho;
-  if (!(eta < (R)q.eta_max)) return false;
+  R eta = (R)1 - q.rho0 * inv_rho;
+  if (!(eta < q.eta_max)) return false;
   R pR, dpR, eR, deR;
   mg_ref(q, eta, pR, dpR, eR, deR);
-  p = pR + (R)q.rg * (e - eR);
+  p = pR + q.rg * (e - eR);
   return true;
 }
 
 // e(rho, p) and c^2(rho, p) together (App. B.3 and App. C.2: c^2 = dp/drho|_e + p/rho^2 dp/de|_rho).
 // False if rho <= 0, c^2 <= 0 or the state is outside the EOS domain.
 template <typename R>
-__device__ __forceinline__ bool eos_e_c2(const EosDev& q, R rho, R inv_rho, R p, R& e, R& c2) {
+__device__ __forceinline__ bool eos_e_c2(const EosP<R>& q, R rho, R inv_rho, R p, R& e, R& c2) {
   if (!(rho > (R)0)) return false;
   if (q.type == M2C_EOS_SG) {
-    R pb = p + (R)q.pc;
-    e = (p + (R)q.gpc) * (R)q.inv_gm1 * inv_rho;
-    c2 = (R)q.g * pb * inv_rho;
+    R pb = p + q.pc;
+    e = (p + q.gpc) * q.inv_gm1 * inv_rho;
+    c2 = q.g * pb * inv_rho;
   } else {
-    R eta = (R)1 - (R)q.rho0 * inv_rho;
-    if (!(eta < (R)q.eta_max)) return false;
+    R eta = (R)1 - q.rho0 * inv_rho;
+    if (!(eta < q.eta_max)) return false;
     R pR, dpR, eR, deR;
     mg_ref(q, eta, pR, dpR, eR, deR);
-    e = eR + (p - pR) * (R)q.inv_rg;
+    e = eR + (p - pR) * q.inv_rg;
     R ir2 = inv_rho * inv_rho;
-    c2 = ((dpR - (R)q.rg * deR) * (R)q.rho0 + p * (R)q.rg) * ir2;
+    c2 = ((dpR - q.rg * deR) * q.rho0 + p * q.rg) * ir2;
   }
   return c2 > (R)0 && c2 < (R)INFINITY;
 }
@@ -311,9 +319,13 @@ __device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& 
     rs = rho;
     return M2C_OK;
   }
-  const double hs = (p - K.p) / kRk4Steps;
+  // equal substeps, 64 for an interval of at least 5% of K0, fewer (>= 1) for weaker waves
+  double nsd = ceil(kRk4Steps * fabs(p - K.p) / q.rk4_span);
+  nsd = nsd >= 1.0 ? (nsd > kRk4Steps ? (double)kRk4Steps : nsd) : 1.0;
+  const int ns = (int)nsd;
+  const double hs = (p - K.p) / ns;
   double rho = K.rho, fv = 0.0;
-  for (int i = 0; i < kRk4Steps; ++i) {
+  for (int i = 0; i < ns; ++i) {
     double pi = K.p + i * hs;
     double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
     int st = mg_rhs(q, pi, rho, k1r, k1f);

@@ -38,8 +38,8 @@ namespace m2c {
 // the stiffened gas, the pressure (a difference of large numbers when p_c is
 // large) in FP64, then rounded to FP32.
 template <typename R>
-__device__ __forceinline__ bool cons_to_prim(const EosDev& q, const double* __restrict__ W, long long N, long long c,
-                                             R P[5]) {
+__device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd, const double* __restrict__ W,
+                                             long long N, long long c, R P[5]) {
   const double rho = W[c], m1 = W[N + c], m2 = W[2 * N + c], m3 = W[3 * N + c], E = W[4 * N + c];
   if constexpr (sizeof(R) == 8) {
     const double inv = 1.0 / rho;
@@ -60,7 +60,7 @@ __device__ __forceinline__ bool cons_to_prim(const EosDev& q, const double* __re
     float p = 0.0f;
     bool ok = true;
     if (q.type == M2C_EOS_SG) {
-      p = (float)(q.gm1 * rhoe - q.gpc);
+      p = (float)(qd.gm1 * rhoe - qd.gpc);
     } else {
       ok = eos_p<float>(q, rf, inv, (float)rhoe * inv, p);
     }
@@ -70,7 +70,7 @@ __device__ __forceinline__ bool cons_to_prim(const EosDev& q, const double* __re
 }
 
 template <typename R>
-__device__ __forceinline__ bool make_face(const EosDev& q, R rho, R u, R v, R w, R p, FaceState<R>& F) {
+__device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w, R p, FaceState<R>& F) {
   R e = (R)0, c2 = (R)0;
   const bool ok = eos_e_c2<R>(q, rho, (R)1 / rho, p, e, c2);
   F.rho = rho; F.u = u; F.v = v; F.w = w; F.p = p;
@@ -85,7 +85,7 @@ __device__ __forceinline__ bool make_face(const EosDev& q, R rho, R u, R v, R w,
 // makes the whole axis first order (Reading R12). bad: even the cell state is
 // not admissible.
 template <typename R>
-__device__ __forceinline__ void cell_faces(const EosDev& q, const R Pm[5], const R P[5], const R Pp[5], bool same,
+__device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], const R P[5], const R Pp[5], bool same,
                                            FaceState<R>& Qm, FaceState<R>& Qp, bool& bad) {
   if (same) {
     R s[5];
@@ -103,19 +103,26 @@ __device__ __forceinline__ void cell_faces(const EosDev& q, const R Pm[5], const
 }
 
 // Wave-speed sum of a state, sum over the axes with more than one cell of
-// |V_d| + c (the CFL reading of the design notes).
-__device__ __forceinline__ double wave_sum(const Grid& g, const EosDev& q, const double* W, long long N, long long c,
-                                           bool& ok) {
-  double P[5];
-  ok = cons_to_prim<double>(q, W, N, c, P);
-  double e, c2;
-  ok = ok && eos_e_c2<double>(q, P[0], 1.0 / P[0], P[4], e, c2);
-  const double cs = sqrt(c2);
-  double lam = 0.0;
+// |V_d| + c (the CFL reading of the design notes), in precision R (the mixed
+// path takes the time step from FP32 wave speeds of the FP64 state).
+template <typename R>
+__device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, const EosDev& qd, const double* W,
+                                             long long N, long long c, bool& ok) {
+  R P[5];
+  ok = cons_to_prim<R>(q, qd, W, N, c, P);
+  R e, c2;
+  ok = ok && eos_e_c2<R>(q, P[0], (R)1 / P[0], P[4], e, c2);
+  const R cs = sqrt(c2);
+  R lam = (R)0;
   if (g.active[0]) lam = lam + (fabs(P[1]) + cs);
   if (g.active[1]) lam = lam + (fabs(P[2]) + cs);
   if (g.active[2]) lam = lam + (fabs(P[3]) + cs);
-  return lam;
+  return (double)lam;
+}
+
+__device__ __forceinline__ double wave_sum(const Grid& g, const EosDev& q, const double* W, long long N, long long c,
+                                           bool& ok) {
+  return wave_sum_r<double>(g, q, q, W, N, c, ok);
 }
 
 __device__ __forceinline__ double warp_max(double v) {
@@ -162,7 +169,8 @@ struct StageSmem {
   static constexpr size_t fy_off = fx_off + sizeof(R) * 5 * TY * (TX + 1);
   static constexpr size_t id_off = fy_off + sizeof(R) * 5 * (TY + 1) * TX;
   static constexpr size_t eos_off = (id_off + HY * HX + 15) / 16 * 16;
-  static constexpr size_t bytes = eos_off + sizeof(EosDev) * 2;
+  static constexpr size_t eosd_off = eos_off + (sizeof(EosP<R>) * 2 + 15) / 16 * 16;
+  static constexpr size_t bytes = eosd_off + sizeof(EosDev) * 2;
 };
 
 template <typename R, int TY>
@@ -178,7 +186,8 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   R* s_fx = reinterpret_cast<R*>(smem + SM::fx_off);                       // [5][TY][TX+1]
   R* s_fy = reinterpret_cast<R*>(smem + SM::fy_off);                       // [5][TY+1][TX]
   uint8_t* s_id = smem + SM::id_off;                                       // [HY][HX]
-  EosDev* s_eos = reinterpret_cast<EosDev*>(smem + SM::eos_off);
+  EosP<R>* s_eos = reinterpret_cast<EosP<R>*>(smem + SM::eos_off);
+  EosDev* s_eosd = reinterpret_cast<EosDev*>(smem + SM::eosd_off);
   __shared__ double s_dt;
   __shared__ double s_red[32];
 
@@ -202,7 +211,11 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   const int slot = mode == kStage2 ? 1 : 0;
   const long long step = ctrl->step;
 
-  if (tid < 2) s_eos[tid] = G.eos[tid];
+  if (tid < 2) {
+    if constexpr (sizeof(R) == 8) s_eos[tid] = G.eos[tid];
+    else s_eos[tid] = G.eosf[tid];
+    s_eosd[tid] = G.eos[tid];
+  }
   if (tid == 0) s_dt = mode == kResidual ? 0.0 : lam_to_dt(G, ctrl->lam[step & 1]);
   __syncthreads();
   const double dt = s_dt;
@@ -216,7 +229,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     const double phd = phis[c];
     idv = mode == kStage2 ? (G.id[c] & 1) : (phd < 0.0 ? 1 : 0);
     ph = (R)phd;
-    if (!cons_to_prim<R>(s_eos[idv], Ws, N, c, P)) latch_error(ctrl, M2C_ENONPHYS, c);
+    if (!cons_to_prim<R>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) latch_error(ctrl, M2C_ENONPHYS, c);
   };
 
   // ---- warm-up of the z window: planes k0-2 .. k0+1
@@ -406,7 +419,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
             for (int v = 0; v < 5; ++v) G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * (double)res[v]));
             if (!flip) {
               bool ok;
-              const double lam = wave_sum(G, s_eos[id0], G.W, N, c, ok);
+              const double lam = wave_sum_r<R>(G, s_eos[id0], s_eosd[id0], G.W, N, c, ok);
               if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
               lam_max = fmax(lam_max, lam);
             }
@@ -522,7 +535,7 @@ __device__ __forceinline__ void fiver_fluxes(const FaceState<double>& A, const F
   hllc<D, double>(SB, B, Fb);
 }
 
-__global__ void __launch_bounds__(128) k_fiver(const Grid* __restrict__ grids, int mode) {
+__global__ void __launch_bounds__(128, 1) k_fiver(const Grid* __restrict__ grids, int mode) {
   const Grid& G = grids[blockIdx.y];
   Ctrl* ctrl = G.ctrl;
   const int slot = mode == kStage2 ? 1 : 0;
@@ -539,8 +552,8 @@ __global__ void __launch_bounds__(128) k_fiver(const Grid* __restrict__ grids, i
     const EosDev& qa = G.eos[ia];
     const EosDev& qb = G.eos[ib];
     double Pa[5], Pb[5];
-    bool ok = cons_to_prim<double>(qa, Ws, N, ca, Pa);
-    ok = cons_to_prim<double>(qb, Ws, N, cb, Pb) && ok;
+    bool ok = cons_to_prim<double>(qa, qa, Ws, N, ca, Pa);
+    ok = cons_to_prim<double>(qb, qb, Ws, N, cb, Pb) && ok;
     double Fa[5] = {0, 0, 0, 0, 0}, Fb[5] = {0, 0, 0, 0, 0};
     RiemannOut rs;
     int its = 0;
@@ -704,7 +717,7 @@ __global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grid
       const int new_id = G.phi[nb] < 0.0 ? 1 : 0;
       if (old_id == m && new_id == m) {
         double P[5];
-        if (!cons_to_prim<double>(q, G.W, N, nb, P)) latch_error(ctrl, M2C_ENONPHYS, nb);
+        if (!cons_to_prim<double>(q, q, G.W, N, nb, P)) latch_error(ctrl, M2C_ENONPHYS, nb);
 #pragma unroll
         for (int v = 0; v < 5; ++v) sum[v] = sum[v] + P[v];
         ++cnt;
@@ -1143,7 +1156,8 @@ m2c_status m2c_set_eos(m2c_ctx* c, int material, int type, const double* params,
   } else {
     return set_err(c, M2C_EINVAL, "unknown EOS type");
   }
-  c->host.eos[material] = make_eos_dev(type, prm);
+  c->host.eos[material] = make_eos<double>(type, prm);
+  c->host.eosf[material] = make_eos<float>(type, prm);
   c->eos_set[material] = true;
   return push_grid(c);
 }
@@ -1486,8 +1500,10 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
   g.h = h; g.inv_h = 1.0 / h; g.cfl = 0.5;
   double p0[6], p1[6];
   for (int q = 0; q < 6; ++q) { p0[q] = eos0->params[q]; p1[q] = eos1->params[q]; }
-  g.eos[0] = make_eos_dev(eos0->type, p0);
-  g.eos[1] = make_eos_dev(eos1->type, p1);
+  g.eos[0] = make_eos<double>(eos0->type, p0);
+  g.eos[1] = make_eos<double>(eos1->type, p1);
+  g.eosf[0] = make_eos<float>(eos0->type, p0);
+  g.eosf[1] = make_eos<float>(eos1->type, p1);
   g.W = const_cast<double*>(W);
   g.phi = const_cast<double*>(phi);
   g.id = ws + m2c::kNaId;

@@ -223,3 +223,31 @@ def test_nonphysical_state_is_reported(m2c):
     code, cell = g.sync_status()
     assert code == 5
     assert cell == (5 * 24 + 6) * 24 + 7
+
+
+def _block_l1(a, b, k=4):
+    nz, ny, nx = a.shape
+    A = a.reshape(nz // k, k, ny // k, k, nx // k, k).mean(axis=(1, 3, 5))
+    B = b.reshape(nz // k, k, ny // k, k, nx // k, k).mean(axis=(1, 3, 5))
+    return float(np.abs(A - B).sum() / np.abs(B).sum())
+
+
+def test_mixed_precision_l1_error_against_fp64(m2c):
+    """Mixed precision (FP32 reconstruction and HLLC, FP64 accumulation and Riemann solver) on the
+    MG shock-bubble setup at 64^3 after the shock has reached the bubble: relative L1 error of
+    4^3-block averages of density and pressure against the FP64 path <= 1e-4."""
+    s = WL.shock_bubble(n=64, water=WL.WATER_MG, steps=100)
+    out = {}
+    for prec in (0, 1):
+        g = gpu_start(m2c, s, prec)
+        g.step(100)
+        g.sync()
+        W = g.W.cpu().numpy()
+        phi = g.phi.cpu().numpy()
+        P = O.cons_to_prims(oracle_grid(s), W, phi)
+        out[prec] = (P, phi)
+    P64, P32 = out[0][0], out[1][0]
+    e_rho = _block_l1(P32[0], P64[0])
+    e_p = _block_l1(P32[4], P64[4])
+    assert e_rho <= 1e-4 and e_p <= 1e-4, (e_rho, e_p)
+    assert (out[0][1] < 0).sum() > 0
