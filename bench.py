@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"], help="precision of the headline run")
+    ap.add_argument("--workload", default="grid256", choices=["grid256", "batched", "served"])
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -118,12 +121,8 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- GPU arm
 
 def make_grid(M, s, precision, stream=None):
-    g = M.Grid(s.n, s.h, s.bc, s.eos, precision=precision, cfl=s.cfl, reinit_every=s.reinit_every,
-               reinit_iters=s.reinit_iters, stream=stream)
-    amb = s.prims_by_region[s.shock[1]]
-    r1, u1, _ = M.m2c_shock_state(s.eos[0], (amb[0], amb[1], amb[4]), s.shock[0])
-    g.set_prims(s.prims((r1, u1)), s.phi)
-    return g
+    from paper_2508_16387_gb300 import runner as RN
+    return RN.grid_for(s, precision, stream=stream)
 
 
 def launches_per_step(step_index, reinit_every, reinit_iters):
@@ -318,9 +317,57 @@ def run_reference(args):
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def run_batched(args):
+    """64 shock-bubble grids with edges drawn from {32, 48, 64, 96, 128}, radius, centre and shock
+    pressure drawn from seed 3, stepped together 200 steps in one captured CUDA graph, after the
+    autotuner has picked the tile shape, schedule and persistent grid size."""
+    import torch
+    from paper_2508_16387_gb300 import autotune as AT
+    from paper_2508_16387_gb300 import m2c as M
+    from paper_2508_16387_gb300 import workloads as WL
+    torch.cuda.set_device(dist_env()[2])
+    M.lib()
+    setups = WL.batched_instances(count=args.instances, seed=3, steps=args.batch_steps)
+    N = sum(s.ncells for s in setups)
+    res = {}
+    for name, prec in (("mixed", M.MIXED), ("fp64", M.FP64)):
+        grids = [make_grid(M, s, prec) for s in setups]
+        cands = AT.DEFAULT_CANDIDATES if prec == M.MIXED else [(8, 0, 0, 0), (8, 0, 1, 2), (4, 0, 1, 2), (8, 32, 1, 1)]
+        best, trials = AT.tune_batch(grids, candidates=cands, trial_steps=2)
+        bt = M.Batch(grids, best)
+        t0 = time.perf_counter()
+        bt.capture(args.batch_steps)
+        cap_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dist_env()[2]) as clk:
+            e0.record(torch.cuda.current_stream())
+            bt.launch_graph()
+            e1.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        for g in grids:
+            g.sync()
+        res[name] = {"value": round(N * args.batch_steps / (ms * 1e-3) / 1e6, 2), "ms": round(ms, 1),
+                     "tuning": {"tile_rows": best[0], "tile_z": best[1], "schedule": ["stride", "atomic"][best[2]],
+                                "blocks_per_sm": best[3]},
+                     "autotune_trials": len(trials), "capture_s": round(cap_s, 2), "clocks": clk.summary()}
+        del bt, grids
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "Mcell-updates/s, uneven shock-bubble grids stepped in one CUDA graph",
+                      "value": res["mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.batch_steps,
+                      "higher_is_better": True, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+                      "config": {"workload": f"batched_{args.instances}_grids_seed3", "cells": N,
+                                 "edges": sorted({s.n[0] for s in setups})},
+                      "mixed": res["mixed"], "fp64": res["fp64"]}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batched":
+        run_batched(a)
     else:
         run_ours(a)

@@ -105,6 +105,10 @@ m2c_status m2c_set_eos(m2c_ctx* ctx, int material, int type, const double* param
  * reinit_every-th step, reinit_iters pseudo-time iterations (0 disables). */
 m2c_status m2c_set_scheme(m2c_ctx* ctx, double cfl, int reinit_every, int reinit_iters);
 
+/* Tile of the bulk stage kernel: 32 x tile_rows (4 or 8) columns marching
+ * tile_z cells along z (0: automatic). Results do not depend on the tiling. */
+m2c_status m2c_set_tiling(m2c_ctx* ctx, int tile_rows, int tile_z);
+
 /* Borrows the device arrays W (5N doubles) and phi (N doubles) as the state,
  * sets time t and step counter step, and computes the first time step. */
 m2c_status m2c_set_state(m2c_ctx* ctx, double* W, double* phi, double t, long step);
@@ -121,14 +125,35 @@ m2c_status m2c_download_state(m2c_ctx* ctx, double* W_host, double* phi_host);
 /* Enqueues nsteps time steps on the context's stream. */
 m2c_status m2c_step(m2c_ctx* ctx, int nsteps);
 
-/* Device bytes of the descriptor table of a batch of k contexts. */
-size_t m2c_batch_bytes(int k);
+/* Batches: several contexts of one precision stepped together, one launch per
+ * kernel for all of them (the bulk kernel takes its tiles from all grids of
+ * the batch, largest grid first; every grid keeps its own time step, error
+ * latch and work lists). The reinitialisation schedule is the first context's.
+ * workspace: caller's device buffer of m2c_batch_workspace_bytes(k) bytes,
+ * 256-byte aligned, borrowed for the life of the batch. tuning (may be NULL) =
+ * {tile rows 4 or 8, tile length along z (0: automatic), schedule (0: fixed
+ * stride over tiles, 1: atomic tile counter), blocks per SM of a persistent
+ * grid (0: one block per tile)}. m2c_batch_create synchronises (it uploads the
+ * descriptors and reduces the first time steps). */
+typedef struct m2c_batch m2c_batch;
+size_t m2c_batch_workspace_bytes(int k);
+m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** ctxs, int k, void* workspace, size_t bytes,
+                            const int tuning[4]);
 
-/* Enqueues nsteps time steps of k contexts (one precision, one reinitialisation
- * schedule: the first context's) on the first context's stream, with one launch
- * per kernel for all contexts. batch_ws: caller's device buffer of
- * m2c_batch_bytes(k) bytes, 256-byte aligned, borrowed until the steps complete. */
-m2c_status m2c_step_batch(m2c_ctx** ctxs, int k, int nsteps, void* batch_ws, size_t bytes);
+/* Enqueues nsteps steps of the batch on the first context's stream (no host
+ * synchronisation). */
+m2c_status m2c_batch_step(m2c_batch* b, int nsteps);
+
+/* Captures nsteps steps of the batch into a CUDA graph (instantiated, returned
+ * as an opaque cudaGraphExec_t); m2c_batch_launch_graph launches it on the
+ * batch's stream and advances the step counters; m2c_graph_destroy frees it.
+ * A graph holds the reinitialisation schedule of the steps it captured: it may
+ * be launched again only at the same phase of that schedule (M2C_EINVAL
+ * otherwise), e.g. repeatedly when nsteps is a multiple of reinit_every. */
+m2c_status m2c_batch_capture(m2c_batch* b, int nsteps, void** graph_exec);
+m2c_status m2c_batch_launch_graph(m2c_batch* b, void* graph_exec);
+void m2c_graph_destroy(void* graph_exec);
+void m2c_batch_destroy(m2c_batch* b);
 
 /* Writes the residual of one Runge-Kutta stage of the current state, without
  * advancing it: R (5N) = dW/dt and L (N) = dphi/dt, device arrays. */
@@ -181,7 +206,7 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
                                 const m2c_eos_desc* eos1, int precision, const double* W, const double* phi,
                                 double* R, double* L, void* stream);
 
-/* Kernel timing: while enabled, m2c_step and m2c_step_batch record a CUDA event
+/* Kernel timing: while enabled, m2c_step records a CUDA event
  * pair on the context's stream around every launch of the bulk stage kernel.
  * m2c_profile_read synchronises the stream, returns the summed event time (ms)
  * and the number of timed launches, and starts a new count. */

@@ -59,6 +59,25 @@ __host__ inline EosP<R> make_eos(int type, const double* prm) {
 
 __host__ inline EosDev make_eos_dev(int type, const double* prm) { return make_eos<double>(type, prm); }
 
+// Division, reciprocal and square root of the working precision: IEEE for FP64;
+// for the FP32 half of the mixed path the hardware approximations (a few ulp),
+// which are far below the FP32 rounding already accepted there.
+template <typename R>
+__device__ __forceinline__ R rdiv(R a, R b) {
+  if constexpr (sizeof(R) == 8) return a / b;
+  else return __fdividef(a, b);
+}
+template <typename R>
+__device__ __forceinline__ R rrcp(R x) {
+  if constexpr (sizeof(R) == 8) return (R)1 / x;
+  else return __fdividef(1.0f, x);
+}
+template <typename R>
+__device__ __forceinline__ R rsqrt_pos(R x) {  // sqrt of x > 0
+  if constexpr (sizeof(R) == 8) return sqrt(x);
+  else return x * rsqrtf(x);
+}
+
 // Reference curves p_R, p_R', e_R, e_R' at strain eta (App. B.3); "p_H" in the
 // compression e_R is read as p_R.
 template <typename R>
@@ -66,7 +85,7 @@ __device__ __forceinline__ void mg_ref(const EosP<R>& q, R eta, R& pR, R& dpR, R
   const R K0 = q.K0, rho0 = q.rho0, e0 = q.e0, h2 = q.inv_2rho0;
   if (eta > (R)0) {
     R d = (R)1 - q.s * eta;
-    R id = (R)1 / d;
+    R id = rrcp<R>(d);
     R id2 = id * id;
     pR = K0 * eta * id2;
     dpR = K0 * ((R)1 + q.s * eta) * id2 * id;
@@ -76,7 +95,7 @@ __device__ __forceinline__ void mg_ref(const EosP<R>& q, R eta, R& pR, R& dpR, R
     pR = K0 * eta;
     dpR = K0;
     eR = K0 * eta * eta * h2 + e0;
-    deR = K0 * eta / rho0;
+    deR = K0 * eta * ((R)2 * h2);
   } else {
     R em = q.eta_min, pm = q.pmin;
     pR = pm;
@@ -130,7 +149,7 @@ template <typename R>
 __device__ __forceinline__ R va_slope(R a, R b) {
   R ab = a * b;
   if (!(ab > (R)0)) return (R)0;
-  return ab * (a + b) / (a * a + b * b);
+  return rdiv<R>(ab * (a + b), a * a + b * b);
 }
 
 // A reconstructed face state with its sound speed and total energy per mass.
@@ -167,7 +186,7 @@ __device__ __forceinline__ void hllc(const FaceState<R>& L, const FaceState<R>& 
   const R SL = fmin(uL - L.c, uR - Rt.c);
   const R SR = fmax(uL + L.c, uR + Rt.c);
   const R aL = L.rho * (SL - uL), aR = Rt.rho * (SR - uR);
-  const R Ss = (Rt.p - L.p + uL * aL - uR * aR) / (aL - aR);
+  const R Ss = rdiv<R>(Rt.p - L.p + uL * aL - uR * aR, aL - aR);
   if ((R)0 <= SL) {
     phys_flux<D>(L, F);
     return;
@@ -184,8 +203,8 @@ __device__ __forceinline__ void hllc(const FaceState<R>& L, const FaceState<R>& 
   const R uK = left ? uL : uR;
   const R aK = left ? aL : aR;
   phys_flux<D>(K, F);
-  const R fac = aK / (SK - Ss);
-  const R Es = K.E + (Ss - uK) * (Ss + K.p / aK);
+  const R fac = rdiv<R>(aK, SK - Ss);
+  const R Es = K.E + (Ss - uK) * (Ss + rdiv<R>(K.p, aK));
   R ws[5] = {fac, fac * K.u, fac * K.v, fac * K.w, fac * Es};
   ws[1 + D] = fac * Ss;
   const R wk[5] = {K.rho, K.rho * K.u, K.rho * K.v, K.rho * K.w, K.rho * K.E};

@@ -16,6 +16,7 @@
 // the wave-speed sum, atomically, in the kernels that write the new state).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -52,7 +53,7 @@ __device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd,
     return ok && rho > 0.0;
   } else {
     const float rf = (float)rho;
-    const float inv = 1.0f / rf;
+    const float inv = rrcp<float>(rf);
     const float f1 = (float)m1, f2 = (float)m2, f3 = (float)m3;
     const float u = f1 * inv, v = f2 * inv, w = f3 * inv;
     const float ke = 0.5f * ((f1 * u + f2 * v) + f3 * w);
@@ -72,9 +73,9 @@ __device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd,
 template <typename R>
 __device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w, R p, FaceState<R>& F) {
   R e = (R)0, c2 = (R)0;
-  const bool ok = eos_e_c2<R>(q, rho, (R)1 / rho, p, e, c2);
+  const bool ok = eos_e_c2<R>(q, rho, rrcp<R>(rho), p, e, c2);
   F.rho = rho; F.u = u; F.v = v; F.w = w; F.p = p;
-  F.c = sqrt(c2);
+  F.c = ok ? rsqrt_pos<R>(c2) : (R)0;
   F.E = e + (R)0.5 * ((u * u + v * v) + w * w);
   return ok;
 }
@@ -111,8 +112,8 @@ __device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, co
   R P[5];
   ok = cons_to_prim<R>(q, qd, W, N, c, P);
   R e, c2;
-  ok = ok && eos_e_c2<R>(q, P[0], (R)1 / P[0], P[4], e, c2);
-  const R cs = sqrt(c2);
+  ok = ok && eos_e_c2<R>(q, P[0], rrcp<R>(P[0]), P[4], e, c2);
+  const R cs = ok ? rsqrt_pos<R>(c2) : (R)0;
   R lam = (R)0;
   if (g.active[0]) lam = lam + (fabs(P[1]) + cs);
   if (g.active[1]) lam = lam + (fabs(P[2]) + cs);
@@ -175,7 +176,8 @@ struct StageSmem {
 
 template <typename R, int TY>
 __global__ void __launch_bounds__(32 * TY)
-k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, int mode) {
+k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, long long ntiles, int mode,
+        int sched, unsigned long long* __restrict__ tile_counter) {
   constexpr int TX = 32, NT = TX * TY, HX = TX + 4, HY = TY + 4;
   using SM = StageSmem<R, TY>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -192,7 +194,19 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   __shared__ double s_red[32];
 
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-  const long long tile = blockIdx.x;
+  __shared__ long long s_tile;
+  // Tiles of all grids of the launch, taken in order by a fixed stride
+  // (sched 0) or from an atomic counter (sched 1).
+  for (long long iter = 0;; ++iter) {
+  long long tile;
+  if (sched == 1) {
+    if (tid == 0) s_tile = (long long)atomicAdd(tile_counter, 1ull);
+    __syncthreads();
+    tile = s_tile;
+  } else {
+    tile = blockIdx.x + iter * (long long)gridDim.x;
+  }
+  if (tile >= ntiles) break;
   const int gidx = find_grid(tile_begin, ngrid, tile);
   const Grid& G = grids[gidx];
   const int nx = G.nx, ny = G.ny, nz = G.nz;
@@ -517,6 +531,8 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   }
   if (bad) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, gx, gy, k0));
   if (mode == kStage2) block_max_to(lam_max, &ctrl->lam[(step + 1) & 1], s_red);
+  __syncthreads();  // the next tile reuses the shared memory
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -640,9 +656,13 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
 // phi' = phi - dtau S(phi0) (G(phi) - 1), Godunov upwind |grad phi|,
 // S = phi0/sqrt(phi0^2 + h^2), dtau = h/2, first-layer cells fixed.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, const double* __restrict__ src,
-                                                double* __restrict__ dst, int first_iter) {
+__global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, int it, int nits) {
   const Grid& G = grids[blockIdx.y];
+  // phi0 is the state phi; iterations alternate phi1 and phiC and the last one
+  // writes phi (a single iteration ends in phi1 and is copied back)
+  const double* __restrict__ src = it == 1 ? G.phi : ((it % 2 == 0) ? G.phi1 : G.phiC);
+  double* __restrict__ dst = (it == nits && it > 1) ? G.phi : ((it % 2 == 1) ? G.phi1 : G.phiC);
+  const int first_iter = it == 1;
   const double* __restrict__ phi0 = G.phi;
   const long long N = G.N;
   const double h = G.h, ih = G.inv_h, dtau = 0.5 * G.h;
@@ -687,10 +707,10 @@ __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, 
   }
 }
 
-__global__ void k_copy(const Grid* __restrict__ grids, const double* __restrict__ src, double* __restrict__ dst) {
+__global__ void k_copy_phi1(const Grid* __restrict__ grids) {
   const Grid& G = grids[blockIdx.y];
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x)
-    dst[c] = src[c];
+    G.phi[c] = G.phi1[c];
 }
 
 // ---------------------------------------------------------------------------
@@ -912,22 +932,46 @@ void stage_smem_setup() {
   done = true;
 }
 
+struct LaunchPlan {
+  int ty = 8;            // tile rows (4 or 8)
+  int sched = 0;         // 0: fixed stride over tiles, 1: atomic tile counter
+  int blocks_per_sm = 0; // persistent grid of blocks_per_sm x SMs blocks; 0: one block per tile
+  unsigned long long* counter = nullptr;
+};
+
+int sm_count();
+
 template <typename R, int TY>
 cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
-                           cudaStream_t s) {
+                           const LaunchPlan& lp, cudaStream_t s) {
   stage_smem_setup<R, TY>();
-  k_stage<R, TY><<<(unsigned)ntiles, 32 * TY, StageSmem<R, TY>::bytes, s>>>(grids, tiles, ngrid, mode);
+  long long nb = ntiles;
+  if (lp.blocks_per_sm > 0) nb = std::min<long long>(ntiles, (long long)lp.blocks_per_sm * sm_count());
+  if (nb < 1) nb = 1;
+  if (lp.sched == 1) {
+    cudaError_t e = cudaMemsetAsync(lp.counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
+  k_stage<R, TY><<<(unsigned)nb, 32 * TY, StageSmem<R, TY>::bytes, s>>>(grids, tiles, ngrid, ntiles, mode,
+                                                                         lp.sched, lp.counter);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stage(int prec, int ty, const Grid* grids, const long long* tiles, int ngrid, long long ntiles,
-                         int mode, cudaStream_t s) {
+cudaError_t launch_stage(int prec, const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
+                         const LaunchPlan& lp, cudaStream_t s) {
   if (prec == M2C_FP64) {
-    if (ty == 4) return launch_stage_t<double, 4>(grids, tiles, ngrid, ntiles, mode, s);
-    return launch_stage_t<double, 8>(grids, tiles, ngrid, ntiles, mode, s);
+    if (lp.ty == 4) return launch_stage_t<double, 4>(grids, tiles, ngrid, ntiles, mode, lp, s);
+    return launch_stage_t<double, 8>(grids, tiles, ngrid, ntiles, mode, lp, s);
   }
-  if (ty == 4) return launch_stage_t<float, 4>(grids, tiles, ngrid, ntiles, mode, s);
-  return launch_stage_t<float, 8>(grids, tiles, ngrid, ntiles, mode, s);
+  if (lp.ty == 4) return launch_stage_t<float, 4>(grids, tiles, ngrid, ntiles, mode, lp, s);
+  return launch_stage_t<float, 8>(grids, tiles, ngrid, ntiles, mode, lp, s);
+}
+
+void setup_all_stage_kernels() {
+  stage_smem_setup<double, 4>();
+  stage_smem_setup<double, 8>();
+  stage_smem_setup<float, 4>();
+  stage_smem_setup<float, 8>();
 }
 
 int sm_count() {
@@ -994,35 +1038,23 @@ cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s) {
 }
 
 cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int ngrid, long long ntiles, int prec,
-                         int ty, bool reinit, int reinit_iters, const std::vector<Grid>& hosts, cudaStream_t s,
+                         const LaunchPlan& lp, bool reinit, int reinit_iters, long long nmax, cudaStream_t s,
                          StageEvents* pe = nullptr) {
   cudaError_t e;
   const dim3 lg((unsigned)(2 * sm_count()), (unsigned)ngrid);
   for (int stage = 0; stage < 2; ++stage) {
     const int mode = stage == 0 ? kStage1 : kStage2;
     if ((e = record_pair(pe, true, s)) != cudaSuccess) return e;
-    e = launch_stage(prec, ty, dev_grids, dev_tiles, ngrid, ntiles, mode, s);
+    e = launch_stage(prec, dev_grids, dev_tiles, ngrid, ntiles, mode, lp, s);
     if (e != cudaSuccess) return e;
     if ((e = record_pair(pe, false, s)) != cudaSuccess) return e;
     k_fiver<<<lg, 128, 0, s>>>(dev_grids, mode);
     k_finish<<<lg, 128, 0, s>>>(dev_grids, mode);
   }
   if (reinit && reinit_iters > 0) {
-    // phi0 = state phi; iterate through phi1 and phiC and end in phi. A single
-    // iteration goes through phi1 and a copy back.
-    // the per-grid buffers differ, so each iteration is launched per grid
-    for (int gi = 0; gi < ngrid; ++gi) {
-      const Grid& g = hosts[gi];
-      const Grid* dg = dev_grids + gi;
-      const dim3 r1((unsigned)std::min<long long>((g.N + 255) / 256, 8ll * sm_count()), 1);
-      for (int it = 1; it <= reinit_iters; ++it) {
-        const double* src = it == 1 ? g.phi : ((it % 2 == 0) ? g.phi1 : g.phiC);
-        double* dst = (it % 2 == 1) ? g.phi1 : g.phiC;
-        if (it == reinit_iters && it > 1) dst = g.phi;
-        k_reinit<<<r1, 256, 0, s>>>(dg, src, dst, it == 1);
-      }
-      if (reinit_iters == 1) k_copy<<<r1, 256, 0, s>>>(dg, g.phi1, g.phi);
-    }
+    const dim3 rg((unsigned)std::min<long long>((nmax + 255) / 256, 8ll * sm_count()), (unsigned)ngrid);
+    for (int it = 1; it <= reinit_iters; ++it) k_reinit<<<rg, 256, 0, s>>>(dev_grids, it, reinit_iters);
+    if (reinit_iters == 1) k_copy_phi1<<<rg, 256, 0, s>>>(dev_grids);
   }
   k_phase_fix<<<lg, 128, 0, s>>>(dev_grids);
   k_end_step<<<(ngrid + 63) / 64, 64, 0, s>>>(dev_grids, ngrid);
@@ -1051,6 +1083,22 @@ double lam_to_dt_host(const Grid& g, unsigned long long bits) {
 }
 
 }  // namespace
+
+// A batch of grids stepped together: one launch per kernel for all grids.
+struct m2c_batch {
+  std::vector<m2c_ctx*> ctx;      // largest grid first
+  std::vector<Grid> hosts;
+  std::vector<long long> tiles;   // prefix sums of the bulk-kernel tiles
+  Grid* dev = nullptr;
+  long long* dtiles = nullptr;
+  unsigned long long* counter = nullptr;
+  LaunchPlan lp;
+  int prec = 0;
+  cudaStream_t stream = nullptr;
+  long long step = 0, nmax = 1;
+  int reinit_every = 10, reinit_iters = 5, graph_steps = 0;
+  long long graph_phase = 0;  // step index modulo the reinitialisation period at capture
+};
 
 extern "C" {
 
@@ -1114,10 +1162,9 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   c->dev_grid = reinterpret_cast<Grid*>(ws + L.grid);
   c->dev_tiles = reinterpret_cast<long long*>(ws + L.tiles);
   c->stream = static_cast<cudaStream_t>(stream);
+  setup_all_stage_kernels();
   c->ty = 8;
-  if (const char* e = std::getenv("M2C_TILE_TY")) c->ty = std::atoi(e) == 4 ? 4 : 8;
   set_tiling(g, c->ty, default_tz(g, c->ty));
-  if (const char* e = std::getenv("M2C_TILE_TZ")) set_tiling(g, c->ty, std::max(1, std::atoi(e)));
   c->reinit_every = 10;
   c->reinit_iters = 5;
   c->host_step = 0;
@@ -1168,6 +1215,13 @@ m2c_status m2c_set_scheme(m2c_ctx* c, double cfl, int reinit_every, int reinit_i
   c->host.cfl = cfl;
   c->reinit_every = reinit_every;
   c->reinit_iters = reinit_iters;
+  return push_grid(c);
+}
+
+m2c_status m2c_set_tiling(m2c_ctx* c, int tile_rows, int tile_z) {
+  if (!c || (tile_rows != 4 && tile_rows != 8) || tile_z < 0) return M2C_EINVAL;
+  c->ty = tile_rows;
+  set_tiling(c->host, c->ty, tile_z > 0 ? tile_z : default_tz(c->host, c->ty));
   return push_grid(c);
 }
 
@@ -1233,63 +1287,154 @@ m2c_status m2c_step(m2c_ctx* c, int nsteps) {
     cudaError_t e = ensure_lam(c);
     if (e != cudaSuccess) return cuda_check(c, e, "first time step");
   }
-  std::vector<Grid> hosts(1, c->host);
   for (int n = 0; n < nsteps; ++n) {
     const bool re = c->reinit_every > 0 && (c->host_step + 1) % c->reinit_every == 0;
     StageEvents pe{&c->ev, &c->ev_used};
-    cudaError_t e = enqueue_step(c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), c->host.prec, c->ty, re,
-                                 c->reinit_iters, hosts, c->stream, c->profiling ? &pe : nullptr);
+    LaunchPlan lp;
+    lp.ty = c->ty;
+    cudaError_t e = enqueue_step(c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), c->host.prec, lp, re,
+                                 c->reinit_iters, c->host.N, c->stream, c->profiling ? &pe : nullptr);
     if (e != cudaSuccess) return cuda_check(c, e, "step launch");
     ++c->host_step;
   }
   return M2C_OK;
 }
 
-size_t m2c_batch_bytes(int k) {
+size_t m2c_batch_workspace_bytes(int k) {
   if (k < 1) return 0;
-  return align_up(sizeof(Grid) * (size_t)k) + align_up(sizeof(long long) * (size_t)(k + 1));
+  return align_up(sizeof(Grid) * (size_t)k) + align_up(sizeof(long long) * (size_t)(k + 1)) + kAlign;
 }
 
-m2c_status m2c_step_batch(m2c_ctx** v, int k, int nsteps, void* batch_ws, size_t bytes) {
-  if (!v || k < 1 || nsteps < 0 || !batch_ws) return M2C_EINVAL;
-  if (bytes < m2c_batch_bytes(k) || reinterpret_cast<uintptr_t>(batch_ws) % kAlign) return M2C_EINVAL;
-  m2c_ctx* c0 = v[0];
-  if (!c0) return M2C_EINVAL;
+m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace, size_t bytes, const int tuning[4]) {
+  if (!out || !v || k < 1 || !workspace) return M2C_EINVAL;
+  *out = nullptr;
+  if (bytes < m2c_batch_workspace_bytes(k) || reinterpret_cast<uintptr_t>(workspace) % kAlign) return M2C_EINVAL;
   for (int i = 0; i < k; ++i) {
-    if (!v[i] || !v[i]->has_state) return set_err(c0, M2C_EINVAL, "context without state");
-    if (v[i]->host.prec != c0->host.prec) return set_err(c0, M2C_EINVAL, "mixed precisions in one batch");
+    if (!v[i] || !v[i]->has_state) return M2C_EINVAL;
+    if (v[i]->host.prec != v[0]->host.prec) return set_err(v[0], M2C_EINVAL, "one precision per batch");
   }
+  int ty = 8, tz = 0, sched = 0, bpsm = 0;
+  if (tuning) {
+    ty = tuning[0] == 4 ? 4 : 8;
+    tz = std::max(0, tuning[1]);
+    sched = tuning[2] == 1 ? 1 : 0;
+    bpsm = std::max(0, tuning[3]);
+  }
+  m2c_batch* b = new (std::nothrow) m2c_batch();
+  if (!b) return M2C_ENOMEM;
+  // largest grids first, so that the longest tiles start early
+  std::vector<int> order(k);
+  for (int i = 0; i < k; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return v[a]->host.N > v[c]->host.N; });
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  b->dev = reinterpret_cast<Grid*>(ws);
+  b->dtiles = reinterpret_cast<long long*>(ws + align_up(sizeof(Grid) * (size_t)k));
+  b->counter = reinterpret_cast<unsigned long long*>(ws + align_up(sizeof(Grid) * (size_t)k) +
+                                                     align_up(sizeof(long long) * (size_t)(k + 1)));
+  b->tiles.assign(k + 1, 0);
+  b->nmax = 1;
   for (int i = 0; i < k; ++i) {
-    if (!v[i]->lam_valid && nsteps > 0) {
-      cudaError_t e0 = ensure_lam(v[i]);
-      if (e0 != cudaSuccess) return cuda_check(c0, e0, "first time step");
-      cudaStreamSynchronize(v[i]->stream);
+    m2c_ctx* c = v[order[i]];
+    b->ctx.push_back(c);
+    Grid g = c->host;
+    set_tiling(g, ty, tz > 0 ? tz : default_tz(g, ty));
+    b->hosts.push_back(g);
+    b->tiles[i + 1] = b->tiles[i] + ntiles_of(g);
+    b->nmax = std::max(b->nmax, g.N);
+  }
+  b->lp.ty = ty;
+  b->lp.sched = sched;
+  b->lp.blocks_per_sm = bpsm;
+  b->lp.counter = b->counter;
+  b->prec = v[0]->host.prec;
+  b->stream = v[0]->stream;
+  b->step = v[0]->host_step;
+  b->reinit_every = v[0]->reinit_every;
+  b->reinit_iters = v[0]->reinit_iters;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < k && e == cudaSuccess; ++i) {
+    m2c_ctx* c = b->ctx[i];
+    if (!c->lam_valid) {
+      e = ensure_lam(c);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     }
   }
-  Grid* dev = static_cast<Grid*>(batch_ws);
-  long long* dtiles = reinterpret_cast<long long*>(static_cast<unsigned char*>(batch_ws) + align_up(sizeof(Grid) * (size_t)k));
-  std::vector<Grid> hosts(k);
-  std::vector<long long> tiles(k + 1, 0);
-  for (int i = 0; i < k; ++i) {
-    hosts[i] = v[i]->host;
-    set_tiling(hosts[i], c0->ty, default_tz(hosts[i], c0->ty));
-    tiles[i + 1] = tiles[i] + ntiles_of(hosts[i]);
-  }
-  cudaError_t e = cudaMemcpyAsync(dev, hosts.data(), sizeof(Grid) * k, cudaMemcpyHostToDevice, c0->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dtiles, tiles.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, c0->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c0->stream);
-  if (e != cudaSuccess) return cuda_check(c0, e, "batch descriptors");
+    e = cudaMemcpyAsync(b->dev, b->hosts.data(), sizeof(Grid) * k, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->dtiles, b->tiles.data(), sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_check(v[0], e, "batch_create");
+  }
+  *out = b;
+  return M2C_OK;
+}
+
+static m2c_status batch_enqueue(m2c_batch* b, int nsteps, cudaStream_t s) {
+  const int k = (int)b->ctx.size();
   for (int n = 0; n < nsteps; ++n) {
-    const bool re = c0->reinit_every > 0 && (c0->host_step + 1) % c0->reinit_every == 0;
-    StageEvents pe{&c0->ev, &c0->ev_used};
-    e = enqueue_step(dev, dtiles, k, tiles[k], c0->host.prec, c0->ty, re, c0->reinit_iters, hosts, c0->stream,
-                     c0->profiling ? &pe : nullptr);
-    if (e != cudaSuccess) return cuda_check(c0, e, "batch step launch");
-    for (int i = 0; i < k; ++i) ++v[i]->host_step;
+    const bool re = b->reinit_every > 0 && (b->step + 1) % b->reinit_every == 0;
+    cudaError_t e = enqueue_step(b->dev, b->dtiles, k, b->tiles[k], b->prec, b->lp, re, b->reinit_iters, b->nmax, s);
+    if (e != cudaSuccess) return cuda_check(b->ctx[0], e, "batch step launch");
+    ++b->step;
+    for (m2c_ctx* c : b->ctx) ++c->host_step;
   }
   return M2C_OK;
 }
+
+m2c_status m2c_batch_step(m2c_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return M2C_EINVAL;
+  return batch_enqueue(b, nsteps, b->stream);
+}
+
+m2c_status m2c_batch_capture(m2c_batch* b, int nsteps, void** graph_exec) {
+  if (!b || nsteps < 1 || !graph_exec) return M2C_EINVAL;
+  *graph_exec = nullptr;
+  cudaStream_t s;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_check(b->ctx[0], e, "capture stream");
+  const long long step0 = b->step;
+  std::vector<long long> hs0;
+  for (m2c_ctx* c : b->ctx) hs0.push_back(c->host_step);
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  m2c_status st = M2C_OK;
+  if (e == cudaSuccess) st = batch_enqueue(b, nsteps, s);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  // the captured steps run when the graph is launched: the schedule counters advance then
+  b->step = step0;
+  for (size_t i = 0; i < b->ctx.size(); ++i) b->ctx[i]->host_step = hs0[i];
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess && st == M2C_OK && e2 == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(s);
+  if (st != M2C_OK) return st;
+  if (e != cudaSuccess || e2 != cudaSuccess) return cuda_check(b->ctx[0], e != cudaSuccess ? e : e2, "graph capture");
+  b->graph_steps = nsteps;
+  b->graph_phase = b->reinit_every > 0 ? step0 % b->reinit_every : 0;
+  *graph_exec = exec;
+  return M2C_OK;
+}
+
+m2c_status m2c_batch_launch_graph(m2c_batch* b, void* graph_exec) {
+  if (!b || !graph_exec) return M2C_EINVAL;
+  // the graph holds the reinitialisation schedule of the steps it captured
+  if (b->reinit_every > 0 && b->step % b->reinit_every != b->graph_phase)
+    return set_err(b->ctx[0], M2C_EINVAL, "graph launched at another phase of the reinitialisation schedule");
+  cudaError_t e = cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), b->stream);
+  if (e != cudaSuccess) return cuda_check(b->ctx[0], e, "graph launch");
+  b->step += b->graph_steps;
+  for (m2c_ctx* c : b->ctx) c->host_step += b->graph_steps;
+  return M2C_OK;
+}
+
+void m2c_graph_destroy(void* graph_exec) {
+  if (graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph_exec));
+}
+
+void m2c_batch_destroy(m2c_batch* b) { delete b; }
 
 m2c_status m2c_residual(m2c_ctx* c, double* R, double* L) {
   if (!c || !R || !L) return M2C_EINVAL;
@@ -1298,7 +1443,9 @@ m2c_status m2c_residual(m2c_ctx* c, double* R, double* L) {
   c->host.resL = L;
   m2c_status st = push_grid(c);
   if (st) return st;
-  cudaError_t e = launch_stage(c->host.prec, c->ty, c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), kResidual,
+  LaunchPlan lp;
+  lp.ty = c->ty;
+  cudaError_t e = launch_stage(c->host.prec, c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), kResidual, lp,
                                c->stream);
   if (e == cudaSuccess) {
     const dim3 lg((unsigned)(2 * sm_count()), 1);
@@ -1525,7 +1672,9 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
   cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(Ctrl), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dg, &g, sizeof(Grid), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles, sizeof(tiles), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = launch_stage(precision, ty, dg, dt, 1, tiles[1], kResidual, s);
+  LaunchPlan lp;
+  lp.ty = ty;
+  if (e == cudaSuccess) e = launch_stage(precision, dg, dt, 1, tiles[1], kResidual, lp, s);
   if (e == cudaSuccess) {
     const dim3 lg((unsigned)(2 * sm_count()), 1);
     k_fiver<<<lg, 128, 0, s>>>(dg, kResidual);

@@ -53,17 +53,25 @@ def lib():
         p, i, d, z, L_ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_long
         L.m2c_workspace_bytes.restype = z
         L.m2c_workspace_bytes.argtypes = [i, i, i, i]
-        L.m2c_batch_bytes.restype = z
-        L.m2c_batch_bytes.argtypes = [i]
+        L.m2c_batch_workspace_bytes.restype = z
+        L.m2c_batch_workspace_bytes.argtypes = [i]
+        L.m2c_batch_create.argtypes = [ctypes.POINTER(p), p, i, p, z, p]
+        L.m2c_batch_step.argtypes = [p, i]
+        L.m2c_batch_capture.argtypes = [p, i, ctypes.POINTER(p)]
+        L.m2c_batch_launch_graph.argtypes = [p, p]
+        L.m2c_graph_destroy.argtypes = [p]
+        L.m2c_graph_destroy.restype = None
+        L.m2c_batch_destroy.argtypes = [p]
+        L.m2c_batch_destroy.restype = None
         L.m2c_init_grid.argtypes = [ctypes.POINTER(p), i, i, i, p, d, p, i, p, z, p]
         L.m2c_set_eos.argtypes = [p, i, i, p, i]
         L.m2c_set_scheme.argtypes = [p, d, i, i]
+        L.m2c_set_tiling.argtypes = [p, i, i]
         L.m2c_set_state.argtypes = [p, p, p, d, L_]
         L.m2c_prims_to_state.argtypes = [p, p]
         L.m2c_upload_state.argtypes = [p, p, p]
         L.m2c_download_state.argtypes = [p, p, p]
         L.m2c_step.argtypes = [p, i]
-        L.m2c_step_batch.argtypes = [p, i, i, p, z]
         L.m2c_residual.argtypes = [p, p, p]
         L.m2c_sync.argtypes = [p, p, p, p]
         L.m2c_get_stats.argtypes = [p, ctypes.POINTER(Stats)]
@@ -123,8 +131,8 @@ def m2c_workspace_bytes(nx, ny, nz, precision=FP64) -> int:
     return lib().m2c_workspace_bytes(nx, ny, nz, precision)
 
 
-def m2c_batch_bytes(k) -> int:
-    return lib().m2c_batch_bytes(k)
+def m2c_batch_workspace_bytes(k) -> int:
+    return lib().m2c_batch_workspace_bytes(k)
 
 
 def m2c_solve_riemann(eosL, L, eosR, R, stream=None):
@@ -230,6 +238,9 @@ class Grid:
             _lib.m2c_destroy(ctx)
             self.ctx = None
 
+    def set_tiling(self, tile_rows=8, tile_z=0):
+        _check(lib().m2c_set_tiling(self.ctx, tile_rows, tile_z), "m2c_set_tiling", self.ctx)
+
     # -- state
     def set_state(self, W=None, phi=None, t=0.0, step=0):
         torch = self.torch
@@ -296,15 +307,47 @@ class Grid:
         return R, L
 
 
-def m2c_step_batch(grids, nsteps, batch_ws=None):
-    """Steps several Grid objects together (one launch per kernel for all)."""
-    import torch
-    k = len(grids)
-    nb = m2c_batch_bytes(k)
-    if batch_ws is None:
-        batch_ws = torch.empty(nb + 256, dtype=torch.uint8, device=grids[0].device)
-    off = (-batch_ws.data_ptr()) % 256
-    arr = (ctypes.c_void_p * k)(*[g.ctx.value for g in grids])
-    code = lib().m2c_step_batch(arr, k, nsteps, ctypes.c_void_p(batch_ws.data_ptr() + off), nb)
-    _check(code, "m2c_step_batch", grids[0].ctx)
-    return batch_ws
+class Batch:
+    """Several Grid contexts stepped together (one launch per kernel for all of them).
+    tuning = (tile rows 4|8, tile z-length (0 auto), schedule 0 static | 1 dynamic,
+    blocks per SM of a persistent grid (0 = one block per tile))."""
+
+    def __init__(self, grids, tuning=(8, 0, 0, 0)):
+        import torch
+        self.grids = list(grids)
+        k = len(self.grids)
+        nb = m2c_batch_workspace_bytes(k)
+        self.ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.grids[0].device)
+        off = (-self.ws.data_ptr()) % 256
+        arr = (ctypes.c_void_p * k)(*[g.ctx.value for g in self.grids])
+        tun = (ctypes.c_int * 4)(*tuning)
+        b = ctypes.c_void_p()
+        code = lib().m2c_batch_create(ctypes.byref(b), arr, k, ctypes.c_void_p(self.ws.data_ptr() + off), nb, tun)
+        _check(code, "m2c_batch_create", self.grids[0].ctx)
+        self.b = b
+        self.graph = None
+        self.graph_steps = 0
+
+    def step(self, nsteps):
+        _check(lib().m2c_batch_step(self.b, nsteps), "m2c_batch_step", self.grids[0].ctx)
+
+    def capture(self, nsteps):
+        if self.graph is not None:
+            lib().m2c_graph_destroy(self.graph)
+            self.graph = None
+        g = ctypes.c_void_p()
+        _check(lib().m2c_batch_capture(self.b, nsteps, ctypes.byref(g)), "m2c_batch_capture", self.grids[0].ctx)
+        self.graph = g
+        self.graph_steps = nsteps
+
+    def launch_graph(self):
+        _check(lib().m2c_batch_launch_graph(self.b, self.graph), "m2c_batch_launch_graph", self.grids[0].ctx)
+
+    def __del__(self):
+        if _lib is not None:
+            if getattr(self, "graph", None) is not None:
+                _lib.m2c_graph_destroy(self.graph)
+                self.graph = None
+            if getattr(self, "b", None) is not None:
+                _lib.m2c_batch_destroy(self.b)
+                self.b = None
