@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--workload", default="grid256", choices=["grid256", "batched", "served"])
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--jobs", type=int, default=200)
+    ap.add_argument("--serial-jobs", type=int, default=16)
+    ap.add_argument("--slice-steps", type=int, default=25)
     return ap.parse_args()
 
 
@@ -363,11 +366,48 @@ def run_batched(args):
                       "mixed": res["mixed"], "fp64": res["fp64"]}))
 
 
+def run_served(args):
+    """Poisson arrivals at 20 jobs/s of shock-bubble jobs (edge log-uniform on [48, 192], 100-1000
+    steps, seed 4) served with continuous batching in mixed precision; the first `--serial-jobs`
+    jobs of the trace are also served one at a time in plain FP64 and with continuous batching,
+    for a same-trace comparison."""
+    import torch
+    from paper_2508_16387_gb300 import m2c as M
+    from paper_2508_16387_gb300 import serve as S
+    from paper_2508_16387_gb300 import workloads as WL
+    torch.cuda.set_device(dist_env()[2])
+    M.lib()
+    jobs = WL.served_trace(n_jobs=args.jobs, rate=20.0, seed=4)
+
+    def summary(st):
+        ok = sum(1 for r in st.results if r.status == 0)
+        return {"jobs": len(st.results), "ok": ok, "wall_s": round(st.wall_s, 2),
+                "value": round(st.cell_updates / st.wall_s / 1e6, 2),
+                "p50_latency_s": round(st.percentile(50), 3), "p99_latency_s": round(st.percentile(99), 3),
+                "max_resident": st.max_resident, "slices": st.slices}
+    with ClockSampler(dist_env()[2]) as clk:
+        full = S.Server(precision=M.MIXED, slice_steps=args.slice_steps).run(jobs, realtime=True)
+    sub = jobs[:args.serial_jobs]
+    cont = S.Server(precision=M.MIXED, slice_steps=args.slice_steps).run(sub, realtime=True)
+    ser = S.serve_serial(sub, precision=M.FP64, realtime=True)
+    offered = sum(j.params.edge ** 3 * j.params.steps for j in jobs) / jobs[-1].arrival
+    out = {"metric": "served shock-bubble jobs: Mcell-updates/s and p50/p99 job latency",
+           "value": summary(full)["value"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f32+f64 (mixed)", "data": "synthetic",
+           "config": {"workload": f"served_{args.jobs}_jobs_poisson20_seed4", "slice_steps": args.slice_steps,
+                      "offered_Mcell_updates_per_s": round(offered / 1e6, 1)},
+           "served_mixed": summary(full), "clocks": clk.summary(),
+           f"first_{len(sub)}_jobs": {"continuous_mixed": summary(cont), "serial_fp64": summary(ser)}}
+    print(json.dumps(out))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batched":
         run_batched(a)
+    elif a.workload == "served":
+        run_served(a)
     else:
         run_ours(a)

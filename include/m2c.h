@@ -128,7 +128,7 @@ m2c_status m2c_step(m2c_ctx* ctx, int nsteps);
 /* Batches: several contexts of one precision stepped together, one launch per
  * kernel for all of them (the bulk kernel takes its tiles from all grids of
  * the batch, largest grid first; every grid keeps its own time step, error
- * latch and work lists). The reinitialisation schedule is the first context's.
+ * latch, work lists and reinitialisation schedule, counted from its own step).
  * workspace: caller's device buffer of m2c_batch_workspace_bytes(k) bytes,
  * 256-byte aligned, borrowed for the life of the batch. tuning (may be NULL) =
  * {tile rows 4 or 8, tile length along z (0: automatic), schedule (0: fixed
@@ -146,10 +146,8 @@ m2c_status m2c_batch_step(m2c_batch* b, int nsteps);
 
 /* Captures nsteps steps of the batch into a CUDA graph (instantiated, returned
  * as an opaque cudaGraphExec_t); m2c_batch_launch_graph launches it on the
- * batch's stream and advances the step counters; m2c_graph_destroy frees it.
- * A graph holds the reinitialisation schedule of the steps it captured: it may
- * be launched again only at the same phase of that schedule (M2C_EINVAL
- * otherwise), e.g. repeatedly when nsteps is a multiple of reinit_every. */
+ * batch's stream (any number of times: every grid reads its own step counter on
+ * the device) and advances the step counters; m2c_graph_destroy frees it. */
 m2c_status m2c_batch_capture(m2c_batch* b, int nsteps, void** graph_exec);
 m2c_status m2c_batch_launch_graph(m2c_batch* b, void* graph_exec);
 void m2c_graph_destroy(void* graph_exec);

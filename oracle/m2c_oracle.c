@@ -825,10 +825,12 @@ static void reinit(const or_grid_t* g, double* phi, int iters, double* phi0, dou
  * takes the arithmetic mean of the primitive states of its face neighbours
  * (order x-, x+, y-, y+, z-, z+) that were and still are of its new material,
  * converted with the new EOS; if there is none, the 26-neighbourhood (z, y, x
- * loops from -1 to 1) is used; if there is still none the step fails with
- * OR_ENONPHYS at that cell. */
-static int phase_fix(const or_grid_t* g, double* W, const unsigned char* id_old, const unsigned char* id_new,
-                     double* P, long* nflip, long* err_cell) {
+ * loops from -1 to 1) is used; if there is still none (a material fragment
+ * smaller than a cell, e.g. a level-set undershoot), the cell keeps its old
+ * material and state and its level set takes the old material's sign:
+ * phi = |phi| for material 0, phi = -max(|phi|, 1e-12 h) for material 1. */
+static int phase_fix(const or_grid_t* g, double* W, double* phi, const unsigned char* id_old,
+                     const unsigned char* id_new, double* P, long* nflip, long* err_cell) {
   long N = ncells(g);
   const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
   /* primitive states of the cells that keep their material */
@@ -879,7 +881,7 @@ static int phase_fix(const or_grid_t* g, double* W, const unsigned char* id_old,
               }
         }
         if (cnt == 0) {
-          record_error(OR_ENONPHYS, c, &err, &ec);
+          phi[c] = id_old[c] ? -fmax(fabs(phi[c]), 1e-12 * g->h) : fabs(phi[c]);
           continue;
         }
         double pr[5], w[5];
@@ -959,7 +961,7 @@ static int step_one(const or_grid_t* g, double* W, double* phi, long step_index,
   /* (6) phase update */
   for (long c = 0; c < N; ++c) wk->id2[c] = phi[c] < 0.0;
   long nf = 0;
-  st = phase_fix(g, W, wk->id, wk->id2, wk->P, &nf, &ec);
+  st = phase_fix(g, W, phi, wk->id, wk->id2, wk->P, &nf, &ec);
   stats->flipped = nf;
   if (st) stats->err_cell = ec;
   return st;

@@ -56,7 +56,8 @@ struct Grid {
   double* W1;       // stage-1 state
   double* phi1;
   double* phiC;     // reinitialisation scratch
-  uint8_t* id;      // bit 0: material at the start of the step; bit 1: first-layer flag
+  uint8_t* id;      // bit 0: material at the start of the step; bit 1: first-layer flag of the
+                    // reinitialisation; bit 2: material at the end of the step
   int* cell_slot;   // interface-cell list slot of a cell (valid only for listed cells)
   IfFace* faces;
   IfCell* cells;
@@ -67,6 +68,8 @@ struct Grid {
   double* resL;
   // tiling of the bulk stage kernel
   int tiles_x, tiles_y, tiles_z, tz;
+  // reinitialisation after every reinit_every-th step (0: never), reinit_iters iterations
+  int reinit_every, reinit_iters;
 };
 
 enum StageMode { kStage1 = 0, kStage2 = 1, kResidual = 2 };

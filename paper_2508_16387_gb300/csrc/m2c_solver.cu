@@ -428,6 +428,8 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
           const double pn = 0.5 * (G.phi[c] + (G.phi1[c] + dt * (double)Lphi));
           G.phi[c] = pn;
           flip = (pn < 0.0) != (id0 == 1);
+          // bit 2: material at the end of the step (read by the phase update)
+          G.id[c] = (uint8_t)(id0 | (pn < 0.0 ? 4 : 0));
           if (!is_if) {
 #pragma unroll
             for (int v = 0; v < 5; ++v) G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * (double)res[v]));
@@ -656,8 +658,11 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
 // phi' = phi - dtau S(phi0) (G(phi) - 1), Godunov upwind |grad phi|,
 // S = phi0/sqrt(phi0^2 + h^2), dtau = h/2, first-layer cells fixed.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, int it, int nits) {
+__global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, int it) {
   const Grid& G = grids[blockIdx.y];
+  // each grid follows its own schedule: after its steps reinit_every, 2 reinit_every, ...
+  const int nits = G.reinit_iters;
+  if (G.reinit_every <= 0 || it > nits || (G.ctrl->step + 1) % G.reinit_every != 0) return;
   // phi0 is the state phi; iterations alternate phi1 and phiC and the last one
   // writes phi (a single iteration ends in phi1 and is copied back)
   const double* __restrict__ src = it == 1 ? G.phi : ((it % 2 == 0) ? G.phi1 : G.phiC);
@@ -677,7 +682,7 @@ __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, 
       first = false;
 #pragma unroll
       for (int q = 0; q < 6; ++q) first = first || ((phi0[nb[q]] < 0.0) != s0);
-      G.id[c] = (uint8_t)((G.id[c] & 1) | (first ? 2 : 0));
+      G.id[c] = (uint8_t)((G.id[c] & 5) | (first ? 2 : 0));
     } else {
       first = (G.id[c] & 2) != 0;
     }
@@ -709,6 +714,7 @@ __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, 
 
 __global__ void k_copy_phi1(const Grid* __restrict__ grids) {
   const Grid& G = grids[blockIdx.y];
+  if (G.reinit_every <= 0 || G.reinit_iters != 1 || (G.ctrl->step + 1) % G.reinit_every != 0) return;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x)
     G.phi[c] = G.phi1[c];
 }
@@ -716,7 +722,9 @@ __global__ void k_copy_phi1(const Grid* __restrict__ grids) {
 // ---------------------------------------------------------------------------
 // Phase update (Sec. 2.3 step (6)): a cell whose material changed takes the
 // mean primitive state of its face neighbours that were and are of its new
-// material, else of its 26-neighbourhood, converted with the new EOS.
+// material, else of its 26-neighbourhood, converted with the new EOS. With no
+// such neighbour at all (a fragment smaller than a cell) the cell keeps its
+// material and state, and its level set takes that material's sign.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grids) {
   __shared__ double s_red[32];
@@ -728,13 +736,13 @@ __global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grid
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const long long c = G.flips[t];
     const int i = (int)(c % G.nx), j = (int)((c / G.nx) % G.ny), k = (int)(c / ((long long)G.nx * G.ny));
-    const int m = (G.phi[c] < 0.0) ? 1 : 0;
+    const int m = (G.id[c] >> 2) & 1;  // material at the end of the step
     const EosDev& q = G.eos[m];
     double sum[5] = {0, 0, 0, 0, 0};
     int cnt = 0;
     auto take = [&](long long nb) {
       const int old_id = G.id[nb] & 1;
-      const int new_id = G.phi[nb] < 0.0 ? 1 : 0;
+      const int new_id = (G.id[nb] >> 2) & 1;
       if (old_id == m && new_id == m) {
         double P[5];
         if (!cons_to_prim<double>(q, q, G.W, N, nb, P)) latch_error(ctrl, M2C_ENONPHYS, nb);
@@ -756,7 +764,13 @@ __global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grid
             if (di || dj || dk) take(cell_of(G, i + di, j + dj, k + dk));
     }
     if (cnt == 0) {
-      latch_error(ctrl, M2C_ENONPHYS, c);
+      const int old_id = 1 - m;
+      const double pv = G.phi[c];
+      G.phi[c] = old_id ? -fmax(fabs(pv), 1e-12 * G.h) : fabs(pv);
+      bool ok;
+      const double lam = wave_sum(G, G.eos[old_id], G.W, N, c, ok);
+      if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
+      lam_max = fmax(lam_max, lam);
       continue;
     }
     double P[5];
@@ -1037,6 +1051,8 @@ cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s) {
   return e;
 }
 
+// reinit: enqueue the reinitialisation kernels (each grid decides on the device
+// whether its own step is due); reinit_iters: the largest iteration count.
 cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int ngrid, long long ntiles, int prec,
                          const LaunchPlan& lp, bool reinit, int reinit_iters, long long nmax, cudaStream_t s,
                          StageEvents* pe = nullptr) {
@@ -1053,8 +1069,8 @@ cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int 
   }
   if (reinit && reinit_iters > 0) {
     const dim3 rg((unsigned)std::min<long long>((nmax + 255) / 256, 8ll * sm_count()), (unsigned)ngrid);
-    for (int it = 1; it <= reinit_iters; ++it) k_reinit<<<rg, 256, 0, s>>>(dev_grids, it, reinit_iters);
-    if (reinit_iters == 1) k_copy_phi1<<<rg, 256, 0, s>>>(dev_grids);
+    for (int it = 1; it <= reinit_iters; ++it) k_reinit<<<rg, 256, 0, s>>>(dev_grids, it);
+    k_copy_phi1<<<rg, 256, 0, s>>>(dev_grids);
   }
   k_phase_fix<<<lg, 128, 0, s>>>(dev_grids);
   k_end_step<<<(ngrid + 63) / 64, 64, 0, s>>>(dev_grids, ngrid);
@@ -1097,7 +1113,6 @@ struct m2c_batch {
   cudaStream_t stream = nullptr;
   long long step = 0, nmax = 1;
   int reinit_every = 10, reinit_iters = 5, graph_steps = 0;
-  long long graph_phase = 0;  // step index modulo the reinitialisation period at capture
 };
 
 extern "C" {
@@ -1167,6 +1182,8 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   set_tiling(g, c->ty, default_tz(g, c->ty));
   c->reinit_every = 10;
   c->reinit_iters = 5;
+  g.reinit_every = 10;
+  g.reinit_iters = 5;
   c->host_step = 0;
   c->has_state = false;
   c->eos_set[0] = c->eos_set[1] = false;
@@ -1215,6 +1232,8 @@ m2c_status m2c_set_scheme(m2c_ctx* c, double cfl, int reinit_every, int reinit_i
   c->host.cfl = cfl;
   c->reinit_every = reinit_every;
   c->reinit_iters = reinit_iters;
+  c->host.reinit_every = reinit_every;
+  c->host.reinit_iters = reinit_iters;
   return push_grid(c);
 }
 
@@ -1350,7 +1369,9 @@ m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace
   b->stream = v[0]->stream;
   b->step = v[0]->host_step;
   b->reinit_every = v[0]->reinit_every;
-  b->reinit_iters = v[0]->reinit_iters;
+  b->reinit_iters = 0;
+  for (int i = 0; i < k; ++i)
+    if (v[i]->reinit_every > 0) b->reinit_iters = std::max(b->reinit_iters, v[i]->reinit_iters);
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < k && e == cudaSuccess; ++i) {
     m2c_ctx* c = b->ctx[i];
@@ -1375,8 +1396,10 @@ m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace
 static m2c_status batch_enqueue(m2c_batch* b, int nsteps, cudaStream_t s) {
   const int k = (int)b->ctx.size();
   for (int n = 0; n < nsteps; ++n) {
-    const bool re = b->reinit_every > 0 && (b->step + 1) % b->reinit_every == 0;
-    cudaError_t e = enqueue_step(b->dev, b->dtiles, k, b->tiles[k], b->prec, b->lp, re, b->reinit_iters, b->nmax, s);
+    // grids of a batch may be at different steps: the reinitialisation kernels
+    // are enqueued every step and each grid checks its own schedule
+    cudaError_t e = enqueue_step(b->dev, b->dtiles, k, b->tiles[k], b->prec, b->lp, b->reinit_iters > 0,
+                                 b->reinit_iters, b->nmax, s);
     if (e != cudaSuccess) return cuda_check(b->ctx[0], e, "batch step launch");
     ++b->step;
     for (m2c_ctx* c : b->ctx) ++c->host_step;
@@ -1413,16 +1436,12 @@ m2c_status m2c_batch_capture(m2c_batch* b, int nsteps, void** graph_exec) {
   if (st != M2C_OK) return st;
   if (e != cudaSuccess || e2 != cudaSuccess) return cuda_check(b->ctx[0], e != cudaSuccess ? e : e2, "graph capture");
   b->graph_steps = nsteps;
-  b->graph_phase = b->reinit_every > 0 ? step0 % b->reinit_every : 0;
   *graph_exec = exec;
   return M2C_OK;
 }
 
 m2c_status m2c_batch_launch_graph(m2c_batch* b, void* graph_exec) {
   if (!b || !graph_exec) return M2C_EINVAL;
-  // the graph holds the reinitialisation schedule of the steps it captured
-  if (b->reinit_every > 0 && b->step % b->reinit_every != b->graph_phase)
-    return set_err(b->ctx[0], M2C_EINVAL, "graph launched at another phase of the reinitialisation schedule");
   cudaError_t e = cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), b->stream);
   if (e != cudaSuccess) return cuda_check(b->ctx[0], e, "graph launch");
   b->step += b->graph_steps;

@@ -231,3 +231,36 @@ def random_state(n: tuple, seed: int, eos=(WATER_SG, AIR_PG), two_phase: bool = 
             P[v][sel] = (vel[m] * noise[v])[sel]
         P[4][sel] = (p0 * (1.0 + amp * noise[4]))[sel]
     return P, phi
+
+
+def shock_bubble_device(n: int, radius: float, centre, p_shock: float, x_shock: float = 0.2, device="cuda"):
+    """The fields of shock_bubble() built directly in device memory (torch, float64), for
+    servers that create many grids: (phi, region) tensors of shape (n, n, n). The same
+    formulas as shock_bubble(), so the fields are identical."""
+    import torch
+    h = 1.0 / n
+    c = (torch.arange(n, dtype=torch.float64, device=device) + 0.5) * h
+    z, y, x = torch.meshgrid(c, c, c, indexing="ij")
+    phi = torch.sqrt((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2) - radius
+    region = torch.full(phi.shape, AMBIENT, dtype=torch.uint8, device=device)
+    region[x < x_shock] = SHOCKED
+    region[phi < 0.0] = BUBBLE
+    return phi, region
+
+
+def prims_device(region, prims_by_region: dict, shocked_state=None, p_shock: float = 0.0):
+    """Primitive fields (5, nz, ny, nx) on the device from a region map (see Setup.prims)."""
+    import torch
+    P = torch.zeros((5,) + tuple(region.shape), dtype=torch.float64, device=region.device)
+    for r, q in prims_by_region.items():
+        m = region == r
+        for v in range(5):
+            P[v][m] = q[v]
+    if shocked_state is not None:
+        m = region == SHOCKED
+        P[0][m] = shocked_state[0]
+        P[1][m] = shocked_state[1]
+        P[2][m] = 0.0
+        P[3][m] = 0.0
+        P[4][m] = p_shock
+    return P

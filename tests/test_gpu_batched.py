@@ -54,18 +54,21 @@ def test_graph_replay_equals_eager(env):
     be.step(20)
     graphed = [RN.grid_for(s, 1) for s in setups]
     bg = M.Batch(graphed, (8, 0, 1, 2))
-    bg.capture(10)       # one reinitialisation period
+    bg.capture(10)
     bg.launch_graph()
-    bg.launch_graph()    # replayed at the same phase of the schedule
+    bg.launch_graph()
     for a, b in zip(eager, graphed):
         ta, ka = a.sync()
         tb, kb = b.sync()
         assert ka == kb == 20 and ta == tb
         assert np.array_equal(a.W.cpu().numpy(), b.W.cpu().numpy())
     bg.capture(3)
-    bg.launch_graph()    # steps 20-22
-    with pytest.raises(M.M2CError):
-        bg.launch_graph()  # steps 23-25 are at another phase
+    for _ in range(4):   # steps 20-31, reinitialisation after step 29 read on the device
+        bg.launch_graph()
+    be.step(12)
+    for a, b in zip(eager, graphed):
+        assert a.sync() == b.sync()
+        assert np.array_equal(a.phi.cpu().numpy(), b.phi.cpu().numpy())
 
 
 def test_autotuner_restores_state(env):
@@ -79,4 +82,26 @@ def test_autotuner_restores_state(env):
     for g, w in zip(grids, W0):
         t, k = g.sync()
         assert k == 0 and t == 0.0
+        assert np.array_equal(g.W.cpu().numpy(), w)
+
+
+def test_grids_at_different_steps_batch_like_alone(env):
+    """A grid that joins a batch at another step keeps its own reinitialisation schedule."""
+    M, RN = env
+    setups = small_batch()[:3]
+    alone = []
+    for s in setups:
+        g = RN.grid_for(s, 0)
+        g.step(17)
+        g.sync()
+        alone.append(g.W.cpu().numpy())
+    grids = [RN.grid_for(s, 0) for s in setups]
+    grids[0].step(7)          # grid 0 runs ahead by 7 steps, then all step together
+    grids[1].step(3)
+    b = M.Batch(grids, (8, 0, 0, 0))
+    b.step(10)
+    grids[1].step(4)
+    grids[2].step(7)
+    for g, w in zip(grids, alone):
+        assert g.sync()[1] == 17
         assert np.array_equal(g.W.cpu().numpy(), w)

@@ -251,3 +251,16 @@ def test_mixed_precision_l1_error_against_fp64(m2c):
     e_p = _block_l1(P32[4], P64[4])
     assert e_rho <= 1e-4 and e_p <= 1e-4, (e_rho, e_p)
     assert (out[0][1] < 0).sum() > 0
+
+
+def test_isolated_flip_matches_oracle(m2c):
+    from tests.test_oracle_pins import _undershoot_setup
+    s, P = _undershoot_setup()
+    g_or, W0 = oracle_start(s, P)
+    ref = O.run(g_or, W0, s.phi, 1)
+    g = gpu_start(m2c, s, prims=P)
+    g.step(1)
+    g.sync()
+    assert np.array_equal(g.phi.cpu().numpy() < 0, ref.phi < 0)
+    assert np.abs(g.phi.cpu().numpy() - ref.phi).max() <= 1e-12
+    assert max(rel_err(g.W.cpu().numpy(), ref.W)) <= TOL

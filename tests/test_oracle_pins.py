@@ -479,3 +479,32 @@ def test_phase_update_follows_translating_interface():
     xi = x[np.argmax(r.phi[0, 0] >= 0.0)]
     assert abs(xi - (0.5 + 100.0 * r.t)) <= 1.0 / nx
     assert r.stats["flipped"] > 0
+
+
+def _undershoot_setup():
+    """A 1D periodic water column in slow uniform flow whose level set has a small positive
+    value next to a steep profile, so that the third-order stencil drives that one cell
+    negative while every neighbour stays positive: a would-be air cell with no air around."""
+    n = (16, 1, 1)
+    phi = np.full((1, 1, 16), 10.0)
+    phi[0, 0, 6] = 0.1
+    phi[0, 0, 7] = 0.01
+    P = np.zeros((5, 1, 1, 16))
+    P[0] = 1000.0
+    P[1] = 20.0
+    P[4] = 1e8
+    s = WL.Setup("undershoot", n, 1.0 / 16, (WL.WATER_SG, WL.AIR_PG), (1,) * 6, phi,
+                 np.zeros(phi.shape, np.uint8), {}, reinit_every=0)
+    return s, P
+
+
+def test_isolated_flip_keeps_its_material():
+    s, P = _undershoot_setup()
+    g = _grid(s, reinit_every=0)
+    W = O.prims_to_cons(g, P, s.phi)
+    R, L, _ = O.residual(g, W, s.phi)
+    assert L[0, 0, 7] * O.time_step(g, W, s.phi) < -0.01   # the level set alone would go negative
+    r = O.run(g, W, s.phi, 1)
+    assert r.stats["flipped"] == 1
+    assert np.all(r.phi >= 0.0)                              # no sub-cell air fragment is created
+    assert np.allclose(r.W, W, rtol=1e-14)                   # uniform water state untouched
