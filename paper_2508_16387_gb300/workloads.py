@@ -7,7 +7,7 @@ needs the equation of state, the post-shock Rankine-Hugoniot state, is left as
 a hole (region ``SHOCKED``) that each consumer fills with its own solver.
 
 Workloads (the shock-bubble family restates the shock-induced bubble collapse
-problem of the paper's Sec. 5.6 on a Cartesian box):
+problem of the paper's Sec. 5.5 on a Cartesian box):
 
 * ``shock_tube``: 1D two-material shock tube on nx x 4 x 4 cells, water
   (stiffened gas) at 1e9 Pa for x < 0.5 and air at 1e5 Pa for x > 0.5,
