@@ -78,6 +78,45 @@ __device__ __forceinline__ R rsqrt_pos(R x) {  // sqrt of x > 0
   else return x * rsqrtf(x);
 }
 
+// Exact IEEE-754 binary64 <-> binary32 conversions written with integer
+// operations (from the bit layout of the two formats), for the mixed-precision
+// loads and updates: GB300 runs its conversion instructions on the narrow
+// FP64 pipe. Values outside the normal binary32 range fall back to the
+// hardware conversion. d2f rounds to nearest, ties to even.
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long a = b & 0x7fffffffffffffffull;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  if (a >= 0x3810000000000000ull && a < 0x47efffffe0000000ull) {
+    const unsigned long long m = a - 0x3800000000000000ull;        // exponent bias 1023 -> 127
+    const unsigned long long r = m + 0x0fffffffull + ((m >> 29) & 1ull);
+    return __uint_as_float((unsigned)(r >> 29) | sign);
+  }
+  if (a == 0ull) return __uint_as_float(sign);
+  return (float)x;
+}
+
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned f = __float_as_uint(x);
+  const unsigned a = f & 0x7fffffffu;
+  const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
+  if (a >= 0x00800000u && a < 0x7f800000u)
+    return __longlong_as_double((long long)((((unsigned long long)a + (896ull << 23)) << 29) | sign));
+  if (a == 0u) return __longlong_as_double((long long)sign);
+  return (double)x;
+}
+
+template <typename R>
+__device__ __forceinline__ R to_r(double x) {
+  if constexpr (sizeof(R) == 8) return x;
+  else return d2f(x);
+}
+template <typename R>
+__device__ __forceinline__ double to_d(R x) {
+  if constexpr (sizeof(R) == 8) return x;
+  else return f2d(x);
+}
+
 // Reference curves p_R, p_R', e_R, e_R' at strain eta (App. B.3); "p_H" in the
 // compression e_R is read as p_R.
 template <typename R>

@@ -52,18 +52,18 @@ __device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd,
     P[0] = rho; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
     return ok && rho > 0.0;
   } else {
-    const float rf = (float)rho;
+    const float rf = d2f(rho);
     const float inv = rrcp<float>(rf);
-    const float f1 = (float)m1, f2 = (float)m2, f3 = (float)m3;
+    const float f1 = d2f(m1), f2 = d2f(m2), f3 = d2f(m3);
     const float u = f1 * inv, v = f2 * inv, w = f3 * inv;
     const float ke = 0.5f * ((f1 * u + f2 * v) + f3 * w);
-    const double rhoe = E - (double)ke;
+    const double rhoe = E - f2d(ke);
     float p = 0.0f;
     bool ok = true;
     if (q.type == M2C_EOS_SG) {
-      p = (float)(qd.gm1 * rhoe - qd.gpc);
+      p = d2f(qd.gm1 * rhoe - qd.gpc);
     } else {
-      ok = eos_p<float>(q, rf, inv, (float)rhoe * inv, p);
+      ok = eos_p<float>(q, rf, inv, d2f(rhoe) * inv, p);
     }
     P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
     return ok && rho > 0.0;
@@ -174,8 +174,11 @@ struct StageSmem {
   static constexpr size_t bytes = eosd_off + sizeof(EosDev) * 2;
 };
 
+// FP64 tiles run one block per SM (FP64-pipe bound); the FP32 tiles of the
+// mixed path are latency bound and run four 256-thread blocks per SM (their
+// shared memory, 55 KB, allows four).
 template <typename R, int TY>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, (sizeof(R) == 8 ? 1 : 4))
 k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, long long ntiles, int mode,
         int sched, unsigned long long* __restrict__ tile_counter) {
   constexpr int TX = 32, NT = TX * TY, HX = TX + 4, HY = TY + 4;
@@ -242,7 +245,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     const long long c = cell_of(G, i, j, k);
     const double phd = phis[c];
     idv = mode == kStage2 ? (G.id[c] & 1) : (phd < 0.0 ? 1 : 0);
-    ph = (R)phd;
+    ph = to_r<R>(phd);
     if (!cons_to_prim<R>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) latch_error(ctrl, M2C_ENONPHYS, c);
   };
 
@@ -312,68 +315,72 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     }
     __syncthreads();
 
-    // ---- MUSCL face states along x (cells x = -1 .. TX) and y (cells y = -1 .. TY)
-    for (int i = tid; i < (TX + 2) * TY; i += NT) {
-      const int xs = i % (TX + 2), row = i / (TX + 2);
-      const int hx = xs + 1, hy = row + 2;
+    // ---- MUSCL face states along x (cells x = -1 .. TX) and y (cells y = -1 .. TY), one loop
+    constexpr int NXS = (TX + 2) * TY, NYS = TX * (TY + 2);
+    for (int i = tid; i < NXS + NYS; i += NT) {
+      int hx, hy, so, ss;  // centre in the plane buffer, stencil stride, output slot
+      FaceState<R>* out;
+      if (i < NXS) {
+        const int xs = i % (TX + 2), row = i / (TX + 2);
+        hx = xs + 1;
+        hy = row + 2;
+        so = 1;
+        out = s_xs + (row * (TX + 2) + xs) * 2;
+        ss = 0;
+      } else {
+        const int j = i - NXS;
+        const int x = j % TX, ys = j / TX;
+        hx = x + 2;
+        hy = ys + 1;
+        so = HX;
+        out = s_ys + (ys * TX + x) * 2;
+        ss = 1;
+      }
+      const int c0 = hy * HX + hx;
       R Pm[5], P[5], Pp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        Pm[v] = s_q[(v * HY + hy) * HX + hx - 1];
-        P[v] = s_q[(v * HY + hy) * HX + hx];
-        Pp[v] = s_q[(v * HY + hy) * HX + hx + 1];
+        Pm[v] = s_q[v * HY * HX + c0 - so];
+        P[v] = s_q[v * HY * HX + c0];
+        Pp[v] = s_q[v * HY * HX + c0 + so];
       }
-      const int ic = s_id[hy * HX + hx];
-      const bool same = s_id[hy * HX + hx - 1] == ic && s_id[hy * HX + hx + 1] == ic;
+      const int ic = s_id[c0];
+      const bool same = s_id[c0 - so] == ic && s_id[c0 + so] == ic;
       bool b = false;
-      cell_faces<R>(s_eos[ic], Pm, P, Pp, same, s_xs[(row * (TX + 2) + xs) * 2 + 0],
-                    s_xs[(row * (TX + 2) + xs) * 2 + 1], b);
-      if (b) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, x0 + xs - 1, y0 + row, k));
-    }
-    for (int i = tid; i < TX * (TY + 2); i += NT) {
-      const int x = i % TX, ys = i / TX;
-      const int hx = x + 2, hy = ys + 1;
-      R Pm[5], P[5], Pp[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Pm[v] = s_q[(v * HY + hy - 1) * HX + hx];
-        P[v] = s_q[(v * HY + hy) * HX + hx];
-        Pp[v] = s_q[(v * HY + hy + 1) * HX + hx];
-      }
-      const int ic = s_id[hy * HX + hx];
-      const bool same = s_id[(hy - 1) * HX + hx] == ic && s_id[(hy + 1) * HX + hx] == ic;
-      bool b = false;
-      cell_faces<R>(s_eos[ic], Pm, P, Pp, same, s_ys[(ys * TX + x) * 2 + 0], s_ys[(ys * TX + x) * 2 + 1], b);
-      if (b) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, x0 + x, y0 + ys - 1, k));
+      cell_faces<R>(s_eos[ic], Pm, P, Pp, same, out[0], out[1], b);
+      if (b) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, x0 + hx - 2, y0 + hy - 2, k));
+      (void)ss;
     }
     __syncthreads();
 
-    // ---- HLLC on every x face (f between cells f-1 and f) and y face of the tile
-    for (int i = tid; i < (TX + 1) * TY; i += NT) {
-      const int f = i % (TX + 1), row = i / (TX + 1);
+    // ---- HLLC on every x face (f between cells f-1 and f) and y face of the tile, one loop
+    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+    for (int i = tid; i < NXF + NYF; i += NT) {
       R F[5];
-      const int il = s_id[(row + 2) * HX + f + 1], ir = s_id[(row + 2) * HX + f + 2];
-      if (il == ir) {
-        hllc<0, R>(s_xs[(row * (TX + 2) + f) * 2 + 1], s_xs[(row * (TX + 2) + f + 1) * 2 + 0], F);
+      if (i < NXF) {
+        const int f = i % (TX + 1), row = i / (TX + 1);
+        const int il = s_id[(row + 2) * HX + f + 1], ir = s_id[(row + 2) * HX + f + 2];
+        if (il == ir) {
+          hllc<0, R>(s_xs[(row * (TX + 2) + f) * 2 + 1], s_xs[(row * (TX + 2) + f + 1) * 2 + 0], F);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) F[v] = (R)0;
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s_fx[(v * TY + row) * (TX + 1) + f] = F[v];
       } else {
+        const int j = i - NXF;
+        const int x = j % TX, f = j / TX;
+        const int il = s_id[(f + 1) * HX + x + 2], ir = s_id[(f + 2) * HX + x + 2];
+        if (il == ir) {
+          hllc<1, R>(s_ys[(f * TX + x) * 2 + 1], s_ys[((f + 1) * TX + x) * 2 + 0], F);
+        } else {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) F[v] = (R)0;
+          for (int v = 0; v < 5; ++v) F[v] = (R)0;
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) s_fy[(v * (TY + 1) + f) * TX + x] = F[v];
       }
-#pragma unroll
-      for (int v = 0; v < 5; ++v) s_fx[(v * TY + row) * (TX + 1) + f] = F[v];
-    }
-    for (int i = tid; i < TX * (TY + 1); i += NT) {
-      const int x = i % TX, f = i / TX;
-      R F[5];
-      const int il = s_id[(f + 1) * HX + x + 2], ir = s_id[(f + 2) * HX + x + 2];
-      if (il == ir) {
-        hllc<1, R>(s_ys[(f * TX + x) * 2 + 1], s_ys[((f + 1) * TX + x) * 2 + 0], F);
-      } else {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) F[v] = (R)0;
-      }
-#pragma unroll
-      for (int v = 0; v < 5; ++v) s_fy[(v * (TY + 1) + f) * TX + x] = F[v];
     }
     __syncthreads();
 
@@ -413,26 +420,27 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
         if (mode == kResidual) {
           if (!is_if) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) G.resR[v * N + c] = (double)res[v];
+            for (int v = 0; v < 5; ++v) G.resR[v * N + c] = to_d<R>(res[v]);
           }
-          G.resL[c] = (double)Lphi;
+          G.resL[c] = to_d<R>(Lphi);
           G.id[c] = (uint8_t)id0;
         } else if (mode == kStage1) {
-          G.phi1[c] = G.phi[c] + dt * (double)Lphi;
+          G.phi1[c] = G.phi[c] + dt * to_d<R>(Lphi);
           G.id[c] = (uint8_t)id0;
           if (!is_if) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) G.W1[v * N + c] = G.W[v * N + c] + dt * (double)res[v];
+            for (int v = 0; v < 5; ++v) G.W1[v * N + c] = G.W[v * N + c] + dt * to_d<R>(res[v]);
           }
         } else {
-          const double pn = 0.5 * (G.phi[c] + (G.phi1[c] + dt * (double)Lphi));
+          const double pn = 0.5 * (G.phi[c] + (G.phi1[c] + dt * to_d<R>(Lphi)));
           G.phi[c] = pn;
           flip = (pn < 0.0) != (id0 == 1);
           // bit 2: material at the end of the step (read by the phase update)
           G.id[c] = (uint8_t)(id0 | (pn < 0.0 ? 4 : 0));
           if (!is_if) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * (double)res[v]));
+            for (int v = 0; v < 5; ++v)
+              G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * to_d<R>(res[v])));
             if (!flip) {
               bool ok;
               const double lam = wave_sum_r<R>(G, s_eos[id0], s_eosd[id0], G.W, N, c, ok);
@@ -459,12 +467,12 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
               e->cell = c;
 #pragma unroll
               for (int v = 0; v < 5; ++v) {
-                e->F[0][v] = (double)Fxm[v];
-                e->F[1][v] = (double)Fxp[v];
-                e->F[2][v] = (double)Fym[v];
-                e->F[3][v] = (double)Fyp[v];
-                e->F[4][v] = (double)Fzm[v];
-                e->F[5][v] = (double)Fzp[v];
+                e->F[0][v] = to_d<R>(Fxm[v]);
+                e->F[1][v] = to_d<R>(Fxp[v]);
+                e->F[2][v] = to_d<R>(Fym[v]);
+                e->F[3][v] = to_d<R>(Fyp[v]);
+                e->F[4][v] = to_d<R>(Fzm[v]);
+                e->F[5][v] = to_d<R>(Fzp[v]);
               }
               G.cell_slot[c] = s;
             } else {
@@ -1018,37 +1026,15 @@ m2c_status push_grid(m2c_ctx* c) {
   return cuda_check(c, e, "descriptor upload");
 }
 
-// Default tile z-chunk: long enough to amortise the z warm-up, short enough
-// to give every SM several blocks.
+// Default tile z-chunk: 64, 32 or 16 planes, the longest that still gives the
+// SMs 16 tiles each (the z warm-up of a chunk costs about four planes of
+// loads); short grids take one chunk.
 int default_tz(const Grid& g, int ty) {
   const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + ty - 1) / ty);
-  const long long want = 4ll * sm_count();
-  int tz = g.nz;
-  while (tz > 8 && cols * ((g.nz + tz - 1) / tz) < want) tz = (tz + 1) / 2;
-  return tz;
-}
-
-// Enqueues one time step for ngrid grids described at dev_grids.
-struct StageEvents {
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev;
-  size_t* used;
-};
-
-cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s) {
-  if (!pe) return cudaSuccess;
-  if (start) {
-    if (*pe->used == pe->ev->size()) {
-      cudaEvent_t a, b;
-      cudaError_t e = cudaEventCreate(&a);
-      if (e == cudaSuccess) e = cudaEventCreate(&b);
-      if (e != cudaSuccess) return e;
-      pe->ev->push_back({a, b});
-    }
-    return cudaEventRecord((*pe->ev)[*pe->used].first, s);
-  }
-  cudaError_t e = cudaEventRecord((*pe->ev)[*pe->used].second, s);
-  ++*pe->used;
-  return e;
+  const long long want = 16ll * sm_count();
+  for (int tz : {64, 32})
+    if (g.nz > tz && cols * ((g.nz + tz - 1) / tz) >= want) return tz;
+  return g.nz > 16 ? 16 : g.nz;
 }
 
 // reinit: enqueue the reinitialisation kernels (each grid decides on the device
