@@ -1037,6 +1037,28 @@ int default_tz(const Grid& g, int ty) {
   return g.nz > 16 ? 16 : g.nz;
 }
 
+struct StageEvents {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev;
+  size_t* used;
+};
+
+cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s) {
+  if (!pe) return cudaSuccess;
+  if (start) {
+    if (*pe->used == pe->ev->size()) {
+      cudaEvent_t a, b;
+      cudaError_t e = cudaEventCreate(&a);
+      if (e == cudaSuccess) e = cudaEventCreate(&b);
+      if (e != cudaSuccess) return e;
+      pe->ev->push_back({a, b});
+    }
+    return cudaEventRecord((*pe->ev)[*pe->used].first, s);
+  }
+  cudaError_t e = cudaEventRecord((*pe->ev)[*pe->used].second, s);
+  ++*pe->used;
+  return e;
+}
+
 // reinit: enqueue the reinitialisation kernels (each grid decides on the device
 // whether its own step is due); reinit_iters: the largest iteration count.
 cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int ngrid, long long ntiles, int prec,
