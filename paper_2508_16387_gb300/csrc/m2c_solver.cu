@@ -177,17 +177,25 @@ struct StageSmem {
 // FP64 tiles run one block per SM (FP64-pipe bound); the FP32 tiles of the
 // mixed path are latency bound and run four 256-thread blocks per SM (their
 // shared memory, 55 KB, allows four).
+//
+// Every thread's share of the plane work (halo cell, face-state items, flux
+// items) and its shared-memory addresses are fixed for the whole launch and
+// computed once; only the plane index changes along the march.
 template <typename R, int TY>
 __global__ void __launch_bounds__(32 * TY, (sizeof(R) == 8 ? 1 : 4))
 k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, long long ntiles, int mode,
         int sched, unsigned long long* __restrict__ tile_counter) {
-  constexpr int TX = 32, NT = TX * TY, HX = TX + 4, HY = TY + 4;
+  constexpr int TX = 32, NT = TX * TY, HX = TX + 4, HY = TY + 4, PL = HY * HX;
+  constexpr int NXS = (TX + 2) * TY, NYS = TX * (TY + 2), NS = NXS + NYS;  // face-state items
+  constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1), NF = NXF + NYF;  // flux items
+  constexpr int NHALO = 4 * (TX + TY);
+  constexpr int SI = (NS + NT - 1) / NT, FI = (NF + NT - 1) / NT;
+  constexpr int SFX = TY * (TX + 1), SFY = (TY + 1) * TX;                   // flux array strides
   using SM = StageSmem<R, TY>;
   extern __shared__ __align__(16) unsigned char smem[];
   R* s_q = reinterpret_cast<R*>(smem + SM::q_off);                         // [5][HY][HX]
   R* s_phi = reinterpret_cast<R*>(smem + SM::phi_off);                     // [HY][HX]
-  FaceState<R>* s_xs = reinterpret_cast<FaceState<R>*>(smem + SM::xs_off);  // [TY][TX+2][2]
-  FaceState<R>* s_ys = reinterpret_cast<FaceState<R>*>(smem + SM::ys_off);  // [TY+2][TX][2]
+  FaceState<R>* s_st = reinterpret_cast<FaceState<R>*>(smem + SM::xs_off);  // x: [TY][TX+2][2], then y: [TY+2][TX][2]
   R* s_fx = reinterpret_cast<R*>(smem + SM::fx_off);                       // [5][TY][TX+1]
   R* s_fy = reinterpret_cast<R*>(smem + SM::fy_off);                       // [5][TY+1][TX]
   uint8_t* s_id = smem + SM::id_off;                                       // [HY][HX]
@@ -195,9 +203,63 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   EosDev* s_eosd = reinterpret_cast<EosDev*>(smem + SM::eosd_off);
   __shared__ double s_dt;
   __shared__ double s_red[32];
+  __shared__ long long s_tile;
 
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-  __shared__ long long s_tile;
+  const unsigned lane = tid & 31, lt = (1u << lane) - 1u;
+
+  // face-state items, packed: centre in the plane buffer (bits 0-9), stencil along y (bit 10); -1: none
+  int st_item[SI];
+#pragma unroll
+  for (int s = 0; s < SI; ++s) {
+    const int i = tid + s * NT;
+    st_item[s] = -1;
+    if (i < NXS) {
+      st_item[s] = (i / (TX + 2) + 2) * HX + i % (TX + 2) + 1;
+    } else if (i < NS) {
+      const int j = i - NXS;
+      st_item[s] = ((j / TX + 1) * HX + j % TX + 2) | (1 << 10);
+    }
+  }
+  // flux items, packed: left face state (bits 0-10), id position of the left cell (11-19),
+  // output offset (20-28), direction y (bit 30); -1: none
+  int fl_item[FI];
+#pragma unroll
+  for (int s = 0; s < FI; ++s) {
+    const int i = tid + s * NT;
+    fl_item[s] = -1;
+    if (i < NXF) {
+      const int f = i % (TX + 1), row = i / (TX + 1);
+      fl_item[s] = (2 * (row * (TX + 2) + f) + 1) | (((row + 2) * HX + f + 1) << 11) | ((row * (TX + 1) + f) << 20);
+    } else if (i < NF) {
+      const int j = i - NXF;
+      const int x = j % TX, f = j / TX;
+      fl_item[s] = (2 * NXS + 2 * (f * TX + x) + 1) | (((f + 1) * HX + x + 2) << 11) | ((f * TX + x) << 20) |
+                   (1 << 30);
+    }
+  }
+  static_assert(2 * NS < 2048 && PL < 512 && SFX < 512 && SFY < 512, "packed item fields");
+  // halo cells of the plane buffer loaded by this thread (two-cell ring without corners):
+  // smem slot, or -1
+  constexpr int HI = (NHALO + NT - 1) / NT;
+  int h_hx[HI], h_hy[HI];
+#pragma unroll
+  for (int s = 0; s < HI; ++s) {
+    const int h = tid + s * NT;
+    h_hx[s] = -1;
+    h_hy[s] = 0;
+    if (h < 4 * TY) {
+      const int c4 = h / TY;
+      h_hx[s] = c4 < 2 ? c4 : TX + c4;
+      h_hy[s] = h % TY + 2;
+    } else if (h < NHALO) {
+      const int h2 = h - 4 * TY;
+      const int c4 = h2 / TX;
+      h_hy[s] = c4 < 2 ? c4 : TY + c4;
+      h_hx[s] = h2 % TX + 2;
+    }
+  }
+
   // Tiles of all grids of the launch, taken in order by a fixed stride
   // (sched 0) or from an atomic counter (sched 1).
   for (long long iter = 0;; ++iter) {
@@ -213,7 +275,8 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   const int gidx = find_grid(tile_begin, ngrid, tile);
   const Grid& G = grids[gidx];
   const int nx = G.nx, ny = G.ny, nz = G.nz;
-  const long long N = G.N;
+  const long long N = G.N, nxy = (long long)nx * ny;
+  const int bcz0 = G.bc[4], bcz1 = G.bc[5];
   long long t = tile - tile_begin[gidx];
   const int bx = (int)(t % G.tiles_x);
   t /= G.tiles_x;
@@ -224,6 +287,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   const R i6h = (R)(1.0 / (6.0 * G.h));
   const double* __restrict__ Ws = mode == kStage2 ? G.W1 : G.W;
   const double* __restrict__ phis = mode == kStage2 ? G.phi1 : G.phi;
+  const uint8_t* __restrict__ idg = G.id;
   Ctrl* ctrl = G.ctrl;
   const int slot = mode == kStage2 ? 1 : 0;
   const long long step = ctrl->step;
@@ -238,16 +302,29 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   const double dt = s_dt;
 
   const int gx = x0 + tx, gy = y0 + ty;
-  const bool own_xy = gx < nx && gy < ny;
+  const bool inside = gx < nx && gy < ny;
+  // column bases (x, y mapped once per tile)
+  const long long own_base = (long long)map_index(gy, ny, G.bc[2], G.bc[3]) * nx + map_index(gx, nx, G.bc[0], G.bc[1]);
+  long long halo_base[HI];
+#pragma unroll
+  for (int s = 0; s < HI; ++s)
+    halo_base[s] = h_hx[s] < 0 ? 0
+                               : (long long)map_index(y0 + h_hy[s] - 2, ny, G.bc[2], G.bc[3]) * nx +
+                                     map_index(x0 + h_hx[s] - 2, nx, G.bc[0], G.bc[1]);
 
-  // material at the start of the step and the stage state of one cell
-  auto load = [&](int i, int j, int k, R P[5], R& ph, int& idv) {
-    const long long c = cell_of(G, i, j, k);
+  // material at the start of the step and the stage state of cell index c
+  auto load = [&](long long c, R P[5], R& ph, int& idv) {
     const double phd = phis[c];
-    idv = mode == kStage2 ? (G.id[c] & 1) : (phd < 0.0 ? 1 : 0);
+    if (mode == kStage2) {
+      idv = idg[c] & 1;
+    } else {
+      const long long b = __double_as_longlong(phd);
+      idv = (b < 0 && (b << 1) != 0) ? 1 : 0;  // phi < 0
+    }
     ph = to_r<R>(phd);
     if (!cons_to_prim<R>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) latch_error(ctrl, M2C_ENONPHYS, c);
   };
+  auto plane = [&](int k) { return (long long)map_index(k, nz, bcz0, bcz1) * nxy; };
 
   // ---- warm-up of the z window: planes k0-2 .. k0+1
   R Pa[5], P0[5], P1[5], P2[5];
@@ -259,10 +336,10 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   {
     R Pb[5];
     int idb;
-    load(gx, gy, k0 - 2, Pb, ph[0], idb);
-    load(gx, gy, k0 - 1, Pa, ph[1], ida);
-    load(gx, gy, k0, P0, ph[2], id0);
-    load(gx, gy, k0 + 1, P1, ph[3], id1);
+    load(plane(k0 - 2) + own_base, Pb, ph[0], idb);
+    load(plane(k0 - 1) + own_base, Pa, ph[1], ida);
+    load(plane(k0) + own_base, P0, ph[2], id0);
+    load(plane(k0 + 1) + own_base, P1, ph[3], id1);
     FaceState<R> QaP, Q0M;
     cell_faces<R>(s_eos[ida], Pb, Pa, P0, idb == ida && id0 == ida, Qtmp, QaP, bad);
     cell_faces<R>(s_eos[id0], Pa, P0, P1, ida == id0 && id1 == id0, Q0M, QzP, bad);
@@ -276,11 +353,12 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   }
 
   double lam_max = 0.0;
-  const int nhalo = 4 * (TX + TY);
+  const int cslot = (ty + 2) * HX + tx + 2;
 
   for (int k = k0; k < k1; ++k) {
+    const long long pk = (long long)k * nxy;  // k is inside the grid
     // ---- own column: plane k+2, z face states of cell k+1, z flux of face k+1/2
-    load(gx, gy, k + 2, P2, ph[4], id2);
+    load(plane(k + 2) + own_base, P2, ph[4], id2);
     cell_faces<R>(s_eos[id1], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad);
     if (id0 == id1) {
       hllc<2, R>(QzP, QzM1, Fzp);
@@ -290,121 +368,90 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     }
     // ---- plane k into shared memory: own cells and the two-cell halo (no corners)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) s_q[(v * HY + ty + 2) * HX + tx + 2] = P0[v];
-    s_phi[(ty + 2) * HX + tx + 2] = ph[2];
-    s_id[(ty + 2) * HX + tx + 2] = (uint8_t)id0;
-    for (int hsel = tid; hsel < nhalo; hsel += NT) {
-      int hx, hy;
-      if (hsel < 4 * TY) {
-        const int c4 = hsel / TY, r = hsel % TY;
-        hx = c4 < 2 ? c4 : TX + c4;
-        hy = r + 2;
-      } else {
-        const int h2 = hsel - 4 * TY;
-        const int c4 = h2 / TX, col = h2 % TX;
-        hy = c4 < 2 ? c4 : TY + c4;
-        hx = col + 2;
-      }
+    for (int v = 0; v < 5; ++v) s_q[v * PL + cslot] = P0[v];
+    s_phi[cslot] = ph[2];
+    s_id[cslot] = (uint8_t)id0;
+#pragma unroll
+    for (int s = 0; s < HI; ++s) {
+      if (h_hx[s] < 0) break;
+      const int hslot = h_hy[s] * HX + h_hx[s];
       R Ph[5], phh;
       int idh;
-      load(x0 + hx - 2, y0 + hy - 2, k, Ph, phh, idh);
+      load(pk + halo_base[s], Ph, phh, idh);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) s_q[(v * HY + hy) * HX + hx] = Ph[v];
-      s_phi[hy * HX + hx] = phh;
-      s_id[hy * HX + hx] = (uint8_t)idh;
+      for (int v = 0; v < 5; ++v) s_q[v * PL + hslot] = Ph[v];
+      s_phi[hslot] = phh;
+      s_id[hslot] = (uint8_t)idh;
     }
     __syncthreads();
 
-    // ---- MUSCL face states along x (cells x = -1 .. TX) and y (cells y = -1 .. TY), one loop
-    constexpr int NXS = (TX + 2) * TY, NYS = TX * (TY + 2);
-    for (int i = tid; i < NXS + NYS; i += NT) {
-      int hx, hy, so, ss;  // centre in the plane buffer, stencil stride, output slot
-      FaceState<R>* out;
-      if (i < NXS) {
-        const int xs = i % (TX + 2), row = i / (TX + 2);
-        hx = xs + 1;
-        hy = row + 2;
-        so = 1;
-        out = s_xs + (row * (TX + 2) + xs) * 2;
-        ss = 0;
-      } else {
-        const int j = i - NXS;
-        const int x = j % TX, ys = j / TX;
-        hx = x + 2;
-        hy = ys + 1;
-        so = HX;
-        out = s_ys + (ys * TX + x) * 2;
-        ss = 1;
-      }
-      const int c0 = hy * HX + hx;
+    // ---- MUSCL face states along x (cells x = -1 .. TX) and y (cells y = -1 .. TY)
+#pragma unroll
+    for (int s = 0; s < SI; ++s) {
+      const int it = st_item[s];
+      if (it < 0) break;
+      const int c0 = it & 1023, so = (it >> 10) ? HX : 1;
       R Pm[5], P[5], Pp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        Pm[v] = s_q[v * HY * HX + c0 - so];
-        P[v] = s_q[v * HY * HX + c0];
-        Pp[v] = s_q[v * HY * HX + c0 + so];
+        Pm[v] = s_q[v * PL + c0 - so];
+        P[v] = s_q[v * PL + c0];
+        Pp[v] = s_q[v * PL + c0 + so];
       }
       const int ic = s_id[c0];
       const bool same = s_id[c0 - so] == ic && s_id[c0 + so] == ic;
       bool b = false;
+      FaceState<R>* out = s_st + 2 * (tid + s * NT);
       cell_faces<R>(s_eos[ic], Pm, P, Pp, same, out[0], out[1], b);
-      if (b) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, x0 + hx - 2, y0 + hy - 2, k));
-      (void)ss;
+      if (b) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, x0 + c0 % HX - 2, y0 + c0 / HX - 2, k));
     }
     __syncthreads();
 
-    // ---- HLLC on every x face (f between cells f-1 and f) and y face of the tile, one loop
-    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
-    for (int i = tid; i < NXF + NYF; i += NT) {
+    // ---- HLLC on every x face (between cells f-1 and f of a row) and y face of the tile
+#pragma unroll
+    for (int s = 0; s < FI; ++s) {
+      const int it = fl_item[s];
+      if (it < 0) break;
+      const int dir = (it >> 30) & 1;
+      const int lsi = it & 2047, idp = (it >> 11) & 511, outo = (it >> 20) & 511;
+      const int il = s_id[idp], ir = s_id[idp + (dir ? HX : 1)];
+      const FaceState<R>& QL = s_st[lsi];
+      const FaceState<R>& QR = s_st[lsi + (dir ? 2 * TX - 1 : 1)];
       R F[5];
-      if (i < NXF) {
-        const int f = i % (TX + 1), row = i / (TX + 1);
-        const int il = s_id[(row + 2) * HX + f + 1], ir = s_id[(row + 2) * HX + f + 2];
-        if (il == ir) {
-          hllc<0, R>(s_xs[(row * (TX + 2) + f) * 2 + 1], s_xs[(row * (TX + 2) + f + 1) * 2 + 0], F);
-        } else {
+      if (il != ir) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) F[v] = (R)0;
-        }
-#pragma unroll
-        for (int v = 0; v < 5; ++v) s_fx[(v * TY + row) * (TX + 1) + f] = F[v];
+        for (int v = 0; v < 5; ++v) F[v] = (R)0;
+      } else if (dir == 0) {
+        hllc<0, R>(QL, QR, F);
       } else {
-        const int j = i - NXF;
-        const int x = j % TX, f = j / TX;
-        const int il = s_id[(f + 1) * HX + x + 2], ir = s_id[(f + 2) * HX + x + 2];
-        if (il == ir) {
-          hllc<1, R>(s_ys[(f * TX + x) * 2 + 1], s_ys[((f + 1) * TX + x) * 2 + 0], F);
-        } else {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F[v] = (R)0;
-        }
-#pragma unroll
-        for (int v = 0; v < 5; ++v) s_fy[(v * (TY + 1) + f) * TX + x] = F[v];
+        hllc<1, R>(QL, QR, F);
       }
+      R* o = (dir ? s_fy : s_fx) + outo;
+      const int stride = dir ? SFY : SFX;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) o[v * stride] = F[v];
     }
     __syncthreads();
 
     // ---- per cell: residual, level set, Runge-Kutta update, work lists
     {
-      const int hxc = tx + 2, hyc = ty + 2;
-      const int idxm = s_id[hyc * HX + hxc - 1], idxp = s_id[hyc * HX + hxc + 1];
-      const int idym = s_id[(hyc - 1) * HX + hxc], idyp = s_id[(hyc + 1) * HX + hxc];
-      const bool inside = own_xy;
+      const int idxm = s_id[cslot - 1], idxp = s_id[cslot + 1];
+      const int idym = s_id[cslot - HX], idyp = s_id[cslot + HX];
       const bool is_if = inside && (idxm != id0 || idxp != id0 || idym != id0 || idyp != id0 || idm != id0 ||
                                     id1 != id0);
       R res[5];
       R Fxm[5], Fxp[5], Fym[5], Fyp[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        Fxm[v] = s_fx[(v * TY + ty) * (TX + 1) + tx];
-        Fxp[v] = s_fx[(v * TY + ty) * (TX + 1) + tx + 1];
-        Fym[v] = s_fy[(v * (TY + 1) + ty) * TX + tx];
-        Fyp[v] = s_fy[(v * (TY + 1) + ty + 1) * TX + tx];
+        Fxm[v] = s_fx[v * SFX + ty * (TX + 1) + tx];
+        Fxp[v] = s_fx[v * SFX + ty * (TX + 1) + tx + 1];
+        Fym[v] = s_fy[v * SFY + ty * TX + tx];
+        Fyp[v] = s_fy[v * SFY + (ty + 1) * TX + tx];
         res[v] = ((Fxm[v] - Fxp[v]) * ih + (Fym[v] - Fyp[v]) * ih) + (Fzm[v] - Fzp[v]) * ih;
       }
       // level-set residual -((u phi_x + v phi_y) + w phi_z), third-order upwind-biased (Sec. 4.4)
       const R u = P0[1], vv = P0[2], w = P0[3];
-      const R* prow = s_phi + hyc * HX + hxc;
+      const R* prow = s_phi + cslot;
       R Dx, Dy, Dz;
       if (u >= (R)0) Dx = (((R)2 * prow[1] + (R)3 * prow[0]) - (R)6 * prow[-1] + prow[-2]) * i6h;
       else Dx = ((-prow[2] + (R)6 * prow[1]) - (R)3 * prow[0] - (R)2 * prow[-1]) * i6h;
@@ -414,7 +461,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       else Dz = ((-ph[4] + (R)6 * ph[3]) - (R)3 * ph[2] - (R)2 * ph[1]) * i6h;
       const R Lphi = -((u * Dx + vv * Dy) + w * Dz);
 
-      const long long c = ((long long)k * ny + (inside ? gy : 0)) * nx + (inside ? gx : 0);
+      const long long c = pk + own_base;
       bool flip = false;
       if (inside) {
         if (mode == kResidual) {
@@ -434,9 +481,10 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
         } else {
           const double pn = 0.5 * (G.phi[c] + (G.phi1[c] + dt * to_d<R>(Lphi)));
           G.phi[c] = pn;
-          flip = (pn < 0.0) != (id0 == 1);
+          const bool neg = pn < 0.0;
+          flip = neg != (id0 == 1);
           // bit 2: material at the end of the step (read by the phase update)
-          G.id[c] = (uint8_t)(id0 | (pn < 0.0 ? 4 : 0));
+          G.id[c] = (uint8_t)(id0 | (neg ? 4 : 0));
           if (!is_if) {
 #pragma unroll
             for (int v = 0; v < 5; ++v)
@@ -450,78 +498,78 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
           }
         }
       }
-      // ---- work lists: warp ballot, one atomic per warp
-      const unsigned lane = tid & 31;
-      const unsigned lt = (1u << lane) - 1u;
-      {
-        const unsigned m = __ballot_sync(0xffffffffu, is_if);
-        if (m) {
-          int base = 0;
-          const int leader = __ffs(m) - 1;
-          if ((int)lane == leader) base = atomicAdd(&ctrl->ncell[slot], __popc(m));
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (is_if) {
-            const int s = base + __popc(m & lt);
-            if (s < G.cell_cap) {
-              IfCell* e = G.cells + s;
-              e->cell = c;
+      // ---- work lists: warp ballot, one atomic per warp (skipped when the warp has none)
+      const bool fxf = inside && idxp != id0, fyf = inside && idyp != id0, fzf = inside && id1 != id0;
+      const int nf = (int)fxf + (int)fyf + (int)fzf;
+      if (__any_sync(0xffffffffu, is_if || nf || flip)) {
+        {
+          const unsigned m = __ballot_sync(0xffffffffu, is_if);
+          if (m) {
+            int base = 0;
+            const int leader = __ffs(m) - 1;
+            if ((int)lane == leader) base = atomicAdd(&ctrl->ncell[slot], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (is_if) {
+              const int s = base + __popc(m & lt);
+              if (s < G.cell_cap) {
+                IfCell* e = G.cells + s;
+                e->cell = c;
 #pragma unroll
-              for (int v = 0; v < 5; ++v) {
-                e->F[0][v] = to_d<R>(Fxm[v]);
-                e->F[1][v] = to_d<R>(Fxp[v]);
-                e->F[2][v] = to_d<R>(Fym[v]);
-                e->F[3][v] = to_d<R>(Fyp[v]);
-                e->F[4][v] = to_d<R>(Fzm[v]);
-                e->F[5][v] = to_d<R>(Fzp[v]);
-              }
-              G.cell_slot[c] = s;
-            } else {
-              latch_error(ctrl, M2C_EOVERFLOW, c);
-            }
-          }
-        }
-      }
-      {
-        const bool fx = inside && idxp != id0, fy = inside && idyp != id0, fz = inside && id1 != id0;
-        const int nf = (int)fx + (int)fy + (int)fz;
-        int incl = nf;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if ((int)lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total) {
-          int base = 0;
-          if (lane == 31) base = atomicAdd(&ctrl->nface[slot], total);
-          base = __shfl_sync(0xffffffffu, base, 31);
-          int s = base + incl - nf;
-          const bool fl[3] = {fx, fy, fz};
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            if (fl[d]) {
-              if (s < G.face_cap) {
-                G.faces[s].cell = c;
-                G.faces[s].dir = d;
+                for (int v = 0; v < 5; ++v) {
+                  e->F[0][v] = to_d<R>(Fxm[v]);
+                  e->F[1][v] = to_d<R>(Fxp[v]);
+                  e->F[2][v] = to_d<R>(Fym[v]);
+                  e->F[3][v] = to_d<R>(Fyp[v]);
+                  e->F[4][v] = to_d<R>(Fzm[v]);
+                  e->F[5][v] = to_d<R>(Fzp[v]);
+                }
+                G.cell_slot[c] = s;
               } else {
                 latch_error(ctrl, M2C_EOVERFLOW, c);
               }
-              ++s;
             }
           }
         }
-      }
-      if (mode == kStage2) {
-        const unsigned m = __ballot_sync(0xffffffffu, flip);
-        if (m) {
-          int base = 0;
-          const int leader = __ffs(m) - 1;
-          if ((int)lane == leader) base = atomicAdd(&ctrl->nflip, __popc(m));
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (flip) {
-            const int s = base + __popc(m & lt);
-            if (s < G.flip_cap) G.flips[s] = c;
-            else latch_error(ctrl, M2C_EOVERFLOW, c);
+        {
+          int incl = nf;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += y;
+          }
+          const int total = __shfl_sync(0xffffffffu, incl, 31);
+          if (total) {
+            int base = 0;
+            if (lane == 31) base = atomicAdd(&ctrl->nface[slot], total);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            int s = base + incl - nf;
+            const bool fl[3] = {fxf, fyf, fzf};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              if (fl[d]) {
+                if (s < G.face_cap) {
+                  G.faces[s].cell = c;
+                  G.faces[s].dir = d;
+                } else {
+                  latch_error(ctrl, M2C_EOVERFLOW, c);
+                }
+                ++s;
+              }
+            }
+          }
+        }
+        if (mode == kStage2) {
+          const unsigned m = __ballot_sync(0xffffffffu, flip);
+          if (m) {
+            int base = 0;
+            const int leader = __ffs(m) - 1;
+            if ((int)lane == leader) base = atomicAdd(&ctrl->nflip, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (flip) {
+              const int s = base + __popc(m & lt);
+              if (s < G.flip_cap) G.flips[s] = c;
+              else latch_error(ctrl, M2C_EOVERFLOW, c);
+            }
           }
         }
       }
