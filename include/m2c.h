@@ -89,7 +89,8 @@ typedef struct {
 /* Workspace bytes for an nx*ny*nz grid. */
 size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
 
-/* Creates a context on the calling thread's current CUDA device.
+/* Creates a context on the calling thread's current CUDA device. At least one
+ * axis must have more than one cell (M2C_EINVAL otherwise).
  * lo: lower corner (only used to report coordinates), h > 0: cell edge,
  * bc[6]: m2c_bc per side, workspace: device pointer of ws_bytes >=
  * m2c_workspace_bytes(), stream: a cudaStream_t (NULL = legacy default stream).

@@ -1046,6 +1046,8 @@ static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
     if (g->n[a] < 1) return OR_EINVAL;
     if ((g->bc[2 * a] == BC_PERIODIC) != (g->bc[2 * a + 1] == BC_PERIODIC)) return OR_EINVAL;
   }
+  /* at least one axis with more than one cell: otherwise nothing moves and the time step is undefined */
+  if (g->n[0] * g->n[1] * g->n[2] < 2) return OR_EINVAL;
   if (!(g->h > 0.0)) return OR_EINVAL;
   return OR_OK;
 }

@@ -1200,6 +1200,7 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   if (!out) return M2C_EINVAL;
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !workspace) return M2C_EINVAL;
+  if ((long long)nx * ny * nz < 2) return M2C_EINVAL;  // no axis to move along: no time step
   if (precision != M2C_FP64 && precision != M2C_MIXED) return M2C_EINVAL;
   for (int a = 0; a < 3; ++a) {
     for (int s = 0; s < 2; ++s)
