@@ -106,8 +106,9 @@ m2c_status m2c_set_eos(m2c_ctx* ctx, int material, int type, const double* param
  * reinit_every-th step, reinit_iters pseudo-time iterations (0 disables). */
 m2c_status m2c_set_scheme(m2c_ctx* ctx, double cfl, int reinit_every, int reinit_iters);
 
-/* Tile of the bulk stage kernel: 32 x tile_rows (4 or 8) columns marching
- * tile_z cells along z (0: automatic). Results do not depend on the tiling. */
+/* Tile of the bulk stage kernel: 32 x tile_rows (4 or 8; 16 for M2C_MIXED)
+ * columns marching tile_z cells along z (0: automatic). Results do not depend
+ * on the tiling. */
 m2c_status m2c_set_tiling(m2c_ctx* ctx, int tile_rows, int tile_z);
 
 /* Borrows the device arrays W (5N doubles) and phi (N doubles) as the state,
@@ -132,7 +133,7 @@ m2c_status m2c_step(m2c_ctx* ctx, int nsteps);
  * latch, work lists and reinitialisation schedule, counted from its own step).
  * workspace: caller's device buffer of m2c_batch_workspace_bytes(k) bytes,
  * 256-byte aligned, borrowed for the life of the batch. tuning (may be NULL) =
- * {tile rows 4 or 8, tile length along z (0: automatic), schedule (0: fixed
+ * {tile rows 4, 8 or (mixed) 16, tile length along z (0: automatic), schedule (0: fixed
  * stride over tiles, 1: atomic tile counter), blocks per SM of a persistent
  * grid (0: one block per tile)}. m2c_batch_create synchronises (it uploads the
  * descriptors and reduces the first time steps). */

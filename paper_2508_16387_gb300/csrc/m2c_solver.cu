@@ -175,14 +175,15 @@ struct StageSmem {
 };
 
 // FP64 tiles run one block per SM (FP64-pipe bound); the FP32 tiles of the
-// mixed path are latency bound and run four 256-thread blocks per SM (their
-// shared memory, 55 KB, allows four).
+// mixed path are latency bound and are compiled for 1024 resident threads per
+// SM (64 registers a thread): four 256-thread blocks of 8-row tiles (55 KB of
+// shared memory each) or two 512-thread blocks of 16-row tiles.
 //
 // Every thread's share of the plane work (halo cell, face-state items, flux
 // items) and its shared-memory addresses are fixed for the whole launch and
 // computed once; only the plane index changes along the march.
 template <typename R, int TY>
-__global__ void __launch_bounds__(32 * TY, (sizeof(R) == 8 ? 1 : 4))
+__global__ void __launch_bounds__(32 * TY, (sizeof(R) == 8 ? 1 : 1024 / (32 * TY)))
 k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, long long ntiles, int mode,
         int sched, unsigned long long* __restrict__ tile_counter) {
   constexpr int TX = 32, NT = TX * TY, HX = TX + 4, HY = TY + 4, PL = HY * HX;
@@ -221,24 +222,26 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       st_item[s] = ((j / TX + 1) * HX + j % TX + 2) | (1 << 10);
     }
   }
-  // flux items, packed: left face state (bits 0-10), id position of the left cell (11-19),
-  // output offset (20-28), direction y (bit 30); -1: none
-  int fl_item[FI];
+  // flux items, packed in two words: left face state (bits 0-15) and direction y (bit 30),
+  // -1: none; id position of the left cell (bits 0-15) and output offset (bits 16-31)
+  int fl_a[FI], fl_b[FI];
 #pragma unroll
   for (int s = 0; s < FI; ++s) {
     const int i = tid + s * NT;
-    fl_item[s] = -1;
+    fl_a[s] = -1;
+    fl_b[s] = 0;
     if (i < NXF) {
       const int f = i % (TX + 1), row = i / (TX + 1);
-      fl_item[s] = (2 * (row * (TX + 2) + f) + 1) | (((row + 2) * HX + f + 1) << 11) | ((row * (TX + 1) + f) << 20);
+      fl_a[s] = 2 * (row * (TX + 2) + f) + 1;
+      fl_b[s] = ((row + 2) * HX + f + 1) | ((row * (TX + 1) + f) << 16);
     } else if (i < NF) {
       const int j = i - NXF;
       const int x = j % TX, f = j / TX;
-      fl_item[s] = (2 * NXS + 2 * (f * TX + x) + 1) | (((f + 1) * HX + x + 2) << 11) | ((f * TX + x) << 20) |
-                   (1 << 30);
+      fl_a[s] = (2 * NXS + 2 * (f * TX + x) + 1) | (1 << 30);
+      fl_b[s] = ((f + 1) * HX + x + 2) | ((f * TX + x) << 16);
     }
   }
-  static_assert(2 * NS < 2048 && PL < 512 && SFX < 512 && SFY < 512, "packed item fields");
+  static_assert(2 * NS < 65536 && PL < 1024 && SFX < 32768 && SFY < 32768, "packed item fields");
   // halo cells of the plane buffer loaded by this thread (two-cell ring without corners):
   // smem slot, or -1
   constexpr int HI = (NHALO + NT - 1) / NT;
@@ -410,10 +413,10 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     // ---- HLLC on every x face (between cells f-1 and f of a row) and y face of the tile
 #pragma unroll
     for (int s = 0; s < FI; ++s) {
-      const int it = fl_item[s];
+      const int it = fl_a[s];
       if (it < 0) break;
       const int dir = (it >> 30) & 1;
-      const int lsi = it & 2047, idp = (it >> 11) & 511, outo = (it >> 20) & 511;
+      const int lsi = it & 0xffff, idp = fl_b[s] & 0xffff, outo = (fl_b[s] >> 16) & 0x7fff;
       const int il = s_id[idp], ir = s_id[idp + (dir ? HX : 1)];
       const FaceState<R>& QL = s_st[lsi];
       const FaceState<R>& QR = s_st[lsi + (dir ? 2 * TX - 1 : 1)];
@@ -1029,11 +1032,12 @@ cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid,
 
 cudaError_t launch_stage(int prec, const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
                          const LaunchPlan& lp, cudaStream_t s) {
-  if (prec == M2C_FP64) {
+  if (prec == M2C_FP64) {  // FP64 tiles have at most 8 rows (registers)
     if (lp.ty == 4) return launch_stage_t<double, 4>(grids, tiles, ngrid, ntiles, mode, lp, s);
     return launch_stage_t<double, 8>(grids, tiles, ngrid, ntiles, mode, lp, s);
   }
   if (lp.ty == 4) return launch_stage_t<float, 4>(grids, tiles, ngrid, ntiles, mode, lp, s);
+  if (lp.ty == 16) return launch_stage_t<float, 16>(grids, tiles, ngrid, ntiles, mode, lp, s);
   return launch_stage_t<float, 8>(grids, tiles, ngrid, ntiles, mode, lp, s);
 }
 
@@ -1042,6 +1046,7 @@ void setup_all_stage_kernels() {
   stage_smem_setup<double, 8>();
   stage_smem_setup<float, 4>();
   stage_smem_setup<float, 8>();
+  stage_smem_setup<float, 16>();
 }
 
 int sm_count() {
@@ -1295,7 +1300,8 @@ m2c_status m2c_set_scheme(m2c_ctx* c, double cfl, int reinit_every, int reinit_i
 }
 
 m2c_status m2c_set_tiling(m2c_ctx* c, int tile_rows, int tile_z) {
-  if (!c || (tile_rows != 4 && tile_rows != 8) || tile_z < 0) return M2C_EINVAL;
+  if (!c || (tile_rows != 4 && tile_rows != 8 && tile_rows != 16) || tile_z < 0) return M2C_EINVAL;
+  if (tile_rows == 16 && c->host.prec == M2C_FP64) return set_err(c, M2C_EINVAL, "FP64 tiles have 4 or 8 rows");
   c->ty = tile_rows;
   set_tiling(c->host, c->ty, tile_z > 0 ? tile_z : default_tz(c->host, c->ty));
   return push_grid(c);
@@ -1391,7 +1397,7 @@ m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace
   }
   int ty = 8, tz = 0, sched = 0, bpsm = 0;
   if (tuning) {
-    ty = tuning[0] == 4 ? 4 : 8;
+    ty = tuning[0] == 4 ? 4 : (tuning[0] == 16 && v[0]->host.prec == M2C_MIXED ? 16 : 8);
     tz = std::max(0, tuning[1]);
     sched = tuning[2] == 1 ? 1 : 0;
     bpsm = std::max(0, tuning[3]);
