@@ -344,7 +344,7 @@ def run_batched(args):
     res = {}
     for name, prec in (("mixed", M.MIXED), ("fp64", M.FP64)):
         grids = [make_grid(M, s, prec) for s in setups]
-        cands = AT.DEFAULT_CANDIDATES if prec == M.MIXED else [(8, 0, 0, 0), (8, 0, 1, 2), (4, 0, 1, 2), (8, 32, 1, 1)]
+        cands = AT.DEFAULT_CANDIDATES if prec == M.MIXED else AT.FP64_CANDIDATES
         best, trials = AT.tune_batch(grids, candidates=cands, trial_steps=2)
         bt = M.Batch(grids, best)
         t0 = time.perf_counter()

@@ -13,8 +13,9 @@ from dataclasses import dataclass
 from . import m2c as M
 
 DEFAULT_CANDIDATES = [(ty, tz, sched, bpsm) for ty, tz, sched, bpsm in
-                      itertools.product((4, 8), (0, 16, 32), (0, 1), (0, 2, 4))
+                      itertools.product((8, 16), (0, 16, 32), (0, 1), (0, 2, 4))
                       if not (sched == 1 and bpsm == 0)]
+FP64_CANDIDATES = [(8, 0, 0, 0), (8, 0, 1, 1), (4, 0, 1, 2), (8, 32, 1, 1)]
 
 
 @dataclass
