@@ -150,9 +150,11 @@ def time_steps(torch, g, steps, warmup, barrier=None):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    kms, klaunch = g.profile_read()
+    kern = g.profile_read_kernels()
     g.profile(False)
     g.sync()
+    time_steps.kernels = kern
+    kms, klaunch = kern["stage"]
     return ms, kms, klaunch
 
 
@@ -258,7 +260,8 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": ncu_traffic(args.prec, args.n),
             "kernel": "k_stage<float,8> (bulk stage)", "peak_source": src,
-            "kernel_ms_avg": round(avg, 4), "kernel_share": round(kms / ms, 3) if ms > 0 else None}
+            "kernel_ms_avg": round(avg, 4), "kernel_share": round(kms / ms, 3) if ms > 0 else None,
+            "step_breakdown_ms": {k: round(v[0] / args.steps, 4) for k, v in time_steps.kernels.items()}}
     launches = sum(launches_per_step(args.warmup + i, s.reinit_every, s.reinit_iters) for i in range(args.steps))
     e2e = None
     if not args.no_e2e:

@@ -62,9 +62,10 @@ typedef enum {
  *   (or fewer than 6 params) turns the tensile cutoff off. */
 typedef enum { M2C_EOS_SG = 0, M2C_EOS_MG = 1 } m2c_eos_type;
 
-/* M2C_FP64: every operation in FP64. M2C_MIXED: reconstruction, HLLC and the
- * level-set residual in FP32; the pressure from the conserved state, the
- * Runge-Kutta accumulation of W and phi, and the exact Riemann solver in FP64. */
+/* M2C_FP64: every operation in FP64. M2C_MIXED: reconstruction, HLLC, the
+ * level-set residual and the reinitialisation update in FP32; the pressure
+ * from the conserved state, the Runge-Kutta accumulation of W and phi, the
+ * level-set values and the exact Riemann solver in FP64. */
 typedef enum { M2C_FP64 = 0, M2C_MIXED = 1 } m2c_precision;
 
 /* Boundary conditions per side (x-, x+, y-, y+, z-, z+): transmissive
@@ -90,7 +91,7 @@ typedef struct {
 size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
 
 /* Creates a context on the calling thread's current CUDA device. At least one
- * axis must have more than one cell (M2C_EINVAL otherwise).
+ * axis must have more than one cell, and nx*ny*nz < 2^31 (M2C_EINVAL otherwise).
  * lo: lower corner (only used to report coordinates), h > 0: cell edge,
  * bc[6]: m2c_bc per side, workspace: device pointer of ws_bytes >=
  * m2c_workspace_bytes(), stream: a cudaStream_t (NULL = legacy default stream).
@@ -206,12 +207,15 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
                                 const m2c_eos_desc* eos1, int precision, const double* W, const double* phi,
                                 double* R, double* L, void* stream);
 
-/* Kernel timing: while enabled, m2c_step records a CUDA event
- * pair on the context's stream around every launch of the bulk stage kernel.
- * m2c_profile_read synchronises the stream, returns the summed event time (ms)
- * and the number of timed launches, and starts a new count. */
+/* Kernel timing: while enabled, m2c_step records a CUDA event pair on the
+ * context's stream around every kernel launch. m2c_profile_read synchronises
+ * the stream, returns the summed event time (ms) and the number of launches of
+ * the bulk stage kernel, and starts a new count; m2c_profile_read_kernels does
+ * the same for every kernel kind: [0] bulk stage, [1] FIVER, [2] interface-cell
+ * finish, [3] reinitialisation, [4] phase update, [5] end of step. */
 m2c_status m2c_profile(m2c_ctx* ctx, int enable);
 m2c_status m2c_profile_read(m2c_ctx* ctx, double* total_ms, long* launches);
+m2c_status m2c_profile_read_kernels(m2c_ctx* ctx, double ms[6], long launches[6]);
 
 /* Releases a context (the borrowed memory stays with the caller). */
 void m2c_destroy(m2c_ctx* ctx);

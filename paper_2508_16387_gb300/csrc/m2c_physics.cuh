@@ -286,7 +286,8 @@ __device__ inline double eos_plow(const EosDev& q) {
   return isfinite(q.eta_min) ? q.pmin : -INFINITY;
 }
 
-__device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs) {
+__device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
+                              bool want_rho = true) {
   const double g = q.g, pb = p + q.pc, pbK = K.p + q.pc;
   if (!(pb >= 0.0) || !(pbK > 0.0)) return M2C_ENONPHYS;
   if (p > K.p) {
@@ -298,10 +299,13 @@ __device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& 
     double r = pb / pbK, gm = (g - 1.0) / (g + 1.0);
     rs = K.rho * (r + gm) / (gm * r + 1.0);
   } else {
-    double r = pb / pbK;
-    f = 2.0 * K.c / (g - 1.0) * (pow(r, (g - 1.0) / (2.0 * g)) - 1.0);
-    df = pow(r, -(g + 1.0) / (2.0 * g)) / (K.rho * K.c);
-    rs = K.rho * pow(r, 1.0 / g);
+    // one power serves f and f': r^{-(g+1)/(2g)} = r^{(g-1)/(2g)} / r; the density
+    // behind the wave is only evaluated when asked for (after the iteration)
+    const double r = pb / pbK;
+    const double q = pow(r, (g - 1.0) / (2.0 * g));
+    f = 2.0 * K.c / (g - 1.0) * (q - 1.0);
+    df = q / (r * K.rho * K.c);
+    rs = want_rho ? K.rho * pow(r, 1.0 / g) : 0.0;
   }
   return M2C_OK;
 }
@@ -402,15 +406,16 @@ __device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& 
   return M2C_OK;
 }
 
-__device__ inline int wave(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs) {
-  return q.type == M2C_EOS_SG ? wave_sg(q, K, p, f, df, rs) : wave_mg(q, K, p, f, df, rs);
+__device__ inline int wave(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
+                           bool want_rho = true) {
+  return q.type == M2C_EOS_SG ? wave_sg(q, K, p, f, df, rs, want_rho) : wave_mg(q, K, p, f, df, rs);
 }
 
 __device__ inline int riemann_F(const EosDev& qL, const Side& L, const EosDev& qR, const Side& Rs, double p,
                                 double& F, double& dF) {
   double fL, dfL, rL, fR, dfR, rR;
-  int st = wave(qL, L, p, fL, dfL, rL);
-  if (!st) st = wave(qR, Rs, p, fR, dfR, rR);
+  int st = wave(qL, L, p, fL, dfL, rL, false);
+  if (!st) st = wave(qR, Rs, p, fR, dfR, rR, false);
   if (st) return st;
   F = fL + fR + (Rs.u - L.u);
   dF = dfL + dfR;

@@ -715,8 +715,12 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
 // ---------------------------------------------------------------------------
 // Reinitialisation (Eq. reinit, Sec. 4.4): one Jacobi iteration
 // phi' = phi - dtau S(phi0) (G(phi) - 1), Godunov upwind |grad phi|,
-// S = phi0/sqrt(phi0^2 + h^2), dtau = h/2, first-layer cells fixed.
+// S = phi0/sqrt(phi0^2 + h^2), dtau = h/2, first-layer cells fixed. phi stays
+// FP64 in memory; the update is computed in R (FP32 on the mixed path: the
+// level set is a distance to within the grid's resolution, far above FP32
+// rounding). One thread per cell with 32-bit index arithmetic.
 // ---------------------------------------------------------------------------
+template <typename R>
 __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, int it) {
   const Grid& G = grids[blockIdx.y];
   // each grid follows its own schedule: after its steps reinit_every, 2 reinit_every, ...
@@ -728,10 +732,10 @@ __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, 
   double* __restrict__ dst = (it == nits && it > 1) ? G.phi : ((it % 2 == 1) ? G.phi1 : G.phiC);
   const int first_iter = it == 1;
   const double* __restrict__ phi0 = G.phi;
-  const long long N = G.N;
-  const double h = G.h, ih = G.inv_h, dtau = 0.5 * G.h;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(c % G.nx), j = (int)((c / G.nx) % G.ny), k = (int)(c / ((long long)G.nx * G.ny));
+  const unsigned nx = (unsigned)G.nx, nxy = (unsigned)G.nx * (unsigned)G.ny, N = (unsigned)G.N;
+  const R h = (R)G.h, ih = (R)G.inv_h, dtau = (R)(0.5 * G.h);
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    const unsigned k = c / nxy, rem = c - k * nxy, j = rem / nx, i = rem - j * nx;
     const long long nb[6] = {cell_of(G, i - 1, j, k), cell_of(G, i + 1, j, k), cell_of(G, i, j - 1, k),
                              cell_of(G, i, j + 1, k), cell_of(G, i, j, k - 1), cell_of(G, i, j, k + 1)};
     const double p0 = phi0[c];
@@ -750,24 +754,27 @@ __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, 
       dst[c] = cur;
       continue;
     }
-    double G2[3];
+    const R cr = to_r<R>(cur);
+    R G2[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double a = (cur - src[nb[2 * d]]) * ih;
-      const double b = (src[nb[2 * d + 1]] - cur) * ih;
-      double x, y;
+      const R a = (cr - to_r<R>(src[nb[2 * d]])) * ih;
+      const R b = (to_r<R>(src[nb[2 * d + 1]]) - cr) * ih;
+      R x, y;
       if (p0 >= 0.0) {
-        x = fmax(a, 0.0);
-        y = fmin(b, 0.0);
+        x = fmax(a, (R)0);
+        y = fmin(b, (R)0);
       } else {
-        x = fmin(a, 0.0);
-        y = fmax(b, 0.0);
+        x = fmin(a, (R)0);
+        y = fmax(b, (R)0);
       }
       G2[d] = fmax(x * x, y * y);
     }
-    const double Gn = sqrt((G2[0] + G2[1]) + G2[2]);
-    const double S = p0 / sqrt(p0 * p0 + h * h);
-    dst[c] = cur - dtau * S * (Gn - 1.0);
+    const R Gn = sqrt((G2[0] + G2[1]) + G2[2]);
+    const R pr = to_r<R>(p0);
+    const R S = pr / sqrt(pr * pr + h * h);
+    if constexpr (sizeof(R) == 8) dst[c] = cur - dtau * S * (Gn - (R)1);
+    else dst[c] = cur - f2d(dtau * S * (Gn - (R)1));
   }
 }
 
@@ -951,7 +958,8 @@ struct m2c_ctx {
   long long host_step;
   bool has_state, eos_set[2], dirty, lam_valid;
   bool profiling;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pairs around bulk stage launches
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pairs around launches while profiling
+  std::vector<int> ev_kind;
   size_t ev_used;
   std::string err;
 };
@@ -1090,12 +1098,16 @@ int default_tz(const Grid& g, int ty) {
   return g.nz > 16 ? 16 : g.nz;
 }
 
+// Event pairs recorded around launches while profiling, tagged with the kernel kind.
+enum KernelKind { kKStage = 0, kKFiver, kKFinish, kKReinit, kKPhaseFix, kKEndStep, kKinds };
+
 struct StageEvents {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev;
+  std::vector<int>* kind;
   size_t* used;
 };
 
-cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s) {
+cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s, int kind = kKStage) {
   if (!pe) return cudaSuccess;
   if (start) {
     if (*pe->used == pe->ev->size()) {
@@ -1104,7 +1116,9 @@ cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s) {
       if (e == cudaSuccess) e = cudaEventCreate(&b);
       if (e != cudaSuccess) return e;
       pe->ev->push_back({a, b});
+      pe->kind->push_back(kind);
     }
+    (*pe->kind)[*pe->used] = kind;
     return cudaEventRecord((*pe->ev)[*pe->used].first, s);
   }
   cudaError_t e = cudaEventRecord((*pe->ev)[*pe->used].second, s);
@@ -1119,22 +1133,30 @@ cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int 
                          StageEvents* pe = nullptr) {
   cudaError_t e;
   const dim3 lg((unsigned)(2 * sm_count()), (unsigned)ngrid);
+#define M2C_TIMED(kind, launch)                                     \
+  do {                                                              \
+    if ((e = record_pair(pe, true, s, kind)) != cudaSuccess) return e; \
+    launch;                                                         \
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;          \
+    if ((e = record_pair(pe, false, s)) != cudaSuccess) return e;   \
+  } while (0)
   for (int stage = 0; stage < 2; ++stage) {
     const int mode = stage == 0 ? kStage1 : kStage2;
-    if ((e = record_pair(pe, true, s)) != cudaSuccess) return e;
-    e = launch_stage(prec, dev_grids, dev_tiles, ngrid, ntiles, mode, lp, s);
-    if (e != cudaSuccess) return e;
-    if ((e = record_pair(pe, false, s)) != cudaSuccess) return e;
-    k_fiver<<<lg, 128, 0, s>>>(dev_grids, mode);
-    k_finish<<<lg, 128, 0, s>>>(dev_grids, mode);
+    M2C_TIMED(kKStage, e = launch_stage(prec, dev_grids, dev_tiles, ngrid, ntiles, mode, lp, s); if (e) return e);
+    M2C_TIMED(kKFiver, (k_fiver<<<lg, 128, 0, s>>>(dev_grids, mode)));
+    M2C_TIMED(kKFinish, (k_finish<<<lg, 128, 0, s>>>(dev_grids, mode)));
   }
   if (reinit && reinit_iters > 0) {
     const dim3 rg((unsigned)std::min<long long>((nmax + 255) / 256, 8ll * sm_count()), (unsigned)ngrid);
-    for (int it = 1; it <= reinit_iters; ++it) k_reinit<<<rg, 256, 0, s>>>(dev_grids, it);
-    k_copy_phi1<<<rg, 256, 0, s>>>(dev_grids);
+    for (int it = 1; it <= reinit_iters; ++it) {
+      if (prec == M2C_FP64) M2C_TIMED(kKReinit, (k_reinit<double><<<rg, 256, 0, s>>>(dev_grids, it)));
+      else M2C_TIMED(kKReinit, (k_reinit<float><<<rg, 256, 0, s>>>(dev_grids, it)));
+    }
+    M2C_TIMED(kKReinit, (k_copy_phi1<<<rg, 256, 0, s>>>(dev_grids)));
   }
-  k_phase_fix<<<lg, 128, 0, s>>>(dev_grids);
-  k_end_step<<<(ngrid + 63) / 64, 64, 0, s>>>(dev_grids, ngrid);
+  M2C_TIMED(kKPhaseFix, (k_phase_fix<<<lg, 128, 0, s>>>(dev_grids)));
+  M2C_TIMED(kKEndStep, (k_end_step<<<(ngrid + 63) / 64, 64, 0, s>>>(dev_grids, ngrid)));
+#undef M2C_TIMED
   return cudaGetLastError();
 }
 
@@ -1206,6 +1228,7 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !workspace) return M2C_EINVAL;
   if ((long long)nx * ny * nz < 2) return M2C_EINVAL;  // no axis to move along: no time step
+  if ((long long)nx * ny * nz >= (1ll << 31)) return M2C_EINVAL;  // 32-bit cell indices in some kernels
   if (precision != M2C_FP64 && precision != M2C_MIXED) return M2C_EINVAL;
   for (int a = 0; a < 3; ++a) {
     for (int s = 0; s < 2; ++s)
@@ -1371,7 +1394,7 @@ m2c_status m2c_step(m2c_ctx* c, int nsteps) {
   }
   for (int n = 0; n < nsteps; ++n) {
     const bool re = c->reinit_every > 0 && (c->host_step + 1) % c->reinit_every == 0;
-    StageEvents pe{&c->ev, &c->ev_used};
+    StageEvents pe{&c->ev, &c->ev_kind, &c->ev_used};
     LaunchPlan lp;
     lp.ty = c->ty;
     cudaError_t e = enqueue_step(c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), c->host.prec, lp, re,
@@ -1780,20 +1803,33 @@ m2c_status m2c_profile(m2c_ctx* c, int enable) {
   return M2C_OK;
 }
 
-m2c_status m2c_profile_read(m2c_ctx* c, double* total_ms, long* launches) {
-  if (!c || !total_ms || !launches) return M2C_EINVAL;
+m2c_status m2c_profile_read_kernels(m2c_ctx* c, double ms[6], long launches[6]) {
+  if (!c || !ms || !launches) return M2C_EINVAL;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_check(c, e, "profile_read");
-  double sum = 0.0;
-  for (size_t i = 0; i < c->ev_used; ++i) {
-    float ms = 0.0f;
-    e = cudaEventElapsedTime(&ms, c->ev[i].first, c->ev[i].second);
-    if (e != cudaSuccess) return cuda_check(c, e, "profile_read");
-    sum += ms;
+  for (int k = 0; k < kKinds; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
   }
-  *total_ms = sum;
-  *launches = (long)c->ev_used;
+  for (size_t i = 0; i < c->ev_used; ++i) {
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, c->ev[i].first, c->ev[i].second);
+    if (e != cudaSuccess) return cuda_check(c, e, "profile_read");
+    ms[c->ev_kind[i]] += t;
+    launches[c->ev_kind[i]] += 1;
+  }
   c->ev_used = 0;
+  return M2C_OK;
+}
+
+m2c_status m2c_profile_read(m2c_ctx* c, double* total_ms, long* launches) {
+  if (!c || !total_ms || !launches) return M2C_EINVAL;
+  double ms[kKinds];
+  long n[kKinds];
+  m2c_status st = m2c_profile_read_kernels(c, ms, n);
+  if (st) return st;
+  *total_ms = ms[kKStage];
+  *launches = n[kKStage];
   return M2C_OK;
 }
 

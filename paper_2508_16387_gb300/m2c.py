@@ -83,6 +83,7 @@ def lib():
                                            p, p, p, p, p]
         L.m2c_profile.argtypes = [p, i]
         L.m2c_profile_read.argtypes = [p, ctypes.POINTER(d), ctypes.POINTER(L_)]
+        L.m2c_profile_read_kernels.argtypes = [p, p, p]
         L.m2c_destroy.argtypes = [p]
         L.m2c_destroy.restype = None
         L.m2c_last_error.argtypes = [p]
@@ -297,6 +298,16 @@ class Grid:
         n = ctypes.c_long()
         _check(lib().m2c_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)), "m2c_profile_read", self.ctx)
         return ms.value, n.value
+
+    KERNEL_KINDS = ("stage", "fiver", "finish", "reinit", "phase_fix", "end_step")
+
+    def profile_read_kernels(self):
+        """{kernel kind: (total ms, launches)} since profiling was enabled or last read."""
+        ms = (ctypes.c_double * 6)()
+        n = (ctypes.c_long * 6)()
+        _check(lib().m2c_profile_read_kernels(self.ctx, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p)),
+               "m2c_profile_read_kernels", self.ctx)
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_KINDS)}
 
     def residual(self):
         torch = self.torch
