@@ -79,31 +79,113 @@ __device__ __forceinline__ R rsqrt_pos(R x) {  // sqrt of x > 0
 }
 
 // Exact IEEE-754 binary64 <-> binary32 conversions written with integer
-// operations (from the bit layout of the two formats), for the mixed-precision
-// loads and updates: GB300 runs its conversion instructions on the narrow
-// FP64 pipe. Values outside the normal binary32 range fall back to the
-// hardware conversion. d2f rounds to nearest, ties to even.
-__device__ __forceinline__ float d2f(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long a = b & 0x7fffffffffffffffull;
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  if (a >= 0x3810000000000000ull && a < 0x47efffffe0000000ull) {
-    const unsigned long long m = a - 0x3800000000000000ull;        // exponent bias 1023 -> 127
-    const unsigned long long r = m + 0x0fffffffull + ((m >> 29) & 1ull);
-    return __uint_as_float((unsigned)(r >> 29) | sign);
-  }
-  if (a == 0ull) return __uint_as_float(sign);
-  return (float)x;
+// operations only (from the bit layout of the two formats), for the
+// mixed-precision loads and updates: GB300 runs its conversion instructions on
+// the narrow FP64 pipe, and a conversion kept as a fallback branch is still
+// issued when the compiler predicates the branch. d2f rounds to nearest, ties
+// to even, including results in the binary32 subnormal range and overflow to
+// infinity; a NaN stays a NaN. Host-callable so that they can be checked
+// against the host's conversions.
+__host__ __device__ __forceinline__ unsigned long long bits_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ double double_of(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  __builtin_memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned bits_of(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned b;
+  __builtin_memcpy(&b, &x, 4);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float float_of(unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float x;
+  __builtin_memcpy(&x, &b, 4);
+  return x;
+#endif
 }
 
-__device__ __forceinline__ double f2d(float x) {
-  const unsigned f = __float_as_uint(x);
+// x < 0 and x > 0 for a binary64 x, decided on its bits (one unsigned
+// compare each; false for zeros of either sign and for NaNs), so that sign
+// tests of FP64 data stay off the FP64 pipe.
+__host__ __device__ __forceinline__ bool lt0(double x) {
+  return bits_of(x) - 0x8000000000000001ull < 0x7ff0000000000000ull;
+}
+__host__ __device__ __forceinline__ bool gt0(double x) {
+  return bits_of(x) - 1ull < 0x7ff0000000000000ull;
+}
+
+__host__ __device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = bits_of(x);
+  const unsigned long long a = b & 0x7fffffffffffffffull;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  unsigned r;
+  if (a >= 0x3810000000000000ull && a < 0x47f0000000000000ull) {
+    // 2^-126 <= |x| < 2^128: rebias the exponent (1023 -> 127), round the
+    // 52-bit mantissa to 23 bits; a carry out of the mantissa increments the
+    // exponent (at the top of the range, to the infinity pattern)
+    const unsigned long long m = a - 0x3800000000000000ull;
+    r = (unsigned)((m + 0x0fffffffull + ((m >> 29) & 1ull)) >> 29);
+  } else if (a < 0x3810000000000000ull) {
+    // |x| < 2^-126: result in units of 2^-149, M 2^(e-1075) = M 2^-(926-e) units
+    const int e = (int)(a >> 52);
+    if (e < 873) {
+      r = 0u;  // below 2^-150 (exactly 2^-150 is handled below: a tie to even 0)
+    } else {
+      const unsigned long long M = (a & 0x000fffffffffffffull) | 0x0010000000000000ull;
+      const int sh = 926 - e;  // 30 .. 53
+      const unsigned long long q = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+      r = (unsigned)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
+    }
+  } else if (a <= 0x7ff0000000000000ull) {
+    r = 0x7f800000u;  // |x| >= 2^128 and infinity
+  } else {
+    r = 0x7fc00000u | (unsigned)((a >> 29) & 0x003fffffull);  // quiet NaN
+  }
+  return float_of(r | sign);
+}
+
+__host__ __device__ __forceinline__ double f2d(float x) {
+  const unsigned f = bits_of(x);
   const unsigned a = f & 0x7fffffffu;
   const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
-  if (a >= 0x00800000u && a < 0x7f800000u)
-    return __longlong_as_double((long long)((((unsigned long long)a + (896ull << 23)) << 29) | sign));
-  if (a == 0u) return __longlong_as_double((long long)sign);
-  return (double)x;
+  unsigned long long r;
+  if (a >= 0x00800000u && a < 0x7f800000u) {
+    r = ((unsigned long long)a + (896ull << 23)) << 29;  // rebias 127 -> 1023
+  } else if (a == 0u) {
+    r = 0ull;
+  } else if (a < 0x00800000u) {
+    // subnormal a 2^-149: normalise the leading bit to position 23
+#ifdef __CUDA_ARCH__
+    const int s = __clz(a) - 8;
+#else
+    const int s = __builtin_clz(a) - 8;
+#endif
+    r = ((unsigned long long)(897 - s) << 52) | ((unsigned long long)((a << s) & 0x007fffffu) << 29);
+  } else if (a == 0x7f800000u) {
+    r = 0x7ff0000000000000ull;
+  } else {
+    r = 0x7ff8000000000000ull | ((unsigned long long)(a & 0x003fffffu) << 29);
+  }
+  return double_of(r | sign);
 }
 
 template <typename R>

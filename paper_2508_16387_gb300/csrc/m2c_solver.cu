@@ -66,7 +66,7 @@ __device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd,
       ok = eos_p<float>(q, rf, inv, d2f(rhoe) * inv, p);
     }
     P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
-    return ok && rho > 0.0;
+    return ok && gt0(rho);
   }
 }
 
@@ -321,8 +321,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     if (mode == kStage2) {
       idv = idg[c] & 1;
     } else {
-      const long long b = __double_as_longlong(phd);
-      idv = (b < 0 && (b << 1) != 0) ? 1 : 0;  // phi < 0
+      idv = lt0(phd) ? 1 : 0;
     }
     ph = to_r<R>(phd);
     if (!cons_to_prim<R>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) latch_error(ctrl, M2C_ENONPHYS, c);
@@ -484,7 +483,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
         } else {
           const double pn = 0.5 * (G.phi[c] + (G.phi1[c] + dt * to_d<R>(Lphi)));
           G.phi[c] = pn;
-          const bool neg = pn < 0.0;
+          const bool neg = lt0(pn);
           flip = neg != (id0 == 1);
           // bit 2: material at the end of the step (read by the phase update)
           G.id[c] = (uint8_t)(id0 | (neg ? 4 : 0));
@@ -700,7 +699,7 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
 #pragma unroll
       for (int v = 0; v < 5; ++v) G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * res[v]));
       const int id0 = G.id[c] & 1;
-      const bool flip = (G.phi[c] < 0.0) != (id0 == 1);
+      const bool flip = lt0(G.phi[c]) != (id0 == 1);
       if (!flip) {
         bool ok;
         const double lam = wave_sum(G, G.eos[id0], G.W, N, c, ok);
@@ -741,10 +740,10 @@ __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, 
     const double p0 = phi0[c];
     bool first;
     if (first_iter) {
-      const bool s0 = p0 < 0.0;
+      const bool s0 = lt0(p0);
       first = false;
 #pragma unroll
-      for (int q = 0; q < 6; ++q) first = first || ((phi0[nb[q]] < 0.0) != s0);
+      for (int q = 0; q < 6; ++q) first = first || (lt0(phi0[nb[q]]) != s0);
       G.id[c] = (uint8_t)((G.id[c] & 5) | (first ? 2 : 0));
     } else {
       first = (G.id[c] & 2) != 0;
@@ -761,7 +760,7 @@ __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, 
       const R a = (cr - to_r<R>(src[nb[2 * d]])) * ih;
       const R b = (to_r<R>(src[nb[2 * d + 1]]) - cr) * ih;
       R x, y;
-      if (p0 >= 0.0) {
+      if (!lt0(p0)) {
         x = fmax(a, (R)0);
         y = fmin(b, (R)0);
       } else {
@@ -883,7 +882,7 @@ __global__ void __launch_bounds__(256) k_lam_init(const Grid* __restrict__ grids
   const Grid& G = grids[blockIdx.y];
   double lam_max = 0.0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x) {
-    const int m = G.phi[c] < 0.0 ? 1 : 0;
+    const int m = lt0(G.phi[c]) ? 1 : 0;
     bool ok;
     const double lam = wave_sum(G, G.eos[m], G.W, G.N, c, ok);
     if (!ok) latch_error(G.ctrl, M2C_ENONPHYS, c);
@@ -896,7 +895,7 @@ __global__ void k_prims_to_state(const Grid* __restrict__ grids, const double* _
   const Grid& G = grids[0];
   const long long N = G.N;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-    const int m = G.phi[c] < 0.0 ? 1 : 0;
+    const int m = lt0(G.phi[c]) ? 1 : 0;
     const double rho = prims[c], u = prims[N + c], v = prims[2 * N + c], w = prims[3 * N + c], p = prims[4 * N + c];
     double e, c2;
     if (!eos_e_c2<double>(G.eos[m], rho, 1.0 / rho, p, e, c2)) latch_error(G.ctrl, M2C_ENONPHYS, c);

@@ -1,0 +1,71 @@
+// Host-side check of the integer binary64 <-> binary32 conversions used by the
+// mixed-precision kernels, against the host's IEEE conversions (round to
+// nearest, ties to even). f2d is checked on every binary32 value; d2f on every
+// binary32 value, the binary64 neighbours of each, the midpoints between
+// adjacent binary32 values and their neighbours (the rounding ties), and
+// random bit patterns. Prints the number of mismatches and exits non-zero on
+// any.
+#include <cstdio>
+#include <cstdint>
+#include <cmath>
+
+#include "m2c_physics.cuh"
+
+using m2c::d2f;
+using m2c::f2d;
+using m2c::bits_of;
+using m2c::double_of;
+using m2c::float_of;
+
+static long long bad = 0;
+
+static void check_d2f(unsigned long long b) {
+  const double x = double_of(b);
+  const float want = (float)x, got = d2f(x);
+  if (std::isnan(want) ? !std::isnan(got) : bits_of(want) != bits_of(got)) {
+    if (bad < 10) std::printf("d2f %016llx: got %08x want %08x\n", b, bits_of(got), bits_of(want));
+    ++bad;
+  }
+}
+
+int main() {
+  for (unsigned long long u = 0; u <= 0xffffffffull; ++u) {
+    const float f = float_of((unsigned)u);
+    const double want = (double)f, got = f2d(f);
+    if (std::isnan(want) ? !std::isnan(got) : bits_of(want) != bits_of(got)) {
+      if (bad < 10) std::printf("f2d %08llx: got %016llx want %016llx\n", u, bits_of(got), bits_of(want));
+      ++bad;
+    }
+  }
+  // every binary32 value (as a double) and its binary64 neighbours; the
+  // midpoint to the next binary32 value and its neighbours
+  for (unsigned long long u = 0; u < 0x80000000ull; u += 1) {
+    const float f = float_of((unsigned)u);
+    if (std::isnan(f)) continue;
+    const unsigned long long d = bits_of((double)f);
+    for (unsigned long long sgn : {0ull, 0x8000000000000000ull}) {
+      check_d2f((d | sgn));
+      check_d2f((d + 1) | sgn);
+      if (d > 0) check_d2f((d - 1) | sgn);
+      if ((u & 0xff) == 0 && u < 0x7f800000ull) {
+        const double lo = (double)f, hi = (double)float_of((unsigned)u + 1);
+        const unsigned long long mid = bits_of(0.5 * (lo + hi));
+        check_d2f(mid | sgn);
+        check_d2f((mid + 1) | sgn);
+        check_d2f((mid - 1) | sgn);
+      }
+    }
+  }
+  // below the binary32 range, above it, infinities and NaNs, random patterns
+  unsigned long long s = 0x9e3779b97f4a7c15ull;
+  for (int i = 0; i < 20000000; ++i) {
+    s ^= s << 13; s ^= s >> 7; s ^= s << 17;
+    check_d2f(s);
+  }
+  for (unsigned long long e = 0; e < 2048; ++e)
+    for (unsigned long long m : {0ull, 1ull, 0x0008000000000000ull, 0x000fffffffffffffull, 0x0000000010000000ull,
+                                 0x0000000020000000ull, 0x0000000030000000ull})
+      for (unsigned long long sgn : {0ull, 0x8000000000000000ull}) check_d2f((e << 52) | m | sgn);
+  std::printf("mismatches %lld\n", bad);
+  return bad == 0 ? 0 : 1;
+}
