@@ -39,9 +39,8 @@ namespace m2c {
 // the stiffened gas, the pressure (a difference of large numbers when p_c is
 // large) in FP64, then rounded to FP32.
 template <typename R>
-__device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd, const double* __restrict__ W,
-                                             long long N, long long c, R P[5]) {
-  const double rho = W[c], m1 = W[N + c], m2 = W[2 * N + c], m3 = W[3 * N + c], E = W[4 * N + c];
+__device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& qd, double rho, double m1, double m2,
+                                               double m3, double E, R P[5]) {
   if constexpr (sizeof(R) == 8) {
     const double inv = 1.0 / rho;
     const double u = m1 * inv, v = m2 * inv, w = m3 * inv;
@@ -68,6 +67,12 @@ __device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd,
     P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
     return ok && gt0(rho);
   }
+}
+
+template <typename R>
+__device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd, const double* __restrict__ W,
+                                             long long N, long long c, R P[5]) {
+  return cons_to_prim_v<R>(q, qd, W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c], P);
 }
 
 template <typename R>
@@ -107,10 +112,9 @@ __device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], cons
 // |V_d| + c (the CFL reading of the design notes), in precision R (the mixed
 // path takes the time step from FP32 wave speeds of the FP64 state).
 template <typename R>
-__device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, const EosDev& qd, const double* W,
-                                             long long N, long long c, bool& ok) {
+__device__ __forceinline__ R wave_sum_v(const Grid& g, const EosP<R>& q, const EosDev& qd, const double w[5], bool& ok) {
   R P[5];
-  ok = cons_to_prim<R>(q, qd, W, N, c, P);
+  ok = cons_to_prim_v<R>(q, qd, w[0], w[1], w[2], w[3], w[4], P);
   R e, c2;
   ok = ok && eos_e_c2<R>(q, P[0], rrcp<R>(P[0]), P[4], e, c2);
   const R cs = ok ? rsqrt_pos<R>(c2) : (R)0;
@@ -118,7 +122,14 @@ __device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, co
   if (g.active[0]) lam = lam + (fabs(P[1]) + cs);
   if (g.active[1]) lam = lam + (fabs(P[2]) + cs);
   if (g.active[2]) lam = lam + (fabs(P[3]) + cs);
-  return (double)lam;
+  return lam;
+}
+
+template <typename R>
+__device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, const EosDev& qd, const double* W,
+                                             long long N, long long c, bool& ok) {
+  const double w[5] = {W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c]};
+  return to_d<R>(wave_sum_v<R>(g, q, qd, w, ok));
 }
 
 __device__ __forceinline__ double wave_sum(const Grid& g, const EosDev& q, const double* W, long long N, long long c,
@@ -354,7 +365,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     idm = ida;
   }
 
-  double lam_max = 0.0;
+  R lam_max = (R)0;
   const int cslot = (ty + 2) * HX + tx + 2;
 
   for (int k = k0; k < k1; ++k) {
@@ -489,11 +500,15 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
           G.id[c] = (uint8_t)(id0 | (neg ? 4 : 0));
           if (!is_if) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v)
-              G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * to_d<R>(res[v])));
+            double wn[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              wn[v] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * to_d<R>(res[v])));
+              G.W[v * N + c] = wn[v];
+            }
             if (!flip) {
               bool ok;
-              const double lam = wave_sum_r<R>(G, s_eos[id0], s_eosd[id0], G.W, N, c, ok);
+              const R lam = wave_sum_v<R>(G, s_eos[id0], s_eosd[id0], wn, ok);
               if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
               lam_max = fmax(lam_max, lam);
             }
@@ -590,7 +605,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     QzP = QzP1;
   }
   if (bad) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, gx, gy, k0));
-  if (mode == kStage2) block_max_to(lam_max, &ctrl->lam[(step + 1) & 1], s_red);
+  if (mode == kStage2) block_max_to(to_d<R>(lam_max), &ctrl->lam[(step + 1) & 1], s_red);
   __syncthreads();  // the next tile reuses the shared memory
   }
 }
