@@ -626,7 +626,10 @@ __device__ __forceinline__ void fiver_fluxes(const FaceState<double>& A, const F
   hllc<D, double>(SB, B, Fb);
 }
 
-__global__ void __launch_bounds__(128, 1) k_fiver(const Grid* __restrict__ grids, int mode) {
+// One warp-sized block per 32 faces, so that the few warps of a typical
+// interface spread evenly over the SMs (each is FP64-pipe bound).
+constexpr int kFiverThreads = 32;
+__global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restrict__ grids, int mode) {
   const Grid& G = grids[blockIdx.y];
   Ctrl* ctrl = G.ctrl;
   const int slot = mode == kStage2 ? 1 : 0;
@@ -732,8 +735,9 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
 // S = phi0/sqrt(phi0^2 + h^2), dtau = h/2, first-layer cells fixed. phi stays
 // FP64 in memory; the update is computed in R (FP32 on the mixed path: the
 // level set is a distance to within the grid's resolution, far above FP32
-// rounding). One thread per cell with 32-bit index arithmetic.
+// rounding).
 // ---------------------------------------------------------------------------
+constexpr int kReinitChunk = 32;  // planes marched by one thread
 template <typename R>
 __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, int it) {
   const Grid& G = grids[blockIdx.y];
@@ -744,51 +748,69 @@ __global__ void __launch_bounds__(256) k_reinit(const Grid* __restrict__ grids, 
   // writes phi (a single iteration ends in phi1 and is copied back)
   const double* __restrict__ src = it == 1 ? G.phi : ((it % 2 == 0) ? G.phi1 : G.phiC);
   double* __restrict__ dst = (it == nits && it > 1) ? G.phi : ((it % 2 == 1) ? G.phi1 : G.phiC);
-  const int first_iter = it == 1;
-  const double* __restrict__ phi0 = G.phi;
-  const unsigned nx = (unsigned)G.nx, nxy = (unsigned)G.nx * (unsigned)G.ny, N = (unsigned)G.N;
+  const bool first_iter = it == 1;  // src is phi0: the first-layer flags are set from it
+  const double* phi0 = G.phi;  // also dst in the last of several iterations (read first, same cell)
+  uint8_t* __restrict__ idg = G.id;
+  const int nx = G.nx, ny = G.ny, nz = G.nz;
+  const unsigned ncol = (unsigned)nx * (unsigned)ny;
+  const long long nxy = ncol;
+  const unsigned nchunk = (unsigned)((nz + kReinitChunk - 1) / kReinitChunk);
   const R h = (R)G.h, ih = (R)G.inv_h, dtau = (R)(0.5 * G.h);
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-    const unsigned k = c / nxy, rem = c - k * nxy, j = rem / nx, i = rem - j * nx;
-    const long long nb[6] = {cell_of(G, i - 1, j, k), cell_of(G, i + 1, j, k), cell_of(G, i, j - 1, k),
-                             cell_of(G, i, j + 1, k), cell_of(G, i, j, k - 1), cell_of(G, i, j, k + 1)};
-    const double p0 = phi0[c];
-    bool first;
-    if (first_iter) {
-      const bool s0 = lt0(p0);
-      first = false;
+  // one thread marches one column (i, j) over a chunk of planes with a
+  // three-plane window of src in registers; x and y neighbours are loaded
+  for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x; w < ncol * nchunk; w += gridDim.x * blockDim.x) {
+    const unsigned chunk = w / ncol, col = w - chunk * ncol;
+    const int j = (int)(col / (unsigned)nx), i = (int)(col - (unsigned)j * (unsigned)nx);
+    const int k0 = (int)chunk * kReinitChunk, k1 = min(k0 + kReinitChunk, nz);
+    const long long oxm = (long long)j * nx + map_index(i - 1, nx, G.bc[0], G.bc[1]);
+    const long long oxp = (long long)j * nx + map_index(i + 1, nx, G.bc[0], G.bc[1]);
+    const long long oym = (long long)map_index(j - 1, ny, G.bc[2], G.bc[3]) * nx + i;
+    const long long oyp = (long long)map_index(j + 1, ny, G.bc[2], G.bc[3]) * nx + i;
+    double sm = src[map_index(k0 - 1, nz, G.bc[4], G.bc[5]) * nxy + col];
+    double s0 = src[k0 * nxy + col];
+    for (int k = k0; k < k1; ++k) {
+      const long long base = k * nxy, c = base + col;
+      const double sp = src[map_index(k + 1, nz, G.bc[4], G.bc[5]) * nxy + col];
+      const double nbv[6] = {src[base + oxm], src[base + oxp], src[base + oym], src[base + oyp], sm, sp};
+      const double p0 = first_iter ? s0 : phi0[c];
+      bool first;
+      if (first_iter) {
+        const bool neg0 = lt0(p0);
+        first = false;
 #pragma unroll
-      for (int q = 0; q < 6; ++q) first = first || (lt0(phi0[nb[q]]) != s0);
-      G.id[c] = (uint8_t)((G.id[c] & 5) | (first ? 2 : 0));
-    } else {
-      first = (G.id[c] & 2) != 0;
-    }
-    const double cur = src[c];
-    if (first) {
-      dst[c] = cur;
-      continue;
-    }
-    const R cr = to_r<R>(cur);
-    R G2[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const R a = (cr - to_r<R>(src[nb[2 * d]])) * ih;
-      const R b = (to_r<R>(src[nb[2 * d + 1]]) - cr) * ih;
-      R x, y;
-      if (!lt0(p0)) {
-        x = fmax(a, (R)0);
-        y = fmin(b, (R)0);
+        for (int q = 0; q < 6; ++q) first = first || (lt0(nbv[q]) != neg0);
+        idg[c] = (uint8_t)((idg[c] & 5) | (first ? 2 : 0));
       } else {
-        x = fmin(a, (R)0);
-        y = fmax(b, (R)0);
+        first = (idg[c] & 2) != 0;
       }
-      G2[d] = fmax(x * x, y * y);
+      if (first) {
+        dst[c] = s0;
+      } else {
+        const R cr = to_r<R>(s0);
+        R G2[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const R a = (cr - to_r<R>(nbv[2 * d])) * ih;
+          const R b = (to_r<R>(nbv[2 * d + 1]) - cr) * ih;
+          R x, y;
+          if (!lt0(p0)) {
+            x = fmax(a, (R)0);
+            y = fmin(b, (R)0);
+          } else {
+            x = fmin(a, (R)0);
+            y = fmax(b, (R)0);
+          }
+          G2[d] = fmax(x * x, y * y);
+        }
+        const R Gn = sqrt((G2[0] + G2[1]) + G2[2]);
+        const R pr = to_r<R>(p0);
+        const R S = pr / sqrt(pr * pr + h * h);
+        if constexpr (sizeof(R) == 8) dst[c] = s0 - dtau * S * (Gn - (R)1);
+        else dst[c] = s0 - f2d(dtau * S * (Gn - (R)1));
+      }
+      sm = s0;
+      s0 = sp;
     }
-    const R Gn = sqrt((G2[0] + G2[1]) + G2[2]);
-    const R pr = to_r<R>(p0);
-    const R S = pr / sqrt(pr * pr + h * h);
-    if constexpr (sizeof(R) == 8) dst[c] = cur - dtau * S * (Gn - (R)1);
-    else dst[c] = cur - f2d(dtau * S * (Gn - (R)1));
   }
 }
 
@@ -1147,6 +1169,7 @@ cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int 
                          StageEvents* pe = nullptr) {
   cudaError_t e;
   const dim3 lg((unsigned)(2 * sm_count()), (unsigned)ngrid);
+  const dim3 fg((unsigned)(8 * sm_count()), (unsigned)ngrid);
 #define M2C_TIMED(kind, launch)                                     \
   do {                                                              \
     if ((e = record_pair(pe, true, s, kind)) != cudaSuccess) return e; \
@@ -1157,7 +1180,7 @@ cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int 
   for (int stage = 0; stage < 2; ++stage) {
     const int mode = stage == 0 ? kStage1 : kStage2;
     M2C_TIMED(kKStage, e = launch_stage(prec, dev_grids, dev_tiles, ngrid, ntiles, mode, lp, s); if (e) return e);
-    M2C_TIMED(kKFiver, (k_fiver<<<lg, 128, 0, s>>>(dev_grids, mode)));
+    M2C_TIMED(kKFiver, (k_fiver<<<fg, kFiverThreads, 0, s>>>(dev_grids, mode)));
     M2C_TIMED(kKFinish, (k_finish<<<lg, 128, 0, s>>>(dev_grids, mode)));
   }
   if (reinit && reinit_iters > 0) {
@@ -1568,7 +1591,7 @@ m2c_status m2c_residual(m2c_ctx* c, double* R, double* L) {
                                c->stream);
   if (e == cudaSuccess) {
     const dim3 lg((unsigned)(2 * sm_count()), 1);
-    k_fiver<<<lg, 128, 0, c->stream>>>(c->dev_grid, kResidual);
+    k_fiver<<<dim3((unsigned)(8 * sm_count()), 1), kFiverThreads, 0, c->stream>>>(c->dev_grid, kResidual);
     k_finish<<<lg, 128, 0, c->stream>>>(c->dev_grid, kResidual);
     e = cudaGetLastError();
   }
@@ -1796,7 +1819,7 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
   if (e == cudaSuccess) e = launch_stage(precision, dg, dt, 1, tiles[1], kResidual, lp, s);
   if (e == cudaSuccess) {
     const dim3 lg((unsigned)(2 * sm_count()), 1);
-    k_fiver<<<lg, 128, 0, s>>>(dg, kResidual);
+    k_fiver<<<dim3((unsigned)(8 * sm_count()), 1), kFiverThreads, 0, s>>>(dg, kResidual);
     k_finish<<<lg, 128, 0, s>>>(dg, kResidual);
     e = cudaGetLastError();
   }
