@@ -220,38 +220,42 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
   const unsigned lane = tid & 31, lt = (1u << lane) - 1u;
 
-  // face-state items, packed: centre in the plane buffer (bits 0-9), stencil along y (bit 10); -1: none
-  int st_item[SI];
-#pragma unroll
-  for (int s = 0; s < SI; ++s) {
-    const int i = tid + s * NT;
-    st_item[s] = -1;
-    if (i < NXS) {
-      st_item[s] = (i / (TX + 2) + 2) * HX + i % (TX + 2) + 1;
-    } else if (i < NS) {
+  // The thread's share of the plane work is recomputed from the thread index
+  // where it is used (a volatile read of %tid.x keeps the compiler from
+  // holding the items in registers across the plane loop).
+  auto tid_now = []() {
+    unsigned t;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
+    return (int)t;
+  };
+  // face-state item s, packed: centre in the plane buffer (bits 0-9), stencil along y (bit 10); -1: none
+  auto st_item = [&](int s) {
+    const int i = tid_now() + s * NT;
+    if (i < NXS) return (i / (TX + 2) + 2) * HX + i % (TX + 2) + 1;
+    if (i < NS) {
       const int j = i - NXS;
-      st_item[s] = ((j / TX + 1) * HX + j % TX + 2) | (1 << 10);
+      return ((j / TX + 1) * HX + j % TX + 2) | (1 << 10);
     }
-  }
-  // flux items, packed in two words: left face state (bits 0-15) and direction y (bit 30),
+    return -1;
+  };
+  // flux item s, packed in two words: left face state (bits 0-15) and direction y (bit 30),
   // -1: none; id position of the left cell (bits 0-15) and output offset (bits 16-31)
-  int fl_a[FI], fl_b[FI];
-#pragma unroll
-  for (int s = 0; s < FI; ++s) {
-    const int i = tid + s * NT;
-    fl_a[s] = -1;
-    fl_b[s] = 0;
+  auto flux_item = [&](int s, int& b) {
+    const int i = tid_now() + s * NT;
     if (i < NXF) {
       const int f = i % (TX + 1), row = i / (TX + 1);
-      fl_a[s] = 2 * (row * (TX + 2) + f) + 1;
-      fl_b[s] = ((row + 2) * HX + f + 1) | ((row * (TX + 1) + f) << 16);
-    } else if (i < NF) {
+      b = ((row + 2) * HX + f + 1) | ((row * (TX + 1) + f) << 16);
+      return 2 * (row * (TX + 2) + f) + 1;
+    }
+    if (i < NF) {
       const int j = i - NXF;
       const int x = j % TX, f = j / TX;
-      fl_a[s] = (2 * NXS + 2 * (f * TX + x) + 1) | (1 << 30);
-      fl_b[s] = ((f + 1) * HX + x + 2) | ((f * TX + x) << 16);
+      b = ((f + 1) * HX + x + 2) | ((f * TX + x) << 16);
+      return (2 * NXS + 2 * (f * TX + x) + 1) | (1 << 30);
     }
-  }
+    b = 0;
+    return -1;
+  };
   static_assert(2 * NS < 65536 && PL < 1024 && SFX < 32768 && SFY < 32768, "packed item fields");
   // halo cells of the plane buffer loaded by this thread (two-cell ring without corners):
   // smem slot, or -1
@@ -326,6 +330,8 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
                                : (long long)map_index(y0 + h_hy[s] - 2, ny, G.bc[2], G.bc[3]) * nx +
                                      map_index(x0 + h_hx[s] - 2, nx, G.bc[0], G.bc[1]);
 
+  // failures seen by this thread in this tile: non-physical state, work-list overflow
+  bool bad = false, ovf = false;
   // material at the start of the step and the stage state of cell index c
   auto load = [&](long long c, R P[5], R& ph, int& idv) {
     const double phd = phis[c];
@@ -335,7 +341,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       idv = lt0(phd) ? 1 : 0;
     }
     ph = to_r<R>(phd);
-    if (!cons_to_prim<R>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) latch_error(ctrl, M2C_ENONPHYS, c);
+    if (!cons_to_prim<R>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) bad = true;
   };
   auto plane = [&](int k) { return (long long)map_index(k, nz, bcz0, bcz1) * nxy; };
 
@@ -345,7 +351,6 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   int ida, idm, id0, id1, id2;
   FaceState<R> QzP, Qtmp, QzM1, QzP1;
   R Fzm[5], Fzp[5];
-  bool bad = false;
   {
     R Pb[5];
     int idb;
@@ -401,7 +406,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     // ---- MUSCL face states along x (cells x = -1 .. TX) and y (cells y = -1 .. TY)
 #pragma unroll
     for (int s = 0; s < SI; ++s) {
-      const int it = st_item[s];
+      const int it = st_item(s);
       if (it < 0) break;
       const int c0 = it & 1023, so = (it >> 10) ? HX : 1;
       R Pm[5], P[5], Pp[5];
@@ -416,17 +421,18 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       bool b = false;
       FaceState<R>* out = s_st + 2 * (tid + s * NT);
       cell_faces<R>(s_eos[ic], Pm, P, Pp, same, out[0], out[1], b);
-      if (b) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, x0 + c0 % HX - 2, y0 + c0 / HX - 2, k));
+      bad = bad || b;
     }
     __syncthreads();
 
     // ---- HLLC on every x face (between cells f-1 and f of a row) and y face of the tile
 #pragma unroll
     for (int s = 0; s < FI; ++s) {
-      const int it = fl_a[s];
+      int itb;
+      const int it = flux_item(s, itb);
       if (it < 0) break;
       const int dir = (it >> 30) & 1;
-      const int lsi = it & 0xffff, idp = fl_b[s] & 0xffff, outo = (fl_b[s] >> 16) & 0x7fff;
+      const int lsi = it & 0xffff, idp = itb & 0xffff, outo = (itb >> 16) & 0x7fff;
       const int il = s_id[idp], ir = s_id[idp + (dir ? HX : 1)];
       const FaceState<R>& QL = s_st[lsi];
       const FaceState<R>& QR = s_st[lsi + (dir ? 2 * TX - 1 : 1)];
@@ -499,7 +505,6 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
           // bit 2: material at the end of the step (read by the phase update)
           G.id[c] = (uint8_t)(id0 | (neg ? 4 : 0));
           if (!is_if) {
-#pragma unroll
             double wn[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
@@ -509,7 +514,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
             if (!flip) {
               bool ok;
               const R lam = wave_sum_v<R>(G, s_eos[id0], s_eosd[id0], wn, ok);
-              if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
+              bad = bad || !ok;
               lam_max = fmax(lam_max, lam);
             }
           }
@@ -542,7 +547,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
                 }
                 G.cell_slot[c] = s;
               } else {
-                latch_error(ctrl, M2C_EOVERFLOW, c);
+                ovf = true;
               }
             }
           }
@@ -568,7 +573,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
                   G.faces[s].cell = c;
                   G.faces[s].dir = d;
                 } else {
-                  latch_error(ctrl, M2C_EOVERFLOW, c);
+                  ovf = true;
                 }
                 ++s;
               }
@@ -585,7 +590,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
             if (flip) {
               const int s = base + __popc(m & lt);
               if (s < G.flip_cap) G.flips[s] = c;
-              else latch_error(ctrl, M2C_EOVERFLOW, c);
+              else ovf = true;
             }
           }
         }
@@ -604,7 +609,9 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     idm = id0; id0 = id1; id1 = id2;
     QzP = QzP1;
   }
+  // failures are latched once per tile, with the thread's column at the tile's first plane
   if (bad) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, gx, gy, k0));
+  if (ovf) latch_error(ctrl, M2C_EOVERFLOW, cell_of(G, gx, gy, k0));
   if (mode == kStage2) block_max_to(to_d<R>(lam_max), &ctrl->lam[(step + 1) & 1], s_red);
   __syncthreads();  // the next tile reuses the shared memory
   }
