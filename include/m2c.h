@@ -64,8 +64,9 @@ typedef enum { M2C_EOS_SG = 0, M2C_EOS_MG = 1 } m2c_eos_type;
 
 /* M2C_FP64: every operation in FP64. M2C_MIXED: reconstruction, HLLC, the
  * level-set residual and the reinitialisation update in FP32; the pressure
- * from the conserved state, the Runge-Kutta accumulation of W and phi, the
- * level-set values and the exact Riemann solver in FP64. */
+ * from the conserved state, the Runge-Kutta accumulation of W and phi and the
+ * level-set values in FP64; the exact Riemann solver iterates in FP32 and
+ * finishes with FP64 Newton steps (m2c_solve_riemann_mixed). */
 typedef enum { M2C_FP64 = 0, M2C_MIXED = 1 } m2c_precision;
 
 /* Boundary conditions per side (x-, x+, y-, y+, z-, z+): transmissive
@@ -176,6 +177,18 @@ m2c_status m2c_get_stats(m2c_ctx* ctx, m2c_stats* out);
  * the batch (host arrays) or M2C_OK (device arrays; read status[]). */
 m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
                              const double* R, double* out, int* iters, int* status, int on_device, void* stream);
+
+/* The same batch solved the way the FIVER kernel of the M2C_MIXED path solves
+ * it (Sec. 4.2 with the mixed-precision reading): Newton iterations on FP32
+ * wave curves from the same start, then one FP64 Newton step on the FP64 wave
+ * curves (two when the first moves p by more than 1e-7 |p|); u* and the star
+ * densities follow to first order in the last step. Problems whose FP32
+ * iteration fails, signals a vacuum or ends more than 1e-5 |p| from the FP64
+ * step are solved by the FP64 iteration of m2c_solve_riemann. iters counts
+ * the FP32 and FP64 steps. Arguments, layout, ownership and errors as for
+ * m2c_solve_riemann. */
+m2c_status m2c_solve_riemann_mixed(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
+                                   const double* R, double* out, int* iters, int* status, int on_device, void* stream);
 
 /* Post-shock state of a shock moving in +x into the state w = (rho, u, p) with
  * pressure p1 behind it (the right-facing wave of the exact Riemann solver):

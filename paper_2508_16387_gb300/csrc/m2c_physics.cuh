@@ -369,7 +369,7 @@ __device__ inline double eos_plow(const EosDev& q) {
 }
 
 __device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
-                              bool want_rho = true) {
+                              bool want_rho = true, double* drs = nullptr) {
   const double g = q.g, pb = p + q.pc, pbK = K.p + q.pc;
   if (!(pb >= 0.0) || !(pbK > 0.0)) return M2C_ENONPHYS;
   if (p > K.p) {
@@ -380,6 +380,7 @@ __device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& 
     df = sq * (1.0 - 0.5 * (p - K.p) / (pb + B));
     double r = pb / pbK, gm = (g - 1.0) / (g + 1.0);
     rs = K.rho * (r + gm) / (gm * r + 1.0);
+    if (drs) *drs = K.rho * (1.0 - gm * gm) / ((gm * r + 1.0) * (gm * r + 1.0) * pbK);
   } else {
     // one power serves f and f': r^{-(g+1)/(2g)} = r^{(g-1)/(2g)} / r; the density
     // behind the wave is only evaluated when asked for (after the iteration)
@@ -388,6 +389,7 @@ __device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& 
     f = 2.0 * K.c / (g - 1.0) * (q - 1.0);
     df = q / (r * K.rho * K.c);
     rs = want_rho ? K.rho * pow(r, 1.0 / g) : 0.0;
+    if (drs) *drs = rs / (g * pb);
   }
   return M2C_OK;
 }
@@ -445,11 +447,13 @@ __device__ inline int mg_rhs(const EosDev& q, double p, double rho, double& drho
   return M2C_OK;
 }
 
-__device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs) {
+__device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
+                              double* drs = nullptr) {
   if (p == K.p) {
     f = 0.0;
     df = 1.0 / (K.rho * K.c);
     rs = K.rho;
+    if (drs) *drs = 1.0 / (K.c * K.c);
     return M2C_OK;
   }
   if (p > K.p) {
@@ -461,6 +465,7 @@ __device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& 
     f = fv;
     df = (dv + (p - K.p) * drdp / (rho * rho)) / (2.0 * fv);
     rs = rho;
+    if (drs) *drs = drdp;
     return M2C_OK;
   }
   // equal substeps, 64 for an interval of at least 5% of K0, fewer (>= 1) for weaker waves
@@ -485,12 +490,13 @@ __device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& 
   f = fv;
   df = 1.0 / (rho * sqrt(c2));
   rs = rho;
+  if (drs) *drs = 1.0 / c2;
   return M2C_OK;
 }
 
 __device__ inline int wave(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
-                           bool want_rho = true) {
-  return q.type == M2C_EOS_SG ? wave_sg(q, K, p, f, df, rs, want_rho) : wave_mg(q, K, p, f, df, rs);
+                           bool want_rho = true, double* drs = nullptr) {
+  return q.type == M2C_EOS_SG ? wave_sg(q, K, p, f, df, rs, want_rho, drs) : wave_mg(q, K, p, f, df, rs, drs);
 }
 
 __device__ inline int riemann_F(const EosDev& qL, const Side& L, const EosDev& qR, const Side& Rs, double p,
@@ -580,6 +586,218 @@ __device__ inline int riemann_solve(const EosDev& qL, double rl, double ul, doub
   out.rhoR = rR;
   iters = it;
   return M2C_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision exact Riemann solve: Newton on p* first runs on FP32 wave
+// curves (the same PVRS start and curves, with FP32 tolerances; weak waves of
+// a stiff MG material, |p - p_K| <= 1e-5 rho_K c_K^2, take the acoustic
+// curve, which is all an FP32 start can resolve there), then one FP64 Newton
+// step from the FP32 root on the FP64 wave curves (two if the first moves p by
+// more than 1e-7 |p|) gives p*; u* and the star densities follow from the last
+// FP64 evaluation to first order in the step. An FP32 failure, a vacuum
+// signal, a slope that is not finite, or a step larger than 1e-5 |p| leaves
+// the problem to the FP64 iteration above.
+// ---------------------------------------------------------------------------
+struct SideF {
+  float rho, u, p, c, e;
+};
+
+__device__ inline bool make_side_f(const EosP<float>& q, float rho, float u, float p, SideF& K) {
+  if (!(rho > 0.0f)) return false;
+  float e, c2;
+  if (!eos_e_c2<float>(q, rho, 1.0f / rho, p, e, c2)) return false;
+  K.rho = rho;
+  K.u = u;
+  K.p = p;
+  K.c = sqrtf(c2);
+  K.e = e;
+  return true;
+}
+
+__device__ inline float eos_plow_f(const EosP<float>& q) {
+  if (q.type == M2C_EOS_SG) return -q.pc;
+  return isfinite(q.eta_min) ? q.pmin : -INFINITY;
+}
+
+__device__ inline bool wave_sg_f(const EosP<float>& q, const SideF& K, float p, float& f, float& df) {
+  const float g = q.g, pb = p + q.pc, pbK = K.p + q.pc, dp = p - K.p;
+  if (!(pb >= 0.0f) || !(pbK > 0.0f)) return false;
+  if (p > K.p) {
+    const float A = 2.0f / ((g + 1.0f) * K.rho);
+    const float B = (g - 1.0f) / (g + 1.0f) * pbK;
+    const float sq = sqrtf(A / (pb + B));
+    f = dp * sq;
+    df = sq * (1.0f - 0.5f * dp / (pb + B));
+  } else {
+    // (pb/pbK)^a - 1 as expm1(a log1p(dp/pbK)): no cancellation for weak waves
+    const float x = dp / pbK;
+    const float qm1 = expm1f((g - 1.0f) / (2.0f * g) * log1pf(x));
+    f = 2.0f * K.c / (g - 1.0f) * qm1;
+    df = (1.0f + qm1) / ((1.0f + x) * K.rho * K.c);
+  }
+  return true;
+}
+
+__device__ inline bool mg_hugoniot_f(const EosP<float>& q, const SideF& K, float p, float& rho_out, float& drdp) {
+  float lo = K.rho, hi = q.rho0 * q.s / (q.s - 1.0f);
+  if (!(hi > lo)) return false;
+  float rho = K.rho + (p - K.p) / (K.c * K.c);
+  if (!(rho > lo && rho < hi)) rho = 0.5f * (lo + hi);
+  for (int it = 0; it < 40; ++it) {
+    const float eta = 1.0f - q.rho0 / rho;
+    if (!(eta < q.eta_max)) return false;
+    float pR, dpR, eR, deR;
+    mg_ref<float>(q, eta, pR, dpR, eR, deR);
+    const float e = eR + (p - pR) * q.inv_rg;
+    const float ir2 = 1.0f / (rho * rho);
+    const float dedr = (deR - dpR * q.inv_rg) * q.rho0 * ir2;
+    const float H = e - K.e - 0.5f * (p + K.p) * (1.0f / K.rho - 1.0f / rho);
+    const float dH = dedr - 0.5f * (p + K.p) * ir2;
+    if (H > 0.0f) lo = rho; else hi = rho;
+    float rn = rho - H / dH;
+    if (!(rn >= lo && rn <= hi)) rn = 0.5f * (lo + hi);
+    const bool conv = fabsf(rn - rho) <= 1e-6f * rn;
+    rho = rn;
+    if (conv) {
+      const float ir = 1.0f / rho;
+      mg_ref<float>(q, 1.0f - q.rho0 * ir, pR, dpR, eR, deR);
+      const float dedn = (deR - dpR * q.inv_rg) * q.rho0 * ir * ir;
+      const float Hp = q.inv_rg - 0.5f * (1.0f / K.rho - ir);
+      const float Hr = dedn - 0.5f * (p + K.p) * ir * ir;
+      rho_out = rho;
+      drdp = -Hp / Hr;
+      return true;
+    }
+  }
+  return false;
+}
+
+__device__ inline bool mg_rhs_f(const EosP<float>& q, float p, float rho, float& drho, float& dfv) {
+  float e, c2;
+  if (!eos_e_c2<float>(q, rho, 1.0f / rho, p, e, c2)) return false;
+  drho = 1.0f / c2;
+  dfv = 1.0f / (rho * sqrtf(c2));
+  return true;
+}
+
+__device__ inline bool wave_mg_f(const EosP<float>& q, const SideF& K, float p, float& f, float& df) {
+  const float dp = p - K.p, z = K.rho * K.c;
+  if (fabsf(dp) <= 1e-5f * z * K.c) {  // acoustic start for rounding-level waves
+    f = dp / z;
+    df = 1.0f / z;
+    return true;
+  }
+  if (p > K.p) {
+    float rho, drdp;
+    if (!mg_hugoniot_f(q, K, p, rho, drdp)) return false;
+    const float dv = 1.0f / K.rho - 1.0f / rho;
+    const float fv = sqrtf(dp * dv);
+    if (!(fv > 0.0f)) return false;
+    f = fv;
+    df = (dv + dp * drdp / (rho * rho)) / (2.0f * fv);
+    return true;
+  }
+  float nsd = ceilf((float)kRk4Steps * fabsf(dp) / q.rk4_span);
+  nsd = nsd >= 1.0f ? (nsd > (float)kRk4Steps ? (float)kRk4Steps : nsd) : 1.0f;
+  const int ns = (int)nsd;
+  const float hs = dp / (float)ns;
+  float rho = K.rho, fv = 0.0f;
+  for (int i = 0; i < ns; ++i) {
+    const float pi = K.p + (float)i * hs;
+    float k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
+    if (!mg_rhs_f(q, pi, rho, k1r, k1f) || !mg_rhs_f(q, pi + 0.5f * hs, rho + 0.5f * hs * k1r, k2r, k2f) ||
+        !mg_rhs_f(q, pi + 0.5f * hs, rho + 0.5f * hs * k2r, k3r, k3f) ||
+        !mg_rhs_f(q, pi + hs, rho + hs * k3r, k4r, k4f))
+      return false;
+    rho = rho + hs / 6.0f * (k1r + 2.0f * k2r + 2.0f * k3r + k4r);
+    fv = fv + hs / 6.0f * (k1f + 2.0f * k2f + 2.0f * k3f + k4f);
+  }
+  float e, c2;
+  if (!eos_e_c2<float>(q, rho, 1.0f / rho, p, e, c2)) return false;
+  f = fv;
+  df = 1.0f / (rho * sqrtf(c2));
+  return true;
+}
+
+// F(p) = f_L + f_R + (u_R - u_L) and its slope on the FP32 curves; false if a
+// curve is undefined at p or F is not finite (the caller checks the slope).
+__device__ inline bool riemann_F_f(const EosP<float>& qL, const SideF& L, const EosP<float>& qR, const SideF& Rs,
+                                   float p, float& F, float& dF) {
+  float fL, dfL, fR, dfR;
+  const bool okL = qL.type == M2C_EOS_SG ? wave_sg_f(qL, L, p, fL, dfL) : wave_mg_f(qL, L, p, fL, dfL);
+  if (!okL) return false;
+  const bool okR = qR.type == M2C_EOS_SG ? wave_sg_f(qR, Rs, p, fR, dfR) : wave_mg_f(qR, Rs, p, fR, dfR);
+  if (!okR) return false;
+  F = fL + fR + (Rs.u - L.u);
+  dF = dfL + dfR;
+  return isfinite(F);
+}
+
+// FP32 Newton on p* from the PVRS guess; false if it fails, signals a vacuum
+// or does not reach |dp| <= 1e-5 |p| in 30 steps.
+__device__ inline bool riemann_newton_f(const EosP<float>& qL, float rl, float ul, float pl, const EosP<float>& qR,
+                                        float rr, float ur, float pr, float& p_out, int& iters) {
+  SideF L, Rs;
+  if (!make_side_f(qL, rl, ul, pl, L) || !make_side_f(qR, rr, ur, pr, Rs)) return false;
+  const float plow = fmaxf(eos_plow_f(qL), eos_plow_f(qR));
+  float F, dF;
+  if (isfinite(plow)) {
+    if (!riemann_F_f(qL, L, qR, Rs, plow, F, dF) || F >= 0.0f) return false;
+  }
+  float p = 0.5f * (L.p + Rs.p) - 0.125f * (Rs.u - L.u) * (L.rho + Rs.rho) * (L.c + Rs.c);
+  if (!(p > plow)) {
+    float gap = fminf(L.p, Rs.p) - plow;
+    if (!(gap > 0.0f)) gap = fmaxf(L.p, Rs.p) - plow;
+    p = plow + 1e-3f * gap;
+  }
+  for (int it = 1; it <= 30; ++it) {
+    if (!riemann_F_f(qL, L, qR, Rs, p, F, dF) || !(dF > 0.0f)) return false;
+    float pn = p - F / dF;
+    if (!(pn > plow)) pn = 0.5f * (p + plow);
+    const bool small = fabsf(pn - p) <= 1e-5f * fabsf(pn);
+    p = pn;
+    if (small) {
+      p_out = p;
+      iters = it;
+      return true;
+    }
+  }
+  return false;
+}
+
+__device__ inline int riemann_solve_mixed(const EosP<float>& qLf, const EosDev& qL, double rl, double ul, double pl,
+                                          const EosP<float>& qRf, const EosDev& qR, double rr, double ur, double pr,
+                                          RiemannOut& out, int& iters) {
+  float p32;
+  int it32 = 0;
+  Side L, Rs;
+  if (riemann_newton_f(qLf, d2f(rl), d2f(ul), d2f(pl), qRf, d2f(rr), d2f(ur), d2f(pr), p32, it32) &&
+      make_side(qL, rl, ul, pl, L) && make_side(qR, rr, ur, pr, Rs)) {
+    const double plow = fmax(eos_plow(qL), eos_plow(qR));
+    double p = f2d(p32);
+    for (int k = 0; k < 2; ++k) {
+      double fL, dfL, rL, dL = 0.0, fR, dfR, rR, dR = 0.0;
+      if (!(p > plow) || wave(qL, L, p, fL, dfL, rL, true, &dL) || wave(qR, Rs, p, fR, dfR, rR, true, &dR)) break;
+      const double F = fL + fR + (Rs.u - L.u), dF = dfL + dfR;
+      const double dp = -F / dF;
+      // a slope that is not finite (a wave of rounding-level strength on a
+      // shock curve) leaves the problem to the FP64 iteration
+      if (!(isfinite(dF) && dF > 0.0 && isfinite(dL) && isfinite(dR) && fabs(dp) <= 1e-5 * fabs(p) &&
+            p + dp > plow))
+        break;
+      if (k == 1 || fabs(dp) <= 1e-7 * fabs(p)) {
+        out.p = p + dp;
+        out.u = 0.5 * (L.u + Rs.u) + 0.5 * (fR - fL) + 0.5 * (dfR - dfL) * dp;
+        out.rhoL = rL + dL * dp;
+        out.rhoR = rR + dR * dp;
+        iters = it32 + 1 + k;
+        return M2C_OK;
+      }
+      p += dp;
+    }
+  }
+  return riemann_solve(qL, rl, ul, pl, qR, rr, ur, pr, out, iters);
 }
 
 }  // namespace m2c

@@ -658,7 +658,14 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
     double Fa[5] = {0, 0, 0, 0, 0}, Fb[5] = {0, 0, 0, 0, 0};
     RiemannOut rs;
     int its = 0;
-    int st = ok ? riemann_solve(qa, Pa[0], Pa[1 + d], Pa[4], qb, Pb[0], Pb[1 + d], Pb[4], rs, its) : M2C_ENONPHYS;
+    int st = M2C_ENONPHYS;
+    if (ok) {
+      if (G.prec == M2C_MIXED)
+        st = riemann_solve_mixed(G.eosf[ia], qa, Pa[0], Pa[1 + d], Pa[4], G.eosf[ib], qb, Pb[0], Pb[1 + d], Pb[4], rs,
+                                 its);
+      else
+        st = riemann_solve(qa, Pa[0], Pa[1 + d], Pa[4], qb, Pb[0], Pb[1 + d], Pb[4], rs, its);
+    }
     if (st == M2C_OK) {
       FaceState<double> A, SA, SB, B;
       double Sa[5] = {rs.rhoL, Pa[1], Pa[2], Pa[3], rs.p};
@@ -953,11 +960,14 @@ __global__ void k_prims_to_state(const Grid* __restrict__ grids, const double* _
 
 __global__ void k_riemann_batch(int n, EosDev qL, const double* __restrict__ L, EosDev qR,
                                 const double* __restrict__ Rr, double* __restrict__ out, int* __restrict__ iters,
-                                int* __restrict__ status) {
+                                int* __restrict__ status, int mixed, EosP<float> qLf, EosP<float> qRf) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     RiemannOut o;
     int its = 0;
-    const int st = riemann_solve(qL, L[i], L[n + i], L[2 * n + i], qR, Rr[i], Rr[n + i], Rr[2 * n + i], o, its);
+    const int st =
+        mixed ? riemann_solve_mixed(qLf, qL, L[i], L[n + i], L[2 * n + i], qRf, qR, Rr[i], Rr[n + i], Rr[2 * n + i], o,
+                                    its)
+              : riemann_solve(qL, L[i], L[n + i], L[2 * n + i], qR, Rr[i], Rr[n + i], Rr[2 * n + i], o, its);
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
     out[i] = st ? nan : o.p;
     out[n + i] = st ? nan : o.u;
@@ -1640,8 +1650,9 @@ m2c_status m2c_get_stats(m2c_ctx* c, m2c_stats* out) {
   return M2C_OK;
 }
 
-m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
-                             const double* R, double* out, int* iters, int* status, int on_device, void* stream) {
+static m2c_status solve_riemann_batch(int mixed, int n, const m2c_eos_desc* eosL, const double* L,
+                                      const m2c_eos_desc* eosR, const double* R, double* out, int* iters, int* status,
+                                      int on_device, void* stream) {
   if (n < 0 || !eosL || !eosR || !L || !R || !out) return M2C_EINVAL;
   if (n == 0) return M2C_OK;
   double pl[6] = {0, 0, 0, 0, 0, -INFINITY}, pr[6] = {0, 0, 0, 0, 0, -INFINITY};
@@ -1650,11 +1661,12 @@ m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, c
     pr[i] = eosR->params[i];
   }
   const EosDev qL = make_eos_dev(eosL->type, pl), qR = make_eos_dev(eosR->type, pr);
+  const EosP<float> qLf = make_eos<float>(eosL->type, pl), qRf = make_eos<float>(eosR->type, pr);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int threads = 128;
   const int blocks = (int)std::min<long long>((n + threads - 1) / threads, 4ll * sm_count());
   if (on_device) {
-    k_riemann_batch<<<blocks, threads, 0, s>>>(n, qL, L, qR, R, out, iters, status);
+    k_riemann_batch<<<blocks, threads, 0, s>>>(n, qL, L, qR, R, out, iters, status, mixed, qLf, qRf);
     return cudaGetLastError() == cudaSuccess ? M2C_OK : M2C_ECUDA;
   }
   double *dL = nullptr, *dR = nullptr, *dO = nullptr;
@@ -1667,7 +1679,7 @@ m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, c
   } else {
     cudaMemcpyAsync(dL, L, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dR, R, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
-    k_riemann_batch<<<blocks, threads, 0, s>>>(n, qL, dL, qR, dR, dO, dI, dS);
+    k_riemann_batch<<<blocks, threads, 0, s>>>(n, qL, dL, qR, dR, dO, dI, dS, mixed, qLf, qRf);
     std::vector<int> hs(n);
     cudaMemcpyAsync(out, dO, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(hs.data(), dS, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
@@ -1680,6 +1692,17 @@ m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, c
   }
   cudaFree(dL); cudaFree(dR); cudaFree(dO); cudaFree(dI); cudaFree(dS);
   return st;
+}
+
+m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
+                             const double* R, double* out, int* iters, int* status, int on_device, void* stream) {
+  return solve_riemann_batch(0, n, eosL, L, eosR, R, out, iters, status, on_device, stream);
+}
+
+m2c_status m2c_solve_riemann_mixed(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
+                                   const double* R, double* out, int* iters, int* status, int on_device,
+                                   void* stream) {
+  return solve_riemann_batch(1, n, eosL, L, eosR, R, out, iters, status, on_device, stream);
 }
 
 m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]) {

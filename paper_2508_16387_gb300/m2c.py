@@ -76,6 +76,7 @@ def lib():
         L.m2c_sync.argtypes = [p, p, p, p]
         L.m2c_get_stats.argtypes = [p, ctypes.POINTER(Stats)]
         L.m2c_solve_riemann.argtypes = [i, ctypes.POINTER(EosDesc), p, ctypes.POINTER(EosDesc), p, p, p, p, i, p]
+        L.m2c_solve_riemann_mixed.argtypes = L.m2c_solve_riemann.argtypes
         L.m2c_shock_state.argtypes = [ctypes.POINTER(EosDesc), p, d, p]
         L.m2c_residual_noalloc_scratch_bytes.restype = z
         L.m2c_residual_noalloc_scratch_bytes.argtypes = []
@@ -136,19 +137,20 @@ def m2c_batch_workspace_bytes(k) -> int:
     return lib().m2c_batch_workspace_bytes(k)
 
 
-def m2c_solve_riemann(eosL, L, eosR, R, stream=None):
+def m2c_solve_riemann(eosL, L, eosR, R, stream=None, mixed=False):
     """Batch Riemann solve on device tensors L, R of shape (3, n) float64 (rho, u, p).
-    Returns (out (4, n): p*, u*, rho*_L, rho*_R; iters (n,); status (n,))."""
+    Returns (out (4, n): p*, u*, rho*_L, rho*_R; iters (n,); status (n,)).
+    mixed=True: the mixed path's solve (m2c_solve_riemann_mixed)."""
     import torch
     n = L.shape[1]
     out = torch.empty((4, n), dtype=torch.float64, device=L.device)
     iters = torch.zeros(n, dtype=torch.int32, device=L.device)
     status = torch.zeros(n, dtype=torch.int32, device=L.device)
     eL, eR = eos_desc(eosL), eos_desc(eosR)
-    code = lib().m2c_solve_riemann(n, ctypes.byref(eL), _ptr(L.contiguous()), ctypes.byref(eR),
-                                   _ptr(R.contiguous()), _ptr(out), _ptr(iters), _ptr(status), 1,
-                                   _stream_handle(stream))
-    _check(code, "m2c_solve_riemann")
+    fn = lib().m2c_solve_riemann_mixed if mixed else lib().m2c_solve_riemann
+    code = fn(n, ctypes.byref(eL), _ptr(L.contiguous()), ctypes.byref(eR), _ptr(R.contiguous()), _ptr(out),
+              _ptr(iters), _ptr(status), 1, _stream_handle(stream))
+    _check(code, "m2c_solve_riemann_mixed" if mixed else "m2c_solve_riemann")
     return out, iters, status
 
 

@@ -90,6 +90,47 @@ def test_riemann_batch_matches_oracle(m2c, pair):
     assert np.array_equal(it[ok], rit[ok])
 
 
+@pytest.mark.parametrize("pair", ["sg_pg", "mg_pg", "pg_mg", "sg_sg", "mg_mg"])
+def test_riemann_mixed_batch_matches_oracle(m2c, pair):
+    """The mixed path's Riemann solve (FP32 Newton, then FP64 Newton steps) against the
+    FP64 oracle on wide random states and on near-equilibrium states like those at a
+    bubble surface at rest, down to rounding-level differences (where a shock curve's
+    slope is not finite in FP64 and the FP64 iteration takes over)."""
+    import torch
+    rng = np.random.default_rng(12)
+    n = 4096
+    eos = {"sg": WL.WATER_SG, "pg": WL.AIR_PG, "mg": WL.WATER_MG}
+    a, b = pair.split("_")
+    eL, eR = eos[a], eos[b]
+
+    def states(kind, quiet):
+        if quiet is not None:  # 1e5 Pa at rest with relative perturbations of size quiet
+            rho = 1.2 if kind == "pg" else 1000.0
+            return np.stack([rho * (1 + quiet * rng.standard_normal(n)), 10 * quiet * rng.standard_normal(n),
+                             1e5 * (1 + quiet * rng.standard_normal(n))])
+        if kind == "pg":
+            return np.stack([rng.uniform(0.5, 5.0, n), rng.uniform(-300, 300, n), rng.uniform(5e4, 5e6, n)])
+        return np.stack([rng.uniform(950, 1250, n), rng.uniform(-300, 300, n), rng.uniform(1e5, 2e9, n)])
+    for quiet in (None, 1e-4, 1e-8, 1e-12, 0.0):
+        L, R = states(a, quiet), states(b, quiet)
+        ref, _, rst = O.riemann_batch(O.EOS(*eL), L, O.EOS(*eR), R)
+        out, it, st = m2c.m2c_solve_riemann(eL, torch.from_numpy(L).cuda(), eR, torch.from_numpy(R).cuda(),
+                                            mixed=True)
+        out, st = out.cpu().numpy(), st.cpu().numpy()
+        assert np.array_equal(st, rst)
+        ok = rst == 0
+        assert ok.mean() > 0.9
+        assert np.isfinite(out[:, ok]).all()
+        uscale = np.maximum(np.maximum(np.abs(L[1]), np.abs(R[1])), 1.0)[ok]
+        # 1e-9: the two iterations stop at different points of the RK4 rarefaction
+        # curve, whose substep count changes with |p - p_K| (a jump of the order of
+        # its truncation error), so their roots agree to that error, not to rounding
+        assert np.max(np.abs(out[0][ok] - ref[0][ok]) / np.abs(ref[0][ok])) < 1e-9, quiet
+        assert np.max(np.abs(out[1][ok] - ref[1][ok]) / uscale) < 1e-8, quiet  # same reason, through f(p*)
+        for v in (2, 3):
+            assert np.max(np.abs(out[v][ok] - ref[v][ok]) / ref[v][ok]) < 1e-9, (quiet, v)
+
+
 def test_riemann_host_arrays_and_shock_state(m2c):
     L = np.array([[1000.0], [0.0], [1e9]])
     R = np.array([[1.0], [0.0], [1e5]])
