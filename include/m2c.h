@@ -64,9 +64,9 @@ typedef enum { M2C_EOS_SG = 0, M2C_EOS_MG = 1 } m2c_eos_type;
 
 /* M2C_FP64: every operation in FP64. M2C_MIXED: reconstruction, HLLC, the
  * level-set residual and the reinitialisation update in FP32; the pressure
- * from the conserved state, the Runge-Kutta accumulation of W and phi and the
- * level-set values in FP64; the exact Riemann solver iterates in FP32 and
- * finishes with FP64 Newton steps (m2c_solve_riemann_mixed). */
+ * from the conserved state, the Runge-Kutta accumulation of W and phi, the
+ * level-set values and the exact Riemann solver's Newton iteration in FP64
+ * (m2c_set_riemann_start offers an FP32 start for the latter). */
 typedef enum { M2C_FP64 = 0, M2C_MIXED = 1 } m2c_precision;
 
 /* Boundary conditions per side (x-, x+, y-, y+, z-, z+): transmissive
@@ -107,6 +107,13 @@ m2c_status m2c_set_eos(m2c_ctx* ctx, int material, int type, const double* param
  * axes with more than one cell), and the reinitialisation schedule: after every
  * reinit_every-th step, reinit_iters pseudo-time iterations (0 disables). */
 m2c_status m2c_set_scheme(m2c_ctx* ctx, double cfl, int reinit_every, int reinit_iters);
+
+/* M2C_MIXED grids only (M2C_EINVAL otherwise for fp32_start = 1). fp32_start
+ * = 0 (default): the FIVER kernel runs the FP64 Newton iteration of
+ * m2c_solve_riemann. fp32_start = 1: it starts the iteration on FP32 wave
+ * curves and finishes with FP64 Newton steps, as m2c_solve_riemann_mixed
+ * (an option beyond the paper's method, which does not discuss precision). */
+m2c_status m2c_set_riemann_start(m2c_ctx* ctx, int fp32_start);
 
 /* Tile of the bulk stage kernel: 32 x tile_rows (4 or 8; 16 for M2C_MIXED)
  * columns marching tile_z cells along z (0: automatic). Results do not depend

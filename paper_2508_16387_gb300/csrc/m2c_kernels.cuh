@@ -70,6 +70,9 @@ struct Grid {
   int tiles_x, tiles_y, tiles_z, tz;
   // reinitialisation after every reinit_every-th step (0: never), reinit_iters iterations
   int reinit_every, reinit_iters;
+  // M2C_MIXED only: 1 = the FIVER Newton iteration starts on FP32 wave curves
+  // and finishes with FP64 steps (riemann_solve_mixed); 0 = FP64 throughout
+  int riemann_fp32_start, pad2;
 };
 
 enum StageMode { kStage1 = 0, kStage2 = 1, kResidual = 2 };

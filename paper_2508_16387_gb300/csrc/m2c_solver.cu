@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
     int its = 0;
     int st = M2C_ENONPHYS;
     if (ok) {
-      if (G.prec == M2C_MIXED)
+      if (G.prec == M2C_MIXED && G.riemann_fp32_start)
         st = riemann_solve_mixed(G.eosf[ia], qa, Pa[0], Pa[1 + d], Pa[4], G.eosf[ib], qb, Pb[0], Pb[1 + d], Pb[4], rs,
                                  its);
       else
@@ -1373,6 +1373,14 @@ m2c_status m2c_set_scheme(m2c_ctx* c, double cfl, int reinit_every, int reinit_i
   c->reinit_iters = reinit_iters;
   c->host.reinit_every = reinit_every;
   c->host.reinit_iters = reinit_iters;
+  return push_grid(c);
+}
+
+m2c_status m2c_set_riemann_start(m2c_ctx* c, int fp32_start) {
+  if (!c || (fp32_start != 0 && fp32_start != 1)) return M2C_EINVAL;
+  if (fp32_start && c->host.prec != M2C_MIXED)
+    return set_err(c, M2C_EINVAL, "the FP32 Riemann start is an option of M2C_MIXED grids");
+  c->host.riemann_fp32_start = fp32_start;
   return push_grid(c);
 }
 

@@ -67,6 +67,7 @@ def lib():
         L.m2c_set_eos.argtypes = [p, i, i, p, i]
         L.m2c_set_scheme.argtypes = [p, d, i, i]
         L.m2c_set_tiling.argtypes = [p, i, i]
+        L.m2c_set_riemann_start.argtypes = [p, i]
         L.m2c_set_state.argtypes = [p, p, p, d, L_]
         L.m2c_prims_to_state.argtypes = [p, p]
         L.m2c_upload_state.argtypes = [p, p, p]
@@ -243,6 +244,9 @@ class Grid:
 
     def set_tiling(self, tile_rows=8, tile_z=0):
         _check(lib().m2c_set_tiling(self.ctx, tile_rows, tile_z), "m2c_set_tiling", self.ctx)
+
+    def set_riemann_start(self, fp32_start=True):
+        _check(lib().m2c_set_riemann_start(self.ctx, 1 if fp32_start else 0), "m2c_set_riemann_start", self.ctx)
 
     # -- state
     def set_state(self, W=None, phi=None, t=0.0, step=0):

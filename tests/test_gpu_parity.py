@@ -273,14 +273,22 @@ def _block_l1(a, b, k=4):
     return float(np.abs(A - B).sum() / np.abs(B).sum())
 
 
-def test_mixed_precision_l1_error_against_fp64(m2c):
-    """Mixed precision (FP32 reconstruction and HLLC, FP64 accumulation and Riemann solver) on the
-    MG shock-bubble setup at 64^3 after the shock has reached the bubble: relative L1 error of
-    4^3-block averages of density and pressure against the FP64 path <= 1e-4."""
+@pytest.mark.parametrize("fp32_start", [False, True])
+def test_mixed_precision_l1_error_against_fp64(m2c, fp32_start):
+    """Mixed precision (FP32 reconstruction and HLLC, FP64 accumulation and Riemann solver; with
+    fp32_start the Riemann iteration starts on FP32 curves) on the MG shock-bubble setup at 64^3
+    after the shock has reached the bubble: relative L1 error of 4^3-block averages of density
+    and pressure against the FP64 path <= 1e-4."""
     s = WL.shock_bubble(n=64, water=WL.WATER_MG, steps=100)
     out = {}
     for prec in (0, 1):
         g = gpu_start(m2c, s, prec)
+        if fp32_start:
+            if prec == 0:  # an option of mixed grids only
+                with pytest.raises(m2c.M2CError):
+                    g.set_riemann_start(True)
+            else:
+                g.set_riemann_start(True)
         g.step(100)
         g.sync()
         W = g.W.cpu().numpy()
