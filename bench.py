@@ -37,7 +37,7 @@ UNIT = "Mcell-updates/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="grid edge")
@@ -85,6 +85,9 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()  # the first sample marks the sampler as running (nvidia-smi starts slowly)
+            while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except OSError:
             self.proc = None
         return self
@@ -215,8 +218,8 @@ def ncu_traffic(kind, n):
         return None
 
 
-def cpu_baseline(n=128, steps=2):
-    """The oracle, as it stands, on the 128^3 version of the same workload (bounded sample)."""
+def cpu_baseline(n=256, steps=8):
+    """The oracle, as it stands, on the same 256^3 workload for a bounded number of steps."""
     from oracle import oracle as O
     s = setup(n)
     g = O.Grid(n=s.n, h=s.h, eos=tuple(O.EOS(*e) for e in s.eos), bc=s.bc, cfl=s.cfl,
@@ -229,8 +232,7 @@ def cpu_baseline(n=128, steps=2):
     O.run(g, W, s.phi, steps)
     dt = time.perf_counter() - t0
     return {"value": s.ncells * steps / dt / 1e6, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{steps} oracle time steps of the {n}^3 version of the same MG shock-bubble setup "
-                      f"({dt:.1f} s wall)"}
+            "sample": f"{steps} oracle time steps of the {n}^3 MG shock-bubble setup ({dt:.1f} s wall)"}
 
 
 def run_ours(args):

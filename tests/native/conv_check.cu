@@ -3,8 +3,9 @@
 // nearest, ties to even). f2d is checked on every binary32 value; d2f on every
 // binary32 value, the binary64 neighbours of each, the midpoints between
 // adjacent binary32 values and their neighbours (the rounding ties), and
-// random bit patterns. Prints the number of mismatches and exits non-zero on
-// any.
+// random bit patterns; the bit-level sign tests lt0/gt0 against x < 0 and
+// x > 0 on the same values. Prints the number of mismatches and exits
+// non-zero on any.
 #include <cstdio>
 #include <cstdint>
 #include <cmath>
@@ -16,11 +17,17 @@ using m2c::f2d;
 using m2c::bits_of;
 using m2c::double_of;
 using m2c::float_of;
+using m2c::lt0;
+using m2c::gt0;
 
 static long long bad = 0;
 
 static void check_d2f(unsigned long long b) {
   const double x = double_of(b);
+  if (lt0(x) != (x < 0.0) || gt0(x) != (x > 0.0)) {
+    if (bad < 10) std::printf("sign %016llx: lt0 %d gt0 %d\n", b, (int)lt0(x), (int)gt0(x));
+    ++bad;
+  }
   const float want = (float)x, got = d2f(x);
   if (std::isnan(want) ? !std::isnan(got) : bits_of(want) != bits_of(got)) {
     if (bad < 10) std::printf("d2f %016llx: got %08x want %08x\n", b, bits_of(got), bits_of(want));
