@@ -660,11 +660,28 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
     int its = 0;
     int st = M2C_ENONPHYS;
     if (ok) {
+      // material 0 is put on the left of the 1D problem (the mirror image, normal
+      // velocities negated, when it is on the plus side), so that every lane of a
+      // warp evaluates the same wave curves; the mirrored solve is the same
+      // arithmetic with the two sides exchanged (sums commute exactly), and its
+      // solution is mirrored back below
+      const bool mirror = ia > ib;
+      const EosDev& q0 = mirror ? qb : qa;
+      const EosDev& q1 = mirror ? qa : qb;
+      const double* P0 = mirror ? Pb : Pa;
+      const double* P1 = mirror ? Pa : Pb;
+      const double sgn = mirror ? -1.0 : 1.0;
       if (G.prec == M2C_MIXED && G.riemann_fp32_start)
-        st = riemann_solve_mixed(G.eosf[ia], qa, Pa[0], Pa[1 + d], Pa[4], G.eosf[ib], qb, Pb[0], Pb[1 + d], Pb[4], rs,
-                                 its);
+        st = riemann_solve_mixed(G.eosf[mirror ? ib : ia], q0, P0[0], sgn * P0[1 + d], P0[4], G.eosf[mirror ? ia : ib], q1,
+                                 P1[0], sgn * P1[1 + d], P1[4], rs, its);
       else
-        st = riemann_solve(qa, Pa[0], Pa[1 + d], Pa[4], qb, Pb[0], Pb[1 + d], Pb[4], rs, its);
+        st = riemann_solve(q0, P0[0], sgn * P0[1 + d], P0[4], q1, P1[0], sgn * P1[1 + d], P1[4], rs, its);
+      if (mirror) {
+        const double r = rs.rhoL;
+        rs.rhoL = rs.rhoR;
+        rs.rhoR = r;
+        rs.u = -rs.u;
+      }
     }
     if (st == M2C_OK) {
       FaceState<double> A, SA, SB, B;
