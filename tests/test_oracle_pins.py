@@ -152,6 +152,48 @@ def test_hllc_mirror_and_rotation_symmetry():
         assert np.allclose([H[0], H[2], H[3], H[1], H[4]], F, rtol=1e-12, atol=1e-6 * np.abs(F).max())
 
 
+@pytest.mark.parametrize("eos", [WATER, AIR])
+def test_hllc_star_state_energy_satisfies_the_jump_condition(eos):
+    """Pins the HLLC star energy (App. C.4; reading R13): when the flux is a star flux
+    F*_K = F_K + S_K (U*_K - U_K), the star state recovered from it must carry the contact
+    speed S* as its normal velocity, the side's tangential velocities, and an energy whose
+    physical flux S* ((rho E)*_K + p*) equals F*'s energy component, with
+    p* = p_K + rho_K (S_K - u_K)(S* - u_K) (the jump conditions across S_K). A dropped or
+    mis-signed term in E*_K breaks the last identity."""
+    rng = np.random.default_rng(21)
+    g = eos.prm[0]
+    base = (1000.0, 1e8) if eos is WATER else (1.2, 1e5)
+    checked = {"L": 0, "R": 0}
+    for _ in range(400):
+        qL = [base[0] * rng.uniform(0.7, 1.3), *rng.uniform(-150, 150, 3), base[1] * rng.uniform(0.3, 3.0)]
+        qR = [base[0] * rng.uniform(0.7, 1.3), *rng.uniform(-150, 150, 3), base[1] * rng.uniform(0.3, 3.0)]
+        cL, cR = (math.sqrt(O.sound_speed2(eos, q[0], q[4])) for q in (qL, qR))
+        SL, SR = min(qL[1] - cL, qR[1] - cR), max(qL[1] + cL, qR[1] + cR)
+        if not (SL < 0.0 < SR):
+            continue
+        F = O.hllc(eos, qL, qR, 0)
+        for side, q, S in (("L", qL, SL), ("R", qR, SR)):
+            U = _cons(eos, q)
+            Ustar = U + (F - _phys_flux(eos, q, 0)) / S
+            Sstar = Ustar[1] / Ustar[0]
+            # F is this side's star flux only if 0 lies between S_K and S*
+            if not ((side == "L" and Sstar >= 0.0) or (side == "R" and Sstar < 0.0)):
+                continue
+            pstar = q[4] + q[0] * (S - q[1]) * (Sstar - q[1])
+            assert Ustar[2] / Ustar[0] == pytest.approx(q[2], rel=1e-9, abs=1e-6)
+            assert Ustar[3] / Ustar[0] == pytest.approx(q[3], rel=1e-9, abs=1e-6)
+            assert F[1] == pytest.approx(Ustar[1] * Sstar + pstar, rel=1e-10)
+            assert F[4] == pytest.approx(Sstar * (Ustar[4] + pstar), rel=1e-9, abs=1e-9 * abs(U[4] * S))
+            checked[side] += 1
+    assert checked["L"] > 20 and checked["R"] > 20, checked
+
+
+def _cons(eos, q):
+    rho, u, v, w, p = q
+    E = O.energy(eos, rho, p) + 0.5 * (u * u + v * v + w * w)
+    return np.array([rho, rho * u, rho * v, rho * w, rho * E])
+
+
 # --------------------------------------------------------------------------- exact Riemann solver
 
 def _e_sg(eos, rho, p):
