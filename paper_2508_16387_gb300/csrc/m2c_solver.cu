@@ -132,9 +132,13 @@ __device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, co
   return to_d<R>(wave_sum_v<R>(g, q, qd, w, ok));
 }
 
-__device__ __forceinline__ double wave_sum(const Grid& g, const EosDev& q, const double* W, long long N, long long c,
+// The same in the grid's precision, for material m: every wave-speed maximum
+// of a grid (first step, bulk, interface and flipped cells) is taken the same
+// way, so that a step from a restored state repeats the uninterrupted one.
+__device__ __forceinline__ double wave_sum(const Grid& g, int m, const double* W, long long N, long long c,
                                            bool& ok) {
-  return wave_sum_r<double>(g, q, q, W, N, c, ok);
+  if (g.prec == M2C_MIXED) return wave_sum_r<float>(g, g.eosf[m], g.eos[m], W, N, c, ok);
+  return wave_sum_r<double>(g, g.eos[m], g.eos[m], W, N, c, ok);
 }
 
 __device__ __forceinline__ double warp_max(double v) {
@@ -751,7 +755,7 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
       const bool flip = lt0(G.phi[c]) != (id0 == 1);
       if (!flip) {
         bool ok;
-        const double lam = wave_sum(G, G.eos[id0], G.W, N, c, ok);
+        const double lam = wave_sum(G, id0, G.W, N, c, ok);
         if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
         lam_max = fmax(lam_max, lam);
       }
@@ -901,7 +905,7 @@ __global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grid
       const double pv = G.phi[c];
       G.phi[c] = old_id ? -fmax(fabs(pv), 1e-12 * G.h) : fabs(pv);
       bool ok;
-      const double lam = wave_sum(G, G.eos[old_id], G.W, N, c, ok);
+      const double lam = wave_sum(G, old_id, G.W, N, c, ok);
       if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
       lam_max = fmax(lam_max, lam);
       continue;
@@ -917,7 +921,7 @@ __global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grid
     G.W[3 * N + c] = P[0] * P[3];
     G.W[4 * N + c] = P[0] * e + 0.5 * P[0] * ((P[1] * P[1] + P[2] * P[2]) + P[3] * P[3]);
     bool ok;
-    const double lam = wave_sum(G, q, G.W, N, c, ok);
+    const double lam = wave_sum(G, m, G.W, N, c, ok);
     lam_max = fmax(lam_max, lam);
   }
   block_max_to(lam_max, &ctrl->lam[(ctrl->step + 1) & 1], s_red);
@@ -952,7 +956,7 @@ __global__ void __launch_bounds__(256) k_lam_init(const Grid* __restrict__ grids
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x) {
     const int m = lt0(G.phi[c]) ? 1 : 0;
     bool ok;
-    const double lam = wave_sum(G, G.eos[m], G.W, G.N, c, ok);
+    const double lam = wave_sum(G, m, G.W, G.N, c, ok);
     if (!ok) latch_error(G.ctrl, M2C_ENONPHYS, c);
     lam_max = fmax(lam_max, lam);
   }

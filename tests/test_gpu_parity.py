@@ -237,17 +237,18 @@ def test_single_material_periodic_conserves(m2c):
         assert abs(W[v].sum() - W0[v].sum()) <= 1e-13 * np.abs(W0[v]).sum()
 
 
-def test_checkpoint_restart_is_bitwise(m2c):
-    s = WL.shock_bubble(n=32, radius=0.2, steps=20)
-    g = gpu_start(m2c, s)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_checkpoint_restart_is_bitwise(m2c, prec):
+    s = WL.shock_bubble(n=32, radius=0.2, steps=20, water=WL.WATER_MG if prec else WL.WATER_SG)
+    g = gpu_start(m2c, s, prec)
     g.step(20)
     g.sync()
     W_full = g.W.cpu().numpy()
-    g2 = gpu_start(m2c, s)
+    g2 = gpu_start(m2c, s, prec)
     g2.step(10)
     t, k = g2.sync()
     Wm, pm = g2.W.cpu().numpy(), g2.phi.cpu().numpy()
-    g3 = m2c.Grid(s.n, s.h, s.bc, s.eos)
+    g3 = m2c.Grid(s.n, s.h, s.bc, s.eos, precision=prec)
     g3.set_state(Wm, pm, t=t, step=k)
     g3.step(10)
     g3.sync()
