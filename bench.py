@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-variant", action="store_true", help="skip the FP32-Riemann-start line")
+    ap.add_argument("--l1-steps", type=int, default=300,
+                    help="steps of the mixed-vs-FP64 L1 check after the timed runs (0: skip)")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"], help="precision of the headline run")
     ap.add_argument("--workload", default="grid256", choices=["grid256", "batched", "served"])
     ap.add_argument("--instances", type=int, default=64)
@@ -182,6 +184,31 @@ def e2e_run(torch, M, s, g, steps):
     return dt, nbytes
 
 
+def l1_vs_fp64(torch, M, s, steps):
+    """Mixed against FP64 on the same workload after `steps` steps from the same initial state:
+    relative L1 of 4^3-block averages (n^3 -> (n/4)^3) of density and pressure, from the
+    library's own FP64 primitive fields."""
+    prims = {}
+    for prec in (M.MIXED, M.FP64):
+        g = make_grid(M, s, prec)
+        g.step(steps)
+        g.sync()
+        prims[prec] = g.prims()
+        g.sync()
+        del g
+
+    def blocks(a):
+        nz, ny, nx = a.shape
+        return a.reshape(nz // 4, 4, ny // 4, 4, nx // 4, 4).mean(dim=(1, 3, 5))
+    res = {"steps": steps, "blocks": f"4^3 ({s.n[0]}^3 -> {s.n[0] // 4}^3)", "tolerance": 1e-4}
+    for name, v in (("rho", 0), ("p", 4)):
+        a, b = blocks(prims[M.MIXED][v]), blocks(prims[M.FP64][v])
+        res[name] = float((a - b).abs().sum() / b.abs().sum())
+    del prims
+    torch.cuda.empty_cache()
+    return res
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -301,6 +328,9 @@ def run_ours(args):
         del g64
     if rank != 0:
         return
+    l1 = None
+    if args.prec == "mixed" and not args.no_fp64 and args.l1_steps > 0:
+        l1 = l1_vs_fp64(torch, M, s, args.l1_steps)
     out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -310,7 +340,7 @@ def run_ours(args):
                       "l2": f"state ({48 * N / 1e6:.0f} MB) larger than L2, no flush"
                             if 48 * N > 129e6 else f"state ({48 * N / 1e6:.0f} MB) fits in L2"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64,
-           "mixed_fp32_riemann_start": fp32_start}
+           "mixed_fp32_riemann_start": fp32_start, "l1_error_vs_fp64": l1}
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))

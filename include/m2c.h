@@ -128,6 +128,13 @@ m2c_status m2c_set_state(m2c_ctx* ctx, double* W, double* phi, double t, long st
  * using the EOS of each cell's material (from the sign of phi). */
 m2c_status m2c_prims_to_state(m2c_ctx* ctx, const double* prims);
 
+/* The inverse: primitive fields (rho, u, v, w, p) of the current state into
+ * the device array prims (5N doubles, SoA, x fastest, caller-owned), FP64
+ * with each cell's material EOS (material 1 where phi < 0; Sec. 3.3).
+ * Asynchronous on the context's stream; a non-physical cell is latched
+ * (M2C_ENONPHYS from m2c_sync) and its entries are unspecified. */
+m2c_status m2c_state_to_prims(m2c_ctx* ctx, double* prims);
+
 /* Copies host arrays into / out of the borrowed state (pinned host memory gives
  * asynchronous copies; m2c_download_state synchronises the stream). */
 m2c_status m2c_upload_state(m2c_ctx* ctx, const double* W_host, const double* phi_host);

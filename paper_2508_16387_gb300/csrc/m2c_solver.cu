@@ -963,6 +963,20 @@ __global__ void __launch_bounds__(256) k_lam_init(const Grid* __restrict__ grids
   block_max_to(lam_max, &G.ctrl->lam[G.ctrl->step & 1], s_red);
 }
 
+// Primitive fields (rho, u, v, w, p) of the current state, FP64, with the EOS
+// of each cell's material (Sec. 3.3); the inverse of k_prims_to_state.
+__global__ void k_state_to_prims(const Grid* __restrict__ grids, double* __restrict__ prims) {
+  const Grid& G = grids[0];
+  const long long N = G.N;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const int m = lt0(G.phi[c]) ? 1 : 0;
+    double P[5];
+    if (!cons_to_prim<double>(G.eos[m], G.eos[m], G.W, N, c, P)) latch_error(G.ctrl, M2C_ENONPHYS, c);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) prims[v * N + c] = P[v];
+  }
+}
+
 __global__ void k_prims_to_state(const Grid* __restrict__ grids, const double* __restrict__ prims) {
   const Grid& G = grids[0];
   const long long N = G.N;
@@ -1444,6 +1458,14 @@ m2c_status m2c_prims_to_state(m2c_ctx* c, const double* prims) {
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return cuda_check(c, e, "prims_to_state");
+}
+
+m2c_status m2c_state_to_prims(m2c_ctx* c, double* prims) {
+  if (!c || !prims) return M2C_EINVAL;
+  if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first");
+  const dim3 g((unsigned)std::min<long long>((c->host.N + 255) / 256, 8ll * sm_count()), 1);
+  k_state_to_prims<<<g, 256, 0, c->stream>>>(c->dev_grid, prims);
+  return cuda_check(c, cudaGetLastError(), "state_to_prims");
 }
 
 m2c_status m2c_upload_state(m2c_ctx* c, const double* W_host, const double* phi_host) {

@@ -70,6 +70,7 @@ def lib():
         L.m2c_set_riemann_start.argtypes = [p, i]
         L.m2c_set_state.argtypes = [p, p, p, d, L_]
         L.m2c_prims_to_state.argtypes = [p, p]
+        L.m2c_state_to_prims.argtypes = [p, p]
         L.m2c_upload_state.argtypes = [p, p, p]
         L.m2c_download_state.argtypes = [p, p, p]
         L.m2c_step.argtypes = [p, i]
@@ -264,6 +265,14 @@ class Grid:
         _check(lib().m2c_set_state(self.ctx, _ptr(self.W), _ptr(self.phi), t, step), "m2c_set_state", self.ctx)
         P = torch.as_tensor(prims, dtype=torch.float64).to(self.device).contiguous()
         _check(lib().m2c_prims_to_state(self.ctx, _ptr(P)), "m2c_prims_to_state", self.ctx)
+
+    def prims(self):
+        """Primitive fields (5, nz, ny, nx) of the current state (device tensor, FP64)."""
+        torch = self.torch
+        nx, ny, nz = self.n
+        P = torch.empty((5, nz, ny, nx), dtype=torch.float64, device=self.device)
+        _check(lib().m2c_state_to_prims(self.ctx, _ptr(P)), "m2c_state_to_prims", self.ctx)
+        return P
 
     def upload(self, W_host, phi_host):
         _check(lib().m2c_upload_state(self.ctx, _ptr(W_host), _ptr(phi_host)), "m2c_upload_state", self.ctx)

@@ -148,6 +148,22 @@ def test_riemann_host_arrays_and_shock_state(m2c):
     assert code == 6 and st[0] == 6
 
 
+@pytest.mark.parametrize("water", [WL.WATER_SG, WL.WATER_MG])
+def test_state_to_prims_matches_oracle(m2c, water):
+    """m2c_state_to_prims against the oracle's conversion of the same conserved state, and the
+    round trip from primitive fields, on a random two-phase state."""
+    n = (29, 17, 11)
+    P, phi = WL.random_state(n, seed=5, eos=(water, WL.AIR_PG), two_phase=True)
+    s = WL.Setup("rand", n, 1.0 / n[0], (water, WL.AIR_PG), (0, 0, 1, 1, 0, 0), phi,
+                 np.zeros(phi.shape, np.uint8), {})
+    g = gpu_start(m2c, s, prims=P)
+    G = g.prims().cpu().numpy()
+    g.sync()
+    ref = O.cons_to_prims(oracle_grid(s), g.W.cpu().numpy(), phi)
+    assert max(rel_err(G, ref)) < 1e-13
+    assert max(rel_err(G, P)) < 1e-11
+
+
 # --------------------------------------------------------------------------- one stage residual
 
 @pytest.mark.parametrize("n,two_phase,water", [((70, 19, 13), True, WL.WATER_SG), ((45, 33, 9), True, WL.WATER_MG),
