@@ -1,0 +1,150 @@
+// Device helpers shared by the kernels of libm2cgpu: conservative to
+// primitive conversion, face states, wave-speed sums and block reductions.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "m2c_kernels.cuh"
+
+namespace m2c {
+
+// ---------------------------------------------------------------------------
+// Conservative -> primitive
+// ---------------------------------------------------------------------------
+
+// FP64 path: u = (rho u)/rho, e = (rho E - rho|V|^2/2)/rho, p = p(rho, e).
+// Mixed path: the same with FP32 velocities and kinetic energy; rho e and, for
+// the stiffened gas, the pressure (a difference of large numbers when p_c is
+// large) in FP64, then rounded to FP32.
+template <typename R>
+__device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& qd, double rho, double m1, double m2,
+                                               double m3, double E, R P[5]) {
+  if constexpr (sizeof(R) == 8) {
+    const double inv = 1.0 / rho;
+    const double u = m1 * inv, v = m2 * inv, w = m3 * inv;
+    const double ke = 0.5 * ((m1 * u + m2 * v) + m3 * w);
+    const double e = (E - ke) * inv;
+    double p = 0.0;
+    const bool ok = eos_p<double>(q, rho, inv, e, p);
+    P[0] = rho; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
+    return ok && rho > 0.0;
+  } else {
+    const float rf = d2f(rho);
+    const float inv = rrcp<float>(rf);
+    const float f1 = d2f(m1), f2 = d2f(m2), f3 = d2f(m3);
+    const float u = f1 * inv, v = f2 * inv, w = f3 * inv;
+    const float ke = 0.5f * ((f1 * u + f2 * v) + f3 * w);
+    const double rhoe = E - f2d(ke);
+    float p = 0.0f;
+    bool ok = true;
+    if (q.type == M2C_EOS_SG) {
+      p = d2f(qd.gm1 * rhoe - qd.gpc);
+    } else {
+      ok = eos_p<float>(q, rf, inv, d2f(rhoe) * inv, p);
+    }
+    P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
+    return ok && gt0(rho);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd, const double* __restrict__ W,
+                                             long long N, long long c, R P[5]) {
+  return cons_to_prim_v<R>(q, qd, W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c], P);
+}
+
+template <typename R>
+__device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w, R p, FaceState<R>& F) {
+  R e = (R)0, c2 = (R)0;
+  const bool ok = eos_e_c2<R>(q, rho, rrcp<R>(rho), p, e, c2);
+  F.rho = rho; F.u = u; F.v = v; F.w = w; F.p = p;
+  F.c = ok ? rsqrt_pos<R>(c2) : (R)0;
+  F.E = e + (R)0.5 * ((u * u + v * v) + w * w);
+  return ok;
+}
+
+// MUSCL face states of one cell along one axis: q -+ sigma/2 with the modified
+// van Albada slope (App. D). same = both stencil neighbours have the cell's
+// material (otherwise first order, Reading R11); a non-admissible face state
+// makes the whole axis first order (Reading R12). bad: even the cell state is
+// not admissible.
+template <typename R>
+__device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], const R P[5], const R Pp[5], bool same,
+                                           FaceState<R>& Qm, FaceState<R>& Qp, bool& bad) {
+  if (same) {
+    R s[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s[v] = va_slope<R>(P[v] - Pm[v], Pp[v] - P[v]);
+    const R hf = (R)0.5;
+    const bool okm = make_face<R>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2], P[3] - hf * s[3],
+                                  P[4] - hf * s[4], Qm);
+    const bool okp = make_face<R>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2], P[3] + hf * s[3],
+                                  P[4] + hf * s[4], Qp);
+    if (okm && okp) return;
+  }
+  if (!make_face<R>(q, P[0], P[1], P[2], P[3], P[4], Qm)) bad = true;
+  Qp = Qm;
+}
+
+// Wave-speed sum of a state, sum over the axes with more than one cell of
+// |V_d| + c (the CFL reading of the design notes), in precision R (the mixed
+// path takes the time step from FP32 wave speeds of the FP64 state).
+template <typename R>
+__device__ __forceinline__ R wave_sum_v(const Grid& g, const EosP<R>& q, const EosDev& qd, const double w[5], bool& ok) {
+  R P[5];
+  ok = cons_to_prim_v<R>(q, qd, w[0], w[1], w[2], w[3], w[4], P);
+  R e, c2;
+  ok = ok && eos_e_c2<R>(q, P[0], rrcp<R>(P[0]), P[4], e, c2);
+  const R cs = ok ? rsqrt_pos<R>(c2) : (R)0;
+  R lam = (R)0;
+  if (g.active[0]) lam = lam + (fabs(P[1]) + cs);
+  if (g.active[1]) lam = lam + (fabs(P[2]) + cs);
+  if (g.active[2]) lam = lam + (fabs(P[3]) + cs);
+  return lam;
+}
+
+template <typename R>
+__device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, const EosDev& qd, const double* W,
+                                             long long N, long long c, bool& ok) {
+  const double w[5] = {W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c]};
+  return to_d<R>(wave_sum_v<R>(g, q, qd, w, ok));
+}
+
+// The same in the grid's precision, for material m: every wave-speed maximum
+// of a grid (first step, bulk, interface and flipped cells) is taken the same
+// way, so that a step from a restored state repeats the uninterrupted one.
+__device__ __forceinline__ double wave_sum(const Grid& g, int m, const double* W, long long N, long long c,
+                                           bool& ok) {
+  if (g.prec == M2C_MIXED) return wave_sum_r<float>(g, g.eosf[m], g.eos[m], W, N, c, ok);
+  return wave_sum_r<double>(g, g.eos[m], g.eos[m], W, N, c, ok);
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block max of a positive double, then one atomic max on its bit pattern
+// (positive doubles order like their bit patterns).
+__device__ __forceinline__ void block_max_to(double v, unsigned long long* dst, double* s_red) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) s_red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double x = lane < nw ? s_red[lane] : 0.0;
+    x = warp_max(x);
+    if (lane == 0 && x > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(x));
+  }
+}
+
+__device__ __forceinline__ int find_grid(const long long* __restrict__ tile_begin, int ngrid, long long tile) {
+  int lo = 0, hi = ngrid - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_begin[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace m2c

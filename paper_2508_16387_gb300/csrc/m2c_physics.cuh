@@ -162,7 +162,7 @@ __host__ __device__ __forceinline__ bool gt0(double x) {
 
 // The cases outside the normal binary32 range (subnormal results, overflow,
 // zeros, infinities, NaNs), out of line so that the common path stays short.
-__host__ __device__ __noinline__ float d2f_rare(double x) {
+inline __host__ __device__ __noinline__ float d2f_rare(double x) {
   const unsigned long long b = bits_of(x);
   const unsigned long long a = b & 0x7fffffffffffffffull;
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
@@ -200,7 +200,7 @@ __host__ __device__ __forceinline__ float d2f(double x) {
   return d2f_rare(x);
 }
 
-__host__ __device__ __noinline__ double f2d_rare(float x) {
+inline __host__ __device__ __noinline__ double f2d_rare(float x) {
   const unsigned f = bits_of(x);
   const unsigned a = f & 0x7fffffffu;
   const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
@@ -541,7 +541,7 @@ __device__ inline int wave(const EosDev& q, const Side& K, double p, double& f, 
   return q.type == M2C_EOS_SG ? wave_sg(q, K, p, f, df, rs, want_rho, drs) : wave_mg(q, K, p, f, df, rs, drs);
 }
 
-__device__ inline int riemann_F(const EosDev& qL, const Side& L, const EosDev& qR, const Side& Rs, double p,
+static __device__ __noinline__ int riemann_F(const EosDev& qL, const Side& L, const EosDev& qR, const Side& Rs, double p,
                                 double& F, double& dF) {
   double fL, dfL, rL, fR, dfR, rR;
   int st = wave(qL, L, p, fL, dfL, rL, false);
@@ -558,7 +558,7 @@ struct RiemannOut {
 
 // Solves the 1D problem between (rho, u, p) states; returns a status and the
 // Newton/bisection iteration count.
-__device__ inline int riemann_solve(const EosDev& qL, double rl, double ul, double pl, const EosDev& qR, double rr,
+static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, double ul, double pl, const EosDev& qR, double rr,
                                     double ur, double pr, RiemannOut& out, int& iters) {
   Side L, Rs;
   iters = 0;
@@ -778,7 +778,7 @@ __device__ inline bool riemann_F_f(const EosP<float>& qL, const SideF& L, const 
 
 // FP32 Newton on p* from the PVRS guess; false if it fails, signals a vacuum
 // or does not reach |dp| <= 1e-5 |p| in 30 steps.
-__device__ inline bool riemann_newton_f(const EosP<float>& qL, float rl, float ul, float pl, const EosP<float>& qR,
+static __device__ __noinline__ bool riemann_newton_f(const EosP<float>& qL, float rl, float ul, float pl, const EosP<float>& qR,
                                         float rr, float ur, float pr, float& p_out, int& iters) {
   SideF L, Rs;
   if (!make_side_f(qL, rl, ul, pl, L) || !make_side_f(qR, rr, ur, pr, Rs)) return false;
@@ -808,7 +808,7 @@ __device__ inline bool riemann_newton_f(const EosP<float>& qL, float rl, float u
   return false;
 }
 
-__device__ inline int riemann_solve_mixed(const EosP<float>& qLf, const EosDev& qL, double rl, double ul, double pl,
+static __device__ __noinline__ int riemann_solve_mixed(const EosP<float>& qLf, const EosDev& qL, double rl, double ul, double pl,
                                           const EosP<float>& qRf, const EosDev& qR, double rr, double ur, double pr,
                                           RiemannOut& out, int& iters) {
   float p32;

@@ -27,599 +27,10 @@
 #include <vector>
 
 #include "m2c_kernels.cuh"
+#include "m2c_device.cuh"
+#include "m2c_stage.h"
 
 namespace m2c {
-
-// ---------------------------------------------------------------------------
-// Conservative -> primitive
-// ---------------------------------------------------------------------------
-
-// FP64 path: u = (rho u)/rho, e = (rho E - rho|V|^2/2)/rho, p = p(rho, e).
-// Mixed path: the same with FP32 velocities and kinetic energy; rho e and, for
-// the stiffened gas, the pressure (a difference of large numbers when p_c is
-// large) in FP64, then rounded to FP32.
-template <typename R>
-__device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& qd, double rho, double m1, double m2,
-                                               double m3, double E, R P[5]) {
-  if constexpr (sizeof(R) == 8) {
-    const double inv = 1.0 / rho;
-    const double u = m1 * inv, v = m2 * inv, w = m3 * inv;
-    const double ke = 0.5 * ((m1 * u + m2 * v) + m3 * w);
-    const double e = (E - ke) * inv;
-    double p = 0.0;
-    const bool ok = eos_p<double>(q, rho, inv, e, p);
-    P[0] = rho; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
-    return ok && rho > 0.0;
-  } else {
-    const float rf = d2f(rho);
-    const float inv = rrcp<float>(rf);
-    const float f1 = d2f(m1), f2 = d2f(m2), f3 = d2f(m3);
-    const float u = f1 * inv, v = f2 * inv, w = f3 * inv;
-    const float ke = 0.5f * ((f1 * u + f2 * v) + f3 * w);
-    const double rhoe = E - f2d(ke);
-    float p = 0.0f;
-    bool ok = true;
-    if (q.type == M2C_EOS_SG) {
-      p = d2f(qd.gm1 * rhoe - qd.gpc);
-    } else {
-      ok = eos_p<float>(q, rf, inv, d2f(rhoe) * inv, p);
-    }
-    P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
-    return ok && gt0(rho);
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd, const double* __restrict__ W,
-                                             long long N, long long c, R P[5]) {
-  return cons_to_prim_v<R>(q, qd, W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c], P);
-}
-
-template <typename R>
-__device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w, R p, FaceState<R>& F) {
-  R e = (R)0, c2 = (R)0;
-  const bool ok = eos_e_c2<R>(q, rho, rrcp<R>(rho), p, e, c2);
-  F.rho = rho; F.u = u; F.v = v; F.w = w; F.p = p;
-  F.c = ok ? rsqrt_pos<R>(c2) : (R)0;
-  F.E = e + (R)0.5 * ((u * u + v * v) + w * w);
-  return ok;
-}
-
-// MUSCL face states of one cell along one axis: q -+ sigma/2 with the modified
-// van Albada slope (App. D). same = both stencil neighbours have the cell's
-// material (otherwise first order, Reading R11); a non-admissible face state
-// makes the whole axis first order (Reading R12). bad: even the cell state is
-// not admissible.
-template <typename R>
-__device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], const R P[5], const R Pp[5], bool same,
-                                           FaceState<R>& Qm, FaceState<R>& Qp, bool& bad) {
-  if (same) {
-    R s[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) s[v] = va_slope<R>(P[v] - Pm[v], Pp[v] - P[v]);
-    const R hf = (R)0.5;
-    const bool okm = make_face<R>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2], P[3] - hf * s[3],
-                                  P[4] - hf * s[4], Qm);
-    const bool okp = make_face<R>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2], P[3] + hf * s[3],
-                                  P[4] + hf * s[4], Qp);
-    if (okm && okp) return;
-  }
-  if (!make_face<R>(q, P[0], P[1], P[2], P[3], P[4], Qm)) bad = true;
-  Qp = Qm;
-}
-
-// Wave-speed sum of a state, sum over the axes with more than one cell of
-// |V_d| + c (the CFL reading of the design notes), in precision R (the mixed
-// path takes the time step from FP32 wave speeds of the FP64 state).
-template <typename R>
-__device__ __forceinline__ R wave_sum_v(const Grid& g, const EosP<R>& q, const EosDev& qd, const double w[5], bool& ok) {
-  R P[5];
-  ok = cons_to_prim_v<R>(q, qd, w[0], w[1], w[2], w[3], w[4], P);
-  R e, c2;
-  ok = ok && eos_e_c2<R>(q, P[0], rrcp<R>(P[0]), P[4], e, c2);
-  const R cs = ok ? rsqrt_pos<R>(c2) : (R)0;
-  R lam = (R)0;
-  if (g.active[0]) lam = lam + (fabs(P[1]) + cs);
-  if (g.active[1]) lam = lam + (fabs(P[2]) + cs);
-  if (g.active[2]) lam = lam + (fabs(P[3]) + cs);
-  return lam;
-}
-
-template <typename R>
-__device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, const EosDev& qd, const double* W,
-                                             long long N, long long c, bool& ok) {
-  const double w[5] = {W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c]};
-  return to_d<R>(wave_sum_v<R>(g, q, qd, w, ok));
-}
-
-// The same in the grid's precision, for material m: every wave-speed maximum
-// of a grid (first step, bulk, interface and flipped cells) is taken the same
-// way, so that a step from a restored state repeats the uninterrupted one.
-__device__ __forceinline__ double wave_sum(const Grid& g, int m, const double* W, long long N, long long c,
-                                           bool& ok) {
-  if (g.prec == M2C_MIXED) return wave_sum_r<float>(g, g.eosf[m], g.eos[m], W, N, c, ok);
-  return wave_sum_r<double>(g, g.eos[m], g.eos[m], W, N, c, ok);
-}
-
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Block max of a positive double, then one atomic max on its bit pattern
-// (positive doubles order like their bit patterns).
-__device__ __forceinline__ void block_max_to(double v, unsigned long long* dst, double* s_red) {
-  v = warp_max(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  if (lane == 0) s_red[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    double x = lane < nw ? s_red[lane] : 0.0;
-    x = warp_max(x);
-    if (lane == 0 && x > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(x));
-  }
-}
-
-__device__ __forceinline__ int find_grid(const long long* __restrict__ tile_begin, int ngrid, long long tile) {
-  int lo = 0, hi = ngrid - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (tile_begin[mid] <= tile) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// ---------------------------------------------------------------------------
-// Bulk stage kernel
-// ---------------------------------------------------------------------------
-
-template <typename R, int TY>
-struct StageSmem {
-  static constexpr int TX = 32, HX = TX + 4, HY = TY + 4;
-  static constexpr size_t q_off = 0;
-  static constexpr size_t phi_off = q_off + sizeof(R) * 5 * HY * HX;
-  static constexpr size_t xs_off = phi_off + sizeof(R) * HY * HX;
-  static constexpr size_t ys_off = xs_off + sizeof(FaceState<R>) * TY * (TX + 2) * 2;
-  static constexpr size_t fx_off = ys_off + sizeof(FaceState<R>) * (TY + 2) * TX * 2;
-  static constexpr size_t fy_off = fx_off + sizeof(R) * 5 * TY * (TX + 1);
-  static constexpr size_t id_off = fy_off + sizeof(R) * 5 * (TY + 1) * TX;
-  static constexpr size_t eos_off = (id_off + HY * HX + 15) / 16 * 16;
-  static constexpr size_t eosd_off = eos_off + (sizeof(EosP<R>) * 2 + 15) / 16 * 16;
-  static constexpr size_t bytes = eosd_off + sizeof(EosDev) * 2;
-};
-
-// FP64 tiles run one block per SM (FP64-pipe bound); the FP32 tiles of the
-// mixed path are latency bound and are compiled for 1024 resident threads per
-// SM (64 registers a thread): four 256-thread blocks of 8-row tiles (55 KB of
-// shared memory each) or two 512-thread blocks of 16-row tiles.
-//
-// Every thread's share of the plane work (halo cell, face-state items, flux
-// items) and its shared-memory addresses are fixed for the whole launch and
-// computed once; only the plane index changes along the march.
-template <typename R, int TY>
-__global__ void __launch_bounds__(32 * TY, (sizeof(R) == 8 ? 1 : 1024 / (32 * TY)))
-k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, long long ntiles, int mode,
-        int sched, unsigned long long* __restrict__ tile_counter) {
-  constexpr int TX = 32, NT = TX * TY, HX = TX + 4, HY = TY + 4, PL = HY * HX;
-  constexpr int NXS = (TX + 2) * TY, NYS = TX * (TY + 2), NS = NXS + NYS;  // face-state items
-  constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1), NF = NXF + NYF;  // flux items
-  constexpr int NHALO = 4 * (TX + TY);
-  constexpr int SI = (NS + NT - 1) / NT, FI = (NF + NT - 1) / NT;
-  constexpr int SFX = TY * (TX + 1), SFY = (TY + 1) * TX;                   // flux array strides
-  using SM = StageSmem<R, TY>;
-  extern __shared__ __align__(16) unsigned char smem[];
-  R* s_q = reinterpret_cast<R*>(smem + SM::q_off);                         // [5][HY][HX]
-  R* s_phi = reinterpret_cast<R*>(smem + SM::phi_off);                     // [HY][HX]
-  FaceState<R>* s_st = reinterpret_cast<FaceState<R>*>(smem + SM::xs_off);  // x: [TY][TX+2][2], then y: [TY+2][TX][2]
-  R* s_fx = reinterpret_cast<R*>(smem + SM::fx_off);                       // [5][TY][TX+1]
-  R* s_fy = reinterpret_cast<R*>(smem + SM::fy_off);                       // [5][TY+1][TX]
-  uint8_t* s_id = smem + SM::id_off;                                       // [HY][HX]
-  EosP<R>* s_eos = reinterpret_cast<EosP<R>*>(smem + SM::eos_off);
-  EosDev* s_eosd = reinterpret_cast<EosDev*>(smem + SM::eosd_off);
-  __shared__ double s_dt;
-  __shared__ double s_red[32];
-  __shared__ long long s_tile;
-
-  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-  const unsigned lane = tid & 31, lt = (1u << lane) - 1u;
-
-  // The thread's share of the plane work is recomputed from the thread index
-  // where it is used (a volatile read of %tid.x keeps the compiler from
-  // holding the items in registers across the plane loop).
-  auto tid_now = []() {
-    unsigned t;
-    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
-    return (int)t;
-  };
-  // face-state item s, packed: centre in the plane buffer (bits 0-9), stencil along y (bit 10); -1: none
-  auto st_item = [&](int s) {
-    const int i = tid_now() + s * NT;
-    if (i < NXS) return (i / (TX + 2) + 2) * HX + i % (TX + 2) + 1;
-    if (i < NS) {
-      const int j = i - NXS;
-      return ((j / TX + 1) * HX + j % TX + 2) | (1 << 10);
-    }
-    return -1;
-  };
-  // flux item s, packed in two words: left face state (bits 0-15) and direction y (bit 30),
-  // -1: none; id position of the left cell (bits 0-15) and output offset (bits 16-31)
-  auto flux_item = [&](int s, int& b) {
-    const int i = tid_now() + s * NT;
-    if (i < NXF) {
-      const int f = i % (TX + 1), row = i / (TX + 1);
-      b = ((row + 2) * HX + f + 1) | ((row * (TX + 1) + f) << 16);
-      return 2 * (row * (TX + 2) + f) + 1;
-    }
-    if (i < NF) {
-      const int j = i - NXF;
-      const int x = j % TX, f = j / TX;
-      b = ((f + 1) * HX + x + 2) | ((f * TX + x) << 16);
-      return (2 * NXS + 2 * (f * TX + x) + 1) | (1 << 30);
-    }
-    b = 0;
-    return -1;
-  };
-  static_assert(2 * NS < 65536 && PL < 1024 && SFX < 32768 && SFY < 32768, "packed item fields");
-  // halo cells of the plane buffer loaded by this thread (two-cell ring without corners):
-  // smem slot, or -1
-  constexpr int HI = (NHALO + NT - 1) / NT;
-  int h_hx[HI], h_hy[HI];
-#pragma unroll
-  for (int s = 0; s < HI; ++s) {
-    const int h = tid + s * NT;
-    h_hx[s] = -1;
-    h_hy[s] = 0;
-    if (h < 4 * TY) {
-      const int c4 = h / TY;
-      h_hx[s] = c4 < 2 ? c4 : TX + c4;
-      h_hy[s] = h % TY + 2;
-    } else if (h < NHALO) {
-      const int h2 = h - 4 * TY;
-      const int c4 = h2 / TX;
-      h_hy[s] = c4 < 2 ? c4 : TY + c4;
-      h_hx[s] = h2 % TX + 2;
-    }
-  }
-
-  // Tiles of all grids of the launch, taken in order by a fixed stride
-  // (sched 0) or from an atomic counter (sched 1).
-  for (long long iter = 0;; ++iter) {
-  long long tile;
-  if (sched == 1) {
-    if (tid == 0) s_tile = (long long)atomicAdd(tile_counter, 1ull);
-    __syncthreads();
-    tile = s_tile;
-  } else {
-    tile = blockIdx.x + iter * (long long)gridDim.x;
-  }
-  if (tile >= ntiles) break;
-  const int gidx = find_grid(tile_begin, ngrid, tile);
-  const Grid& G = grids[gidx];
-  const int nx = G.nx, ny = G.ny, nz = G.nz;
-  const long long N = G.N, nxy = (long long)nx * ny;
-  const int bcz0 = G.bc[4], bcz1 = G.bc[5];
-  long long t = tile - tile_begin[gidx];
-  const int bx = (int)(t % G.tiles_x);
-  t /= G.tiles_x;
-  const int by = (int)(t % G.tiles_y);
-  const int bz = (int)(t / G.tiles_y);
-  const int x0 = bx * TX, y0 = by * TY, k0 = bz * G.tz, k1 = min(k0 + G.tz, nz);
-  const R ih = (R)G.inv_h;
-  const R i6h = (R)(1.0 / (6.0 * G.h));
-  const double* __restrict__ Ws = mode == kStage2 ? G.W1 : G.W;
-  const double* __restrict__ phis = mode == kStage2 ? G.phi1 : G.phi;
-  const uint8_t* __restrict__ idg = G.id;
-  Ctrl* ctrl = G.ctrl;
-  const int slot = mode == kStage2 ? 1 : 0;
-  const long long step = ctrl->step;
-
-  if (tid < 2) {
-    if constexpr (sizeof(R) == 8) s_eos[tid] = G.eos[tid];
-    else s_eos[tid] = G.eosf[tid];
-    s_eosd[tid] = G.eos[tid];
-  }
-  if (tid == 0) s_dt = mode == kResidual ? 0.0 : lam_to_dt(G, ctrl->lam[step & 1]);
-  __syncthreads();
-  const double dt = s_dt;
-
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool inside = gx < nx && gy < ny;
-  // column bases (x, y mapped once per tile)
-  const long long own_base = (long long)map_index(gy, ny, G.bc[2], G.bc[3]) * nx + map_index(gx, nx, G.bc[0], G.bc[1]);
-  long long halo_base[HI];
-#pragma unroll
-  for (int s = 0; s < HI; ++s)
-    halo_base[s] = h_hx[s] < 0 ? 0
-                               : (long long)map_index(y0 + h_hy[s] - 2, ny, G.bc[2], G.bc[3]) * nx +
-                                     map_index(x0 + h_hx[s] - 2, nx, G.bc[0], G.bc[1]);
-
-  // failures seen by this thread in this tile: non-physical state, work-list overflow
-  bool bad = false, ovf = false;
-  // material at the start of the step and the stage state of cell index c
-  auto load = [&](long long c, R P[5], R& ph, int& idv) {
-    const double phd = phis[c];
-    if (mode == kStage2) {
-      idv = idg[c] & 1;
-    } else {
-      idv = lt0(phd) ? 1 : 0;
-    }
-    ph = to_r<R>(phd);
-    if (!cons_to_prim<R>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) bad = true;
-  };
-  auto plane = [&](int k) { return (long long)map_index(k, nz, bcz0, bcz1) * nxy; };
-
-  // ---- warm-up of the z window: planes k0-2 .. k0+1
-  R Pa[5], P0[5], P1[5], P2[5];
-  R ph[5];
-  int ida, idm, id0, id1, id2;
-  FaceState<R> QzP, Qtmp, QzM1, QzP1;
-  R Fzm[5], Fzp[5];
-  {
-    R Pb[5];
-    int idb;
-    load(plane(k0 - 2) + own_base, Pb, ph[0], idb);
-    load(plane(k0 - 1) + own_base, Pa, ph[1], ida);
-    load(plane(k0) + own_base, P0, ph[2], id0);
-    load(plane(k0 + 1) + own_base, P1, ph[3], id1);
-    FaceState<R> QaP, Q0M;
-    cell_faces<R>(s_eos[ida], Pb, Pa, P0, idb == ida && id0 == ida, Qtmp, QaP, bad);
-    cell_faces<R>(s_eos[id0], Pa, P0, P1, ida == id0 && id1 == id0, Q0M, QzP, bad);
-    if (ida == id0) {
-      hllc<2, R>(QaP, Q0M, Fzm);
-    } else {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Fzm[v] = (R)0;
-    }
-    idm = ida;
-  }
-
-  R lam_max = (R)0;
-  const int cslot = (ty + 2) * HX + tx + 2;
-
-  for (int k = k0; k < k1; ++k) {
-    const long long pk = (long long)k * nxy;  // k is inside the grid
-    // ---- own column: plane k+2, z face states of cell k+1, z flux of face k+1/2
-    load(plane(k + 2) + own_base, P2, ph[4], id2);
-    cell_faces<R>(s_eos[id1], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad);
-    if (id0 == id1) {
-      hllc<2, R>(QzP, QzM1, Fzp);
-    } else {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Fzp[v] = (R)0;
-    }
-    // ---- plane k into shared memory: own cells and the two-cell halo (no corners)
-#pragma unroll
-    for (int v = 0; v < 5; ++v) s_q[v * PL + cslot] = P0[v];
-    s_phi[cslot] = ph[2];
-    s_id[cslot] = (uint8_t)id0;
-#pragma unroll
-    for (int s = 0; s < HI; ++s) {
-      if (h_hx[s] < 0) break;
-      const int hslot = h_hy[s] * HX + h_hx[s];
-      R Ph[5], phh;
-      int idh;
-      load(pk + halo_base[s], Ph, phh, idh);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) s_q[v * PL + hslot] = Ph[v];
-      s_phi[hslot] = phh;
-      s_id[hslot] = (uint8_t)idh;
-    }
-    __syncthreads();
-
-    // ---- MUSCL face states along x (cells x = -1 .. TX) and y (cells y = -1 .. TY)
-#pragma unroll
-    for (int s = 0; s < SI; ++s) {
-      const int it = st_item(s);
-      if (it < 0) break;
-      const int c0 = it & 1023, so = (it >> 10) ? HX : 1;
-      R Pm[5], P[5], Pp[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Pm[v] = s_q[v * PL + c0 - so];
-        P[v] = s_q[v * PL + c0];
-        Pp[v] = s_q[v * PL + c0 + so];
-      }
-      const int ic = s_id[c0];
-      const bool same = s_id[c0 - so] == ic && s_id[c0 + so] == ic;
-      bool b = false;
-      FaceState<R>* out = s_st + 2 * (tid + s * NT);
-      cell_faces<R>(s_eos[ic], Pm, P, Pp, same, out[0], out[1], b);
-      bad = bad || b;
-    }
-    __syncthreads();
-
-    // ---- HLLC on every x face (between cells f-1 and f of a row) and y face of the tile
-#pragma unroll
-    for (int s = 0; s < FI; ++s) {
-      int itb;
-      const int it = flux_item(s, itb);
-      if (it < 0) break;
-      const int dir = (it >> 30) & 1;
-      const int lsi = it & 0xffff, idp = itb & 0xffff, outo = (itb >> 16) & 0x7fff;
-      const int il = s_id[idp], ir = s_id[idp + (dir ? HX : 1)];
-      const FaceState<R>& QL = s_st[lsi];
-      const FaceState<R>& QR = s_st[lsi + (dir ? 2 * TX - 1 : 1)];
-      R F[5];
-      if (il != ir) {
-#pragma unroll
-        for (int v = 0; v < 5; ++v) F[v] = (R)0;
-      } else if (dir == 0) {
-        hllc<0, R>(QL, QR, F);
-      } else {
-        hllc<1, R>(QL, QR, F);
-      }
-      R* o = (dir ? s_fy : s_fx) + outo;
-      const int stride = dir ? SFY : SFX;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) o[v * stride] = F[v];
-    }
-    __syncthreads();
-
-    // ---- per cell: residual, level set, Runge-Kutta update, work lists
-    {
-      const int idxm = s_id[cslot - 1], idxp = s_id[cslot + 1];
-      const int idym = s_id[cslot - HX], idyp = s_id[cslot + HX];
-      const bool is_if = inside && (idxm != id0 || idxp != id0 || idym != id0 || idyp != id0 || idm != id0 ||
-                                    id1 != id0);
-      R res[5];
-      R Fxm[5], Fxp[5], Fym[5], Fyp[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        Fxm[v] = s_fx[v * SFX + ty * (TX + 1) + tx];
-        Fxp[v] = s_fx[v * SFX + ty * (TX + 1) + tx + 1];
-        Fym[v] = s_fy[v * SFY + ty * TX + tx];
-        Fyp[v] = s_fy[v * SFY + (ty + 1) * TX + tx];
-        res[v] = ((Fxm[v] - Fxp[v]) * ih + (Fym[v] - Fyp[v]) * ih) + (Fzm[v] - Fzp[v]) * ih;
-      }
-      // level-set residual -((u phi_x + v phi_y) + w phi_z), third-order upwind-biased (Sec. 4.4)
-      const R u = P0[1], vv = P0[2], w = P0[3];
-      const R* prow = s_phi + cslot;
-      R Dx, Dy, Dz;
-      if (u >= (R)0) Dx = (((R)2 * prow[1] + (R)3 * prow[0]) - (R)6 * prow[-1] + prow[-2]) * i6h;
-      else Dx = ((-prow[2] + (R)6 * prow[1]) - (R)3 * prow[0] - (R)2 * prow[-1]) * i6h;
-      if (vv >= (R)0) Dy = (((R)2 * prow[HX] + (R)3 * prow[0]) - (R)6 * prow[-HX] + prow[-2 * HX]) * i6h;
-      else Dy = ((-prow[2 * HX] + (R)6 * prow[HX]) - (R)3 * prow[0] - (R)2 * prow[-HX]) * i6h;
-      if (w >= (R)0) Dz = (((R)2 * ph[3] + (R)3 * ph[2]) - (R)6 * ph[1] + ph[0]) * i6h;
-      else Dz = ((-ph[4] + (R)6 * ph[3]) - (R)3 * ph[2] - (R)2 * ph[1]) * i6h;
-      const R Lphi = -((u * Dx + vv * Dy) + w * Dz);
-
-      const long long c = pk + own_base;
-      bool flip = false;
-      if (inside) {
-        if (mode == kResidual) {
-          if (!is_if) {
-#pragma unroll
-            for (int v = 0; v < 5; ++v) G.resR[v * N + c] = to_d<R>(res[v]);
-          }
-          G.resL[c] = to_d<R>(Lphi);
-          G.id[c] = (uint8_t)id0;
-        } else if (mode == kStage1) {
-          G.phi1[c] = G.phi[c] + dt * to_d<R>(Lphi);
-          G.id[c] = (uint8_t)id0;
-          if (!is_if) {
-#pragma unroll
-            for (int v = 0; v < 5; ++v) G.W1[v * N + c] = G.W[v * N + c] + dt * to_d<R>(res[v]);
-          }
-        } else {
-          const double pn = 0.5 * (G.phi[c] + (G.phi1[c] + dt * to_d<R>(Lphi)));
-          G.phi[c] = pn;
-          const bool neg = lt0(pn);
-          flip = neg != (id0 == 1);
-          // bit 2: material at the end of the step (read by the phase update)
-          G.id[c] = (uint8_t)(id0 | (neg ? 4 : 0));
-          if (!is_if) {
-            double wn[5];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) {
-              wn[v] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * to_d<R>(res[v])));
-              G.W[v * N + c] = wn[v];
-            }
-            if (!flip) {
-              bool ok;
-              const R lam = wave_sum_v<R>(G, s_eos[id0], s_eosd[id0], wn, ok);
-              bad = bad || !ok;
-              lam_max = fmax(lam_max, lam);
-            }
-          }
-        }
-      }
-      // ---- work lists: warp ballot, one atomic per warp (skipped when the warp has none)
-      const bool fxf = inside && idxp != id0, fyf = inside && idyp != id0, fzf = inside && id1 != id0;
-      const int nf = (int)fxf + (int)fyf + (int)fzf;
-      if (__any_sync(0xffffffffu, is_if || nf || flip)) {
-        {
-          const unsigned m = __ballot_sync(0xffffffffu, is_if);
-          if (m) {
-            int base = 0;
-            const int leader = __ffs(m) - 1;
-            if ((int)lane == leader) base = atomicAdd(&ctrl->ncell[slot], __popc(m));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (is_if) {
-              const int s = base + __popc(m & lt);
-              if (s < G.cell_cap) {
-                IfCell* e = G.cells + s;
-                e->cell = c;
-#pragma unroll
-                for (int v = 0; v < 5; ++v) {
-                  e->F[0][v] = to_d<R>(Fxm[v]);
-                  e->F[1][v] = to_d<R>(Fxp[v]);
-                  e->F[2][v] = to_d<R>(Fym[v]);
-                  e->F[3][v] = to_d<R>(Fyp[v]);
-                  e->F[4][v] = to_d<R>(Fzm[v]);
-                  e->F[5][v] = to_d<R>(Fzp[v]);
-                }
-                G.cell_slot[c] = s;
-              } else {
-                ovf = true;
-              }
-            }
-          }
-        }
-        {
-          int incl = nf;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += y;
-          }
-          const int total = __shfl_sync(0xffffffffu, incl, 31);
-          if (total) {
-            int base = 0;
-            if (lane == 31) base = atomicAdd(&ctrl->nface[slot], total);
-            base = __shfl_sync(0xffffffffu, base, 31);
-            int s = base + incl - nf;
-            const bool fl[3] = {fxf, fyf, fzf};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              if (fl[d]) {
-                if (s < G.face_cap) {
-                  G.faces[s].cell = c;
-                  G.faces[s].dir = d;
-                } else {
-                  ovf = true;
-                }
-                ++s;
-              }
-            }
-          }
-        }
-        if (mode == kStage2) {
-          const unsigned m = __ballot_sync(0xffffffffu, flip);
-          if (m) {
-            int base = 0;
-            const int leader = __ffs(m) - 1;
-            if ((int)lane == leader) base = atomicAdd(&ctrl->nflip, __popc(m));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (flip) {
-              const int s = base + __popc(m & lt);
-              if (s < G.flip_cap) G.flips[s] = c;
-              else ovf = true;
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- shift the z window
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      P0[v] = P1[v];
-      P1[v] = P2[v];
-      Fzm[v] = Fzp[v];
-    }
-    ph[0] = ph[1]; ph[1] = ph[2]; ph[2] = ph[3]; ph[3] = ph[4];
-    idm = id0; id0 = id1; id1 = id2;
-    QzP = QzP1;
-  }
-  // failures are latched once per tile, with the thread's column at the tile's first plane
-  if (bad) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, gx, gy, k0));
-  if (ovf) latch_error(ctrl, M2C_EOVERFLOW, cell_of(G, gx, gy, k0));
-  if (mode == kStage2) block_max_to(to_d<R>(lam_max), &ctrl->lam[(step + 1) & 1], s_red);
-  __syncthreads();  // the next tile reuses the shared memory
-  }
-}
 
 // ---------------------------------------------------------------------------
 // FIVER on the packed interface faces (Sec. 4.2): exact two-material Riemann
@@ -1093,57 +504,20 @@ m2c_status cuda_check(m2c_ctx* c, cudaError_t e, const char* what) {
   return set_err(c, M2C_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-template <typename R, int TY>
-void stage_smem_setup() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_stage<R, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<R, TY>::bytes);
-  done = true;
-}
-
-struct LaunchPlan {
-  int ty = 8;            // tile rows (4 or 8)
-  int sched = 0;         // 0: fixed stride over tiles, 1: atomic tile counter
-  int blocks_per_sm = 0; // persistent grid of blocks_per_sm x SMs blocks; 0: one block per tile
-  unsigned long long* counter = nullptr;
-};
-
-int sm_count();
-
-template <typename R, int TY>
-cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
-                           const LaunchPlan& lp, cudaStream_t s) {
-  stage_smem_setup<R, TY>();
-  long long nb = ntiles;
-  if (lp.blocks_per_sm > 0) nb = std::min<long long>(ntiles, (long long)lp.blocks_per_sm * sm_count());
-  if (nb < 1) nb = 1;
-  if (lp.sched == 1) {
-    cudaError_t e = cudaMemsetAsync(lp.counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
-  }
-  k_stage<R, TY><<<(unsigned)nb, 32 * TY, StageSmem<R, TY>::bytes, s>>>(grids, tiles, ngrid, ntiles, mode,
-                                                                         lp.sched, lp.counter);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_stage(int prec, const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
                          const LaunchPlan& lp, cudaStream_t s) {
-  if (prec == M2C_FP64) {  // FP64 tiles have at most 8 rows (registers)
-    if (lp.ty == 4) return launch_stage_t<double, 4>(grids, tiles, ngrid, ntiles, mode, lp, s);
-    return launch_stage_t<double, 8>(grids, tiles, ngrid, ntiles, mode, lp, s);
-  }
-  if (lp.ty == 4) return launch_stage_t<float, 4>(grids, tiles, ngrid, ntiles, mode, lp, s);
-  if (lp.ty == 16) return launch_stage_t<float, 16>(grids, tiles, ngrid, ntiles, mode, lp, s);
-  return launch_stage_t<float, 8>(grids, tiles, ngrid, ntiles, mode, lp, s);
+  if (prec == M2C_FP64) return launch_stage_fp64(grids, tiles, ngrid, ntiles, mode, lp, s);
+  return launch_stage_fp32(grids, tiles, ngrid, ntiles, mode, lp, s);
 }
 
 void setup_all_stage_kernels() {
-  stage_smem_setup<double, 4>();
-  stage_smem_setup<double, 8>();
-  stage_smem_setup<float, 4>();
-  stage_smem_setup<float, 8>();
-  stage_smem_setup<float, 16>();
+  setup_stage_fp64();
+  setup_stage_fp32();
 }
+
+}  // namespace
+
+namespace m2c {
 
 int sm_count() {
   static int n = 0;
@@ -1155,6 +529,10 @@ int sm_count() {
   }
   return n;
 }
+
+}  // namespace m2c
+
+namespace {
 
 void set_tiling(Grid& g, int ty, int tz) {
   g.tiles_x = (g.nx + 31) / 32;
