@@ -221,7 +221,8 @@ def peaks():
 def _kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("m2c_solver.cu", "m2c_physics.cuh", "m2c_kernels.cuh"):
+    for f in ("m2c_stage.cuh", "m2c_stage_fp32.cu", "m2c_stage_fp64.cu", "m2c_device.cuh", "m2c_physics.cuh",
+              "m2c_kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2508_16387_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
