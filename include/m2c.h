@@ -117,7 +117,8 @@ m2c_status m2c_set_riemann_start(m2c_ctx* ctx, int fp32_start);
 
 /* Tile of the bulk stage kernel: 32 x tile_rows (4 or 8; 16 for M2C_MIXED)
  * columns marching tile_z cells along z (0: automatic). Results do not depend
- * on the tiling. */
+ * on the tiling. Default: 16 rows for M2C_MIXED grids large enough to give
+ * every SM 8 tiles of 16 rows and 16 planes, else 8. */
 m2c_status m2c_set_tiling(m2c_ctx* ctx, int tile_rows, int tile_z);
 
 /* Borrows the device arrays W (5N doubles) and phi (N doubles) as the state,
