@@ -541,14 +541,22 @@ __device__ inline int wave(const EosDev& q, const Side& K, double p, double& f, 
   return q.type == M2C_EOS_SG ? wave_sg(q, K, p, f, df, rs, want_rho, drs) : wave_mg(q, K, p, f, df, rs, drs);
 }
 
+// Both wave curves at p: f and f' of each side, and on request (wv) the star
+// densities behind the two waves and their slopes d rho*/dp as well.
+struct WaveVals {
+  double fL, dfL, rL, dL, fR, dfR, rR, dR;
+};
+
 static __device__ __noinline__ int riemann_F(const EosDev& qL, const Side& L, const EosDev& qR, const Side& Rs, double p,
-                                double& F, double& dF) {
-  double fL, dfL, rL, fR, dfR, rR;
-  int st = wave(qL, L, p, fL, dfL, rL, false);
-  if (!st) st = wave(qR, Rs, p, fR, dfR, rR, false);
+                                double& F, double& dF, WaveVals* wv = nullptr) {
+  double fL, dfL, rL, fR, dfR, rR, dL = 0.0, dR = 0.0;
+  const bool want = wv != nullptr;
+  int st = wave(qL, L, p, fL, dfL, rL, want, want ? &dL : nullptr);
+  if (!st) st = wave(qR, Rs, p, fR, dfR, rR, want, want ? &dR : nullptr);
   if (st) return st;
   F = fL + fR + (Rs.u - L.u);
   dF = dfL + dfR;
+  if (wv) *wv = WaveVals{fL, dfL, rL, dL, fR, dfR, rR, dR};
   return M2C_OK;
 }
 
@@ -579,12 +587,18 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
   }
   int it;
   bool conv = false, extra = false;
+  // the extra (last) Newton step also returns the star densities, so that the
+  // solution follows from it to first order in that step's (rounding-level)
+  // change of p instead of from one more evaluation
+  WaveVals wv{};
+  double p_last = 0.0;
   for (it = 1; it <= kNewtonCap; ++it) {
-    st = riemann_F(qL, L, qR, Rs, p, F, dF);
+    st = riemann_F(qL, L, qR, Rs, p, F, dF, extra ? &wv : nullptr);
     if (st) return st;
     double pn = p - F / dF;
     if (!(pn > plow)) pn = 0.5 * (p + plow);
     bool small = fabs(pn - p) <= kNewtonTol * fabs(pn);
+    p_last = p;
     p = pn;
     if (extra) { conv = true; break; }
     if (small) extra = true;
@@ -617,6 +631,15 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
     }
     if (!ok) return M2C_ENOCONV;
     p = 0.5 * (a + b);
+  }
+  if (conv && isfinite(wv.dfL) && isfinite(wv.dfR) && isfinite(wv.dL) && isfinite(wv.dR)) {
+    const double d = p - p_last;
+    out.p = p;
+    out.u = 0.5 * (L.u + Rs.u) + 0.5 * (wv.fR - wv.fL) + 0.5 * (wv.dfR - wv.dfL) * d;
+    out.rhoL = wv.rL + wv.dL * d;
+    out.rhoR = wv.rR + wv.dR * d;
+    iters = it;
+    return M2C_OK;
   }
   double fL, dfL, rL, fR, dfR, rR;
   st = wave(qL, L, p, fL, dfL, rL);
