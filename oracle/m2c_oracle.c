@@ -350,7 +350,9 @@ static int riemann_F(const or_eos_t* qL, const side_t* L, const or_eos_t* qR, co
  * admissible pressure; stop when |dp| <= 1e-12 |p|, then one more step; after
  * 50 steps, bisection). u* = (u_L + u_R)/2 + (f_R - f_L)/2; rho*_K from the
  * K-wave. Reading R7: no vacuum solution is built; if F(p_low) >= 0 the call
- * fails with OR_EVACUUM. out = {p*, u*, rho*_L, rho*_R}. */
+ * fails with OR_EVACUUM. Both wave curves increase with p and vanish at their
+ * side's pressure (>= p_low), so F(p_low) <= u_R - u_L: the test is only made
+ * when u_R - u_L >= 0. out = {p*, u*, rho*_L, rho*_R}. */
 static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, const double wR[3], double out[4], int* iters) {
   side_t L, R;
   int st = make_side(qL, wL, &L);
@@ -358,7 +360,7 @@ static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, c
   if (st) return st;
   double plow = fmax(eos_plow(qL), eos_plow(qR));
   double F, dF;
-  if (isfinite(plow)) {
+  if (isfinite(plow) && R.u - L.u >= 0.0) {
     st = riemann_F(qL, &L, qR, &R, plow, &F, &dF);
     if (st) return st;
     if (F >= 0.0) return OR_EVACUUM;

@@ -574,7 +574,10 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
   const double plow = fmax(eos_plow(qL), eos_plow(qR));
   double F, dF;
   int st;
-  if (isfinite(plow)) {
+  // vacuum test (F(p_low) >= 0); both wave curves increase with p and vanish at
+  // their side's pressure, so F(p_low) <= u_R - u_L and the test is only made
+  // when u_R - u_L >= 0
+  if (isfinite(plow) && Rs.u - L.u >= 0.0) {
     st = riemann_F(qL, L, qR, Rs, plow, F, dF);
     if (st) return st;
     if (F >= 0.0) return M2C_EVACUUM;
