@@ -116,9 +116,12 @@ m2c_status m2c_set_scheme(m2c_ctx* ctx, double cfl, int reinit_every, int reinit
 m2c_status m2c_set_riemann_start(m2c_ctx* ctx, int fp32_start);
 
 /* Tile of the bulk stage kernel: 32 x tile_rows (4 or 8; 16 for M2C_MIXED)
- * columns marching tile_z cells along z (0: automatic). Results do not depend
- * on the tiling. Default: 16 rows for M2C_MIXED grids large enough to give
- * every SM 8 tiles of 16 rows and 16 planes, else 8. */
+ * columns marching tile_z cells along z (0: automatic). M2C_FP64 results do
+ * not depend on the tiling (bitwise); M2C_MIXED results agree to FP32 rounding
+ * (FP32 multiply-adds may be contracted differently in the code that opens a
+ * z-chunk and in the kernels of other tile heights). Default: 16 rows for
+ * M2C_MIXED grids large enough to give every SM 8 tiles of 16 rows and 16
+ * planes, else 8. */
 m2c_status m2c_set_tiling(m2c_ctx* ctx, int tile_rows, int tile_z);
 
 /* Borrows the device arrays W (5N doubles) and phi (N doubles) as the state,

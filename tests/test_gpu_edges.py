@@ -77,3 +77,32 @@ def test_grid_without_a_moving_axis_is_rejected(m2c):
     g = O.Grid(n=(1, 1, 1), h=0.1, eos=(O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)))
     with pytest.raises(O.OracleError):
         O.time_step(g, np.ones((5, 1, 1, 1)), np.ones((1, 1, 1)))
+
+
+@pytest.mark.parametrize("prec,tilings", [
+    (0, [(8, 0), (4, 0), (8, 16), (4, 7)]),
+    (1, [(8, 0), (16, 0), (4, 8), (16, 32), (8, 5)]),
+])
+def test_results_do_not_depend_on_the_tiling(m2c, prec, tilings):
+    """Every face is computed once, by one formula, whatever the tile that owns it. FP64: the
+    state after several steps (reinitialisation included) is bitwise the same for every tile
+    shape and z-chunk length, ragged chunks included. Mixed: the compiler may contract FP32
+    multiply-adds differently in the code that opens a z-chunk and in the kernel
+    instantiated for another tile height, so results agree to FP32 rounding (here within
+    1e-5 of each component's scale) rather than bitwise."""
+    s = WL.shock_bubble(n=48, radius=0.2, x_shock=0.3, steps=12, water=WL.WATER_MG if prec else WL.WATER_SG)
+    ref = None
+    for rows, tz in tilings:
+        g = gpu_start(m2c, s, prec)
+        g.set_tiling(rows, tz)
+        g.step(12)
+        g.sync()
+        out = (g.W.cpu().numpy(), g.phi.cpu().numpy())
+        if ref is None:
+            ref = out
+        elif prec == 0:
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), (rows, tz)
+        else:
+            assert max(rel_err(out[0], ref[0])) < 1e-5, (rows, tz)
+            assert np.abs(out[1] - ref[1]).max() < 1e-6 * s.h * s.n[0], (rows, tz)
+    assert (ref[1] < 0).any()
