@@ -238,8 +238,10 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
                                 const m2c_eos_desc* eos1, int precision, const double* W, const double* phi,
                                 double* R, double* L, void* stream);
 
-/* Kernel timing: while enabled, m2c_step records a CUDA event pair on the
- * context's stream around every kernel launch. m2c_profile_read synchronises
+/* Kernel timing: while enabled (enable = 1), m2c_step records a CUDA event
+ * pair on the context's stream around every kernel launch; enable = 2 records
+ * them around the bulk stage kernel only (least overhead on the step);
+ * 0 stops. m2c_profile_read synchronises
  * the stream, returns the summed event time (ms) and the number of launches of
  * the bulk stage kernel, and starts a new count; m2c_profile_read_kernels does
  * the same for every kernel kind: [0] bulk stage, [1] FIVER, [2] interface-cell

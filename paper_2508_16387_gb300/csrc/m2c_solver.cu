@@ -456,7 +456,7 @@ struct m2c_ctx {
   int reinit_every, reinit_iters;
   long long host_step;
   bool has_state, eos_set[2], dirty, lam_valid;
-  bool profiling;
+  bool profiling, profile_bulk_only;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pairs around launches while profiling
   std::vector<int> ev_kind;
   size_t ev_used;
@@ -580,10 +580,23 @@ struct StageEvents {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>>* ev;
   std::vector<int>* kind;
   size_t* used;
+  bool bulk_only = false;  // time the bulk stage kernel only
+  bool skip = false;       // the open pair was not recorded
 };
 
 cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s, int kind = kKStage) {
   if (!pe) return cudaSuccess;
+  if (pe->bulk_only) {
+    // only the bulk stage kernel is timed: the end record follows its start record
+    if (start && kind != kKStage) {
+      pe->skip = true;
+      return cudaSuccess;
+    }
+    if (!start && pe->skip) {
+      pe->skip = false;
+      return cudaSuccess;
+    }
+  }
   if (start) {
     if (*pe->used == pe->ev->size()) {
       cudaEvent_t a, b;
@@ -750,6 +763,7 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   c->eos_set[0] = c->eos_set[1] = false;
   c->lam_valid = false;
   c->profiling = false;
+  c->profile_bulk_only = false;
   c->ev_used = 0;
   cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(Ctrl), c->stream);
   if (e != cudaSuccess) {
@@ -886,7 +900,7 @@ m2c_status m2c_step(m2c_ctx* c, int nsteps) {
   }
   for (int n = 0; n < nsteps; ++n) {
     const bool re = c->reinit_every > 0 && (c->host_step + 1) % c->reinit_every == 0;
-    StageEvents pe{&c->ev, &c->ev_kind, &c->ev_used};
+    StageEvents pe{&c->ev, &c->ev_kind, &c->ev_used, c->profile_bulk_only, false};
     LaunchPlan lp;
     lp.ty = c->ty;
     cudaError_t e = enqueue_step(c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), c->host.prec, lp, re,
@@ -1302,8 +1316,9 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
 }
 
 m2c_status m2c_profile(m2c_ctx* c, int enable) {
-  if (!c) return M2C_EINVAL;
+  if (!c || enable < 0 || enable > 2) return M2C_EINVAL;
   c->profiling = enable != 0;
+  c->profile_bulk_only = enable == 2;
   c->ev_used = 0;
   return M2C_OK;
 }

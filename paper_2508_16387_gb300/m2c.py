@@ -305,8 +305,9 @@ class Grid:
         _check(lib().m2c_get_stats(self.ctx, ctypes.byref(st)), "m2c_get_stats", self.ctx)
         return StepStats(st.interface_faces, st.interface_cells, st.flipped_cells, st.dt)
 
-    def profile(self, enable=True):
-        _check(lib().m2c_profile(self.ctx, 1 if enable else 0), "m2c_profile", self.ctx)
+    def profile(self, enable=True, bulk_only=False):
+        mode = (2 if bulk_only else 1) if enable else 0
+        _check(lib().m2c_profile(self.ctx, mode), "m2c_profile", self.ctx)
 
     def profile_read(self):
         ms = ctypes.c_double()
