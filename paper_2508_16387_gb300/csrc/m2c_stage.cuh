@@ -14,17 +14,23 @@ namespace m2c {
 // Bulk stage kernel
 // ---------------------------------------------------------------------------
 
+// The level set and material planes are double-buffered where shared memory
+// allows (16-row FP32 tiles at two blocks per SM, FP64 tiles at one): a plane's
+// update reads them while the next plane's loads already write the other
+// buffer, which saves one block barrier per plane. The 8-row FP32 tiles (four
+// blocks per SM) keep one buffer and the barrier.
 template <typename R, int TY>
 struct StageSmem {
   static constexpr int TX = 32, HX = TX + 4, HY = TY + 4;
+  static constexpr int NB = (TY >= 16 || sizeof(R) == 8) ? 2 : 1;
   static constexpr size_t q_off = 0;
   static constexpr size_t phi_off = q_off + sizeof(R) * 5 * HY * HX;
-  static constexpr size_t xs_off = phi_off + sizeof(R) * HY * HX;
+  static constexpr size_t xs_off = phi_off + sizeof(R) * NB * HY * HX;
   static constexpr size_t ys_off = xs_off + sizeof(FaceState<R>) * TY * (TX + 2) * 2;
   static constexpr size_t fx_off = ys_off + sizeof(FaceState<R>) * (TY + 2) * TX * 2;
   static constexpr size_t fy_off = fx_off + sizeof(R) * 5 * TY * (TX + 1);
   static constexpr size_t id_off = fy_off + sizeof(R) * 5 * (TY + 1) * TX;
-  static constexpr size_t eos_off = (id_off + HY * HX + 15) / 16 * 16;
+  static constexpr size_t eos_off = (id_off + NB * HY * HX + 15) / 16 * 16;
   static constexpr size_t eosd_off = eos_off + (sizeof(EosP<R>) * 2 + 15) / 16 * 16;
   static constexpr size_t bytes = eosd_off + sizeof(EosDev) * 2;
 };
@@ -50,11 +56,11 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   using SM = StageSmem<R, TY>;
   extern __shared__ __align__(16) unsigned char smem[];
   R* s_q = reinterpret_cast<R*>(smem + SM::q_off);                         // [5][HY][HX]
-  R* s_phi = reinterpret_cast<R*>(smem + SM::phi_off);                     // [HY][HX]
+  R* const s_phi0 = reinterpret_cast<R*>(smem + SM::phi_off);               // [NB][HY][HX]
   FaceState<R>* s_st = reinterpret_cast<FaceState<R>*>(smem + SM::xs_off);  // x: [TY][TX+2][2], then y: [TY+2][TX][2]
   R* s_fx = reinterpret_cast<R*>(smem + SM::fx_off);                       // [5][TY][TX+1]
   R* s_fy = reinterpret_cast<R*>(smem + SM::fy_off);                       // [5][TY+1][TX]
-  uint8_t* s_id = smem + SM::id_off;                                       // [HY][HX]
+  uint8_t* const s_id0 = smem + SM::id_off;                                // [NB][HY][HX]
   EosP<R>* s_eos = reinterpret_cast<EosP<R>*>(smem + SM::eos_off);
   EosDev* s_eosd = reinterpret_cast<EosDev*>(smem + SM::eosd_off);
   __shared__ double s_dt;
@@ -219,6 +225,9 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
 
   for (int k = k0; k < k1; ++k) {
     const long long pk = (long long)k * nxy;  // k is inside the grid
+    const int buf = SM::NB == 2 ? ((k - k0) & 1) : 0;
+    R* const s_phi = s_phi0 + buf * PL;
+    uint8_t* const s_id = s_id0 + buf * PL;
     // ---- own column: plane k+2, z face states of cell k+1, z flux of face k+1/2
     load(plane(k + 2) + own_base, P2, ph[4], id2);
     cell_faces<R>(s_eos[id1], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad);
@@ -440,7 +449,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
         }
       }
     }
-    __syncthreads();
+    if constexpr (SM::NB == 1) __syncthreads();  // the next plane overwrites s_phi and s_id
 
     // ---- shift the z window
 #pragma unroll
