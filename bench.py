@@ -344,7 +344,7 @@ def run_ours(args):
                 "ms_per_step": round(ms64 / k64, 3), "dtype": "f64",
                 "roofline": {"bound": "alu", "pipe": "fp64", "peak": 1.25, "unit": "TFLOP/s",
                              "peak_source": "nominal GB300 FP64 rate (1.9 DFMA/clk/SM measured)",
-                             "fp64_pipe_busy_ncu": 0.76, "kernel": "k_stage<double,8> (bulk stage)",
+                             "fp64_pipe_busy_ncu": 0.74, "kernel": "k_stage<double,8> (bulk stage)",
                              "kernel_ms_avg": round(avg64, 4), "traffic": ncu_traffic("fp64", args.n),
                              "hbm_frac": round(alg_bytes / (avg64 * 1e-3) / 1e9 / hbm, 4)}}
         del g64

@@ -19,7 +19,7 @@ template <typename R>
 __device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& qd, double rho, double m1, double m2,
                                                double m3, double E, R P[5]) {
   if constexpr (sizeof(R) == 8) {
-    const double inv = 1.0 / rho;
+    const double inv = rrcp<double>(rho);
     const double u = m1 * inv, v = m2 * inv, w = m3 * inv;
     const double ke = 0.5 * ((m1 * u + m2 * v) + m3 * w);
     const double e = (E - ke) * inv;

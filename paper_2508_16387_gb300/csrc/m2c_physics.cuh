@@ -62,14 +62,16 @@ __host__ inline EosDev make_eos_dev(int type, const double* prm) { return make_e
 // Division, reciprocal and square root of the working precision: IEEE for FP64;
 // for the FP32 half of the mixed path the hardware approximations (a few ulp),
 // which are far below the FP32 rounding already accepted there.
+__device__ __forceinline__ double rcp_nr(double b);
+__device__ __forceinline__ double div_nr(double a, double b);
 template <typename R>
 __device__ __forceinline__ R rdiv(R a, R b) {
-  if constexpr (sizeof(R) == 8) return a / b;
+  if constexpr (sizeof(R) == 8) return div_nr(a, b);
   else return __fdividef(a, b);
 }
 template <typename R>
 __device__ __forceinline__ R rrcp(R x) {
-  if constexpr (sizeof(R) == 8) return (R)1 / x;
+  if constexpr (sizeof(R) == 8) return rcp_nr(x);
   else return __fdividef(1.0f, x);
 }
 template <typename R>
@@ -228,6 +230,41 @@ __host__ __device__ __forceinline__ double f2d(float x) {
   if (a - 0x00800000u < 0x7f800000u - 0x00800000u)  // normal: rebias 127 -> 1023
     return double_of_words(((a >> 3) + (896u << 20)) | (f & 0x80000000u), a << 29);
   return f2d_rare(x);
+}
+
+// FP64 reciprocal and quotient for the bulk kernels: a binary32 seed of 1/b
+// (b's leading 23 mantissa bits, then the hardware's approximate binary32
+// reciprocal; relative error below 2^-21 together), refined by two
+// Newton-Raphson steps x <- x + x (1 - b x), each of which squares the
+// relative error, to 1/b within an ulp; the quotient a x then takes one
+// residual correction q <- q + (a - b q) x (Markstein, IBM J. Res. Dev. 34,
+// 1990). The seed stays on the integer and special-function pipes. For |b|
+// outside [2^-125, 2^125) (zeros, infinities, NaNs included) the IEEE
+// operations. Both are checked against IEEE 1/b and a/b on the device.
+__device__ __forceinline__ bool nr_range(double b) {
+  return (hi_of(b) & 0x7fffffffu) - 0x38200000u < 0x47c00000u - 0x38200000u;
+}
+__device__ __forceinline__ double rcp_nr_in_range(double b) {
+  const unsigned hi = hi_of(b), ah = hi & 0x7fffffffu;
+  const float f = float_of((((ah - 0x38000000u) << 3) | (lo_of(b) >> 29)) | (hi & 0x80000000u));
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));
+  const unsigned rb = bits_of(r), ra = rb & 0x7fffffffu;
+  double x = double_of_words(((ra >> 3) + (896u << 20)) | (rb & 0x80000000u), ra << 29);
+  x = fma(x, fma(-b, x, 1.0), x);
+  x = fma(x, fma(-b, x, 1.0), x);
+  return x;
+}
+__device__ __forceinline__ double rcp_nr(double b) {
+  if (nr_range(b)) return rcp_nr_in_range(b);
+  return 1.0 / b;
+}
+__device__ __forceinline__ double div_nr(double a, double b) {
+  if (nr_range(b)) {
+    const double x = rcp_nr_in_range(b), q = a * x;
+    return fma(fma(-b, q, a), x, q);
+  }
+  return a / b;
 }
 
 template <typename R>
@@ -438,11 +475,11 @@ __device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& 
 
 // de/drho at constant p for MG
 __device__ inline bool mg_dedr(const EosDev& q, double rho, double& dedr) {
-  double eta = 1.0 - q.rho0 / rho;
+  double eta = 1.0 - div_nr(q.rho0, rho);
   if (!(eta < q.eta_max)) return false;
   double pR, dpR, eR, deR;
   mg_ref<double>(q, eta, pR, dpR, eR, deR);
-  dedr = (deR - dpR * q.inv_rg) * q.rho0 / (rho * rho);
+  dedr = div_nr((deR - dpR * q.inv_rg) * q.rho0, rho * rho);
   return true;
 }
 
@@ -451,20 +488,20 @@ __device__ inline bool mg_dedr(const EosDev& q, double rho, double& dedr) {
 __device__ inline int mg_hugoniot(const EosDev& q, const Side& K, double p, double& rho_out, double& drdp) {
   double lo = K.rho, hi = q.rho0 * q.s / (q.s - 1.0);
   if (!(hi > lo)) return M2C_ENONPHYS;
-  double rho = K.rho + (p - K.p) / (K.c * K.c);
+  double rho = K.rho + div_nr(p - K.p, K.c * K.c);
   if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
   bool extra = false, done = false;
   for (int it = 0; it < kHugCap; ++it) {
-    double eta = 1.0 - q.rho0 / rho;
+    double eta = 1.0 - div_nr(q.rho0, rho);
     if (!(eta < q.eta_max)) return M2C_ENONPHYS;
     double pR, dpR, eR, deR;
     mg_ref<double>(q, eta, pR, dpR, eR, deR);
     double e = eR + (p - pR) * q.inv_rg;
-    double dedr = (deR - dpR * q.inv_rg) * q.rho0 / (rho * rho);
-    double H = e - K.e - 0.5 * (p + K.p) * (1.0 / K.rho - 1.0 / rho);
-    double dH = dedr - 0.5 * (p + K.p) / (rho * rho);
+    double dedr = div_nr((deR - dpR * q.inv_rg) * q.rho0, rho * rho);
+    double H = e - K.e - 0.5 * (p + K.p) * (div_nr(1.0, K.rho) - div_nr(1.0, rho));
+    double dH = dedr - div_nr(0.5 * (p + K.p), rho * rho);
     if (H > 0.0) lo = rho; else hi = rho;
-    double rn = rho - H / dH;
+    double rn = rho - div_nr(H, dH);
     if (!(rn >= lo && rn <= hi)) rn = 0.5 * (lo + hi);
     bool conv = fabs(rn - rho) <= kHugTol * rn;
     rho = rn;
@@ -474,18 +511,18 @@ __device__ inline int mg_hugoniot(const EosDev& q, const Side& K, double p, doub
   if (!done) return M2C_ENOCONV;
   double dedr;
   if (!mg_dedr(q, rho, dedr)) return M2C_ENONPHYS;
-  double Hp = q.inv_rg - 0.5 * (1.0 / K.rho - 1.0 / rho);
-  double Hr = dedr - 0.5 * (p + K.p) / (rho * rho);
+  double Hp = q.inv_rg - 0.5 * (div_nr(1.0, K.rho) - div_nr(1.0, rho));
+  double Hr = dedr - div_nr(0.5 * (p + K.p), rho * rho);
   rho_out = rho;
-  drdp = -Hp / Hr;
+  drdp = -div_nr(Hp, Hr);
   return M2C_OK;
 }
 
 __device__ inline int mg_rhs(const EosDev& q, double p, double rho, double& drho, double& dfv) {
   double e, c2;
-  if (!eos_e_c2<double>(q, rho, 1.0 / rho, p, e, c2)) return M2C_ENONPHYS;
-  drho = 1.0 / c2;
-  dfv = 1.0 / (rho * sqrt(c2));
+  if (!eos_e_c2<double>(q, rho, div_nr(1.0, rho), p, e, c2)) return M2C_ENONPHYS;
+  drho = div_nr(1.0, c2);
+  dfv = div_nr(1.0, rho * sqrt(c2));
   return M2C_OK;
 }
 
@@ -502,10 +539,10 @@ __device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& 
     double rho, drdp;
     int st = mg_hugoniot(q, K, p, rho, drdp);
     if (st) return st;
-    double dv = 1.0 / K.rho - 1.0 / rho;
+    double dv = div_nr(1.0, K.rho) - div_nr(1.0, rho);
     double fv = sqrt((p - K.p) * dv);
     f = fv;
-    df = (dv + (p - K.p) * drdp / (rho * rho)) / (2.0 * fv);
+    df = div_nr(dv + div_nr((p - K.p) * drdp, rho * rho), 2.0 * fv);
     rs = rho;
     if (drs) *drs = drdp;
     return M2C_OK;

@@ -22,3 +22,22 @@ def test_integer_conversions_match_ieee(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "mismatches 0" in r.stdout
+
+
+@pytest.mark.gpu
+def test_fp64_reciprocal_and_quotient_match_ieee(tmp_path):
+    """The bulk kernels' FP64 quotient (Newton-Raphson reciprocal from a binary32 seed, then a
+    residual correction) equals IEEE a / b on the device; the reciprocal alone is within an ulp."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = str(tmp_path / "div_check")
+    subprocess.run([nvcc, "-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_2508_16387_gb300", "csrc"),
+                    os.path.join(HERE, "native", "div_check.cu"), "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "quotient mismatches 0" in r.stdout, r.stdout
+    worst = float(r.stdout.split("reciprocal worst ulp")[1].split()[0])
+    assert worst <= 1.0, r.stdout
