@@ -8,7 +8,7 @@
 namespace m2c {
 
 struct LaunchPlan {
-  int ty = 8;            // tile rows (4 or 8)
+  int ty = 8;            // tile rows (4, 8 or, FP32 only, 16)
   int sched = 0;         // 0: fixed stride over tiles, 1: atomic tile counter
   int blocks_per_sm = 0; // persistent grid of blocks_per_sm x SMs blocks; 0: one block per tile
   unsigned long long* counter = nullptr;
