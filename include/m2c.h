@@ -192,7 +192,10 @@ m2c_status m2c_get_stats(m2c_ctx* ctx, m2c_stats* out);
  * get the iteration count and per-problem m2c_status. on_device = 1: all
  * arrays are device pointers and the call is asynchronous on stream; 0: host
  * arrays, the call stages them and blocks. Returns the first non-OK status of
- * the batch (host arrays) or M2C_OK (device arrays; read status[]). */
+ * the batch (host arrays) or M2C_OK (device arrays; read status[]).
+ * M2C_EINVAL, before any device work and with the reason in
+ * m2c_last_error(NULL): n < 0, a NULL array or descriptor, or EOS parameters
+ * that m2c_set_eos rejects. */
 m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
                              const double* R, double* out, int* iters, int* status, int on_device, void* stream);
 
@@ -210,7 +213,8 @@ m2c_status m2c_solve_riemann_mixed(int n, const m2c_eos_desc* eosL, const double
 
 /* Post-shock state of a shock moving in +x into the state w = (rho, u, p) with
  * pressure p1 behind it (the right-facing wave of the exact Riemann solver):
- * out = (rho1, u1, shock speed). Host arrays; blocks. */
+ * out = (rho1, u1, shock speed). Host arrays; blocks. M2C_EINVAL as for
+ * m2c_solve_riemann. */
 m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]);
 
 /* Allocation-free stage residual. The paper has no counterpart: this entry

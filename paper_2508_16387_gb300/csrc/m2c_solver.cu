@@ -494,9 +494,36 @@ Layout layout_for(long long N) {
   return L;
 }
 
+// Error text of the calls that take no context (m2c_last_error(NULL)).
+thread_local std::string g_noctx_error;
+
+// set_err with a null context records the text for m2c_last_error(NULL).
 m2c_status set_err(m2c_ctx* c, m2c_status st, const std::string& msg) {
   if (c) c->err = msg;
+  else g_noctx_error = msg;
   return st;
+}
+
+// Parameter check of an EOS (App. B.1 and B.3): stiffened gas (gamma, p_c) with
+// gamma > 1; Mie-Grueneisen (rho0, c0, s, Gamma0[, e0[, eta_min]]) with rho0,
+// c0, Gamma0 > 0 and s > 1. nullptr when valid, else the reason.
+const char* eos_param_error(int type, const double* prm, int nparams) {
+  if (type == M2C_EOS_SG) {
+    if (nparams < 2 || !(prm[0] > 1.0)) return "SG needs gamma > 1 and p_c";
+    return nullptr;
+  }
+  if (type == M2C_EOS_MG) {
+    if (nparams < 4 || nparams > 6) return "MG needs 4 to 6 params";
+    if (!(prm[0] > 0.0) || !(prm[1] > 0.0) || !(prm[2] > 1.0) || !(prm[3] > 0.0))
+      return "MG needs rho0, c0 > 0, s > 1, Gamma0 > 0";
+    return nullptr;
+  }
+  return "unknown EOS type";
+}
+
+// The same for an EOS descriptor of the Riemann entry points (all six params given).
+const char* eos_desc_error(const m2c_eos_desc* e) {
+  return eos_param_error(e->type, e->params, e->type == M2C_EOS_SG ? 2 : 6);
 }
 
 m2c_status cuda_check(m2c_ctx* c, cudaError_t e, const char* what) {
@@ -782,19 +809,9 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
 m2c_status m2c_set_eos(m2c_ctx* c, int material, int type, const double* params, int nparams) {
   if (!c) return M2C_EINVAL;
   if (material < 0 || material > 1 || !params) return set_err(c, M2C_EINVAL, "bad material or params");
+  if (const char* why = eos_param_error(type, params, nparams)) return set_err(c, M2C_EINVAL, why);
   double prm[6] = {0, 0, 0, 0, 0, -INFINITY};
-  if (type == M2C_EOS_SG) {
-    if (nparams < 2 || !(params[0] > 1.0)) return set_err(c, M2C_EINVAL, "SG needs gamma > 1 and p_c");
-    prm[0] = params[0];
-    prm[1] = params[1];
-  } else if (type == M2C_EOS_MG) {
-    if (nparams < 4 || nparams > 6) return set_err(c, M2C_EINVAL, "MG needs 4 to 6 params");
-    for (int i = 0; i < nparams; ++i) prm[i] = params[i];
-    if (!(prm[0] > 0.0) || !(prm[1] > 0.0) || !(prm[2] > 1.0) || !(prm[3] > 0.0))
-      return set_err(c, M2C_EINVAL, "MG needs rho0, c0 > 0, s > 1, Gamma0 > 0");
-  } else {
-    return set_err(c, M2C_EINVAL, "unknown EOS type");
-  }
+  for (int i = 0; i < (type == M2C_EOS_SG ? 2 : nparams); ++i) prm[i] = params[i];
   c->host.eos[material] = make_eos<double>(type, prm);
   c->host.eosf[material] = make_eos<float>(type, prm);
   c->eos_set[material] = true;
@@ -1105,7 +1122,9 @@ m2c_status m2c_get_stats(m2c_ctx* c, m2c_stats* out) {
 static m2c_status solve_riemann_batch(int mixed, int n, const m2c_eos_desc* eosL, const double* L,
                                       const m2c_eos_desc* eosR, const double* R, double* out, int* iters, int* status,
                                       int on_device, void* stream) {
-  if (n < 0 || !eosL || !eosR || !L || !R || !out) return M2C_EINVAL;
+  if (n < 0 || !eosL || !eosR || !L || !R || !out) return set_err(nullptr, M2C_EINVAL, "bad batch arguments");
+  if (const char* why = eos_desc_error(eosL)) return set_err(nullptr, M2C_EINVAL, std::string("left EOS: ") + why);
+  if (const char* why = eos_desc_error(eosR)) return set_err(nullptr, M2C_EINVAL, std::string("right EOS: ") + why);
   if (n == 0) return M2C_OK;
   double pl[6] = {0, 0, 0, 0, 0, -INFINITY}, pr[6] = {0, 0, 0, 0, 0, -INFINITY};
   for (int i = 0; i < 6; ++i) {
@@ -1158,7 +1177,8 @@ m2c_status m2c_solve_riemann_mixed(int n, const m2c_eos_desc* eosL, const double
 }
 
 m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]) {
-  if (!eos || !w || !out) return M2C_EINVAL;
+  if (!eos || !w || !out) return set_err(nullptr, M2C_EINVAL, "bad shock-state arguments");
+  if (const char* why = eos_desc_error(eos)) return set_err(nullptr, M2C_EINVAL, why);
   double prm[6];
   for (int i = 0; i < 6; ++i) prm[i] = eos->params[i];
   const EosDev q = make_eos_dev(eos->type, prm);
@@ -1215,8 +1235,6 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[kMaxDevices] = {};
-thread_local std::string g_noctx_error;
-
 m2c_status noalloc_fail(m2c_status st, const std::string& msg) {
   g_noctx_error = msg;
   return st;

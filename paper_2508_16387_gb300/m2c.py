@@ -16,7 +16,7 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libm2cgpu.so")
 
-M2C_OK = 0
+M2C_OK, M2C_EINVAL = 0, 1
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENONPHYS", 6: "EVACUUM",
           7: "ETIMEOUT", 8: "EOVERFLOW"}
 EOS_SG, EOS_MG = 0, 1

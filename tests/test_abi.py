@@ -43,3 +43,23 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(m2c, "_lib", None)
     with pytest.raises(RuntimeError):
         m2c.lib()
+
+
+@pytest.mark.parametrize("left,right,why", [
+    ((7, (1.4, 0.0)), (0, (1.4, 0.0)), "left EOS: unknown EOS type"),
+    ((0, (1.0, 0.0)), (0, (1.4, 0.0)), "left EOS: SG needs gamma > 1"),
+    ((0, (1.4, 0.0)), (1, (1000.0, 1483.0, 0.9, 0.28, 0.0, -float("inf"))), "right EOS: MG needs rho0, c0 > 0, s > 1"),
+    ((0, (1.4, 0.0)), (1, (0.0, 1483.0, 1.75, 0.28, 0.0, -float("inf"))), "right EOS: MG needs rho0, c0 > 0, s > 1"),
+])
+def test_riemann_entry_rejects_bad_eos_before_any_device_work(left, right, why):
+    """Argument checks run on the host before any CUDA call, with the reason in
+    m2c_last_error(NULL); the EOS rules are those of m2c_set_eos."""
+    from paper_2508_16387_gb300 import m2c
+    L = m2c.lib()
+    eL, eR = m2c.eos_desc(left), m2c.eos_desc(right)
+    st = ctypes.c_double * 3
+    out = (ctypes.c_double * 4)()
+    for fn in (L.m2c_solve_riemann, L.m2c_solve_riemann_mixed):
+        code = fn(1, ctypes.byref(eL), st(1.0, 0.0, 1e5), ctypes.byref(eR), st(1.0, 0.0, 1e5), out, None, None, 0, None)
+        assert code == m2c.M2C_EINVAL
+        assert L.m2c_last_error(None).decode().startswith(why)
