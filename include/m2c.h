@@ -96,11 +96,15 @@ size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
  * lo: lower corner (only used to report coordinates), h > 0: cell edge,
  * bc[6]: m2c_bc per side, workspace: device pointer of ws_bytes >=
  * m2c_workspace_bytes(), stream: a cudaStream_t (NULL = legacy default stream).
- * Defaults: CFL 0.5, reinitialisation every 10 steps with 5 iterations. */
+ * Defaults: CFL 0.5, reinitialisation every 10 steps with 5 iterations.
+ * Argument errors return before any device work, with the reason in
+ * m2c_last_error(NULL). */
 m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[3], double h, const int bc[6],
                          int precision, void* workspace, size_t ws_bytes, void* stream);
 
-/* Material 0 (phi >= 0) or 1 (phi < 0) gets an EOS; nparams <= 6. */
+/* Material 0 (phi >= 0) or 1 (phi < 0) gets an EOS (App. B.1, B.3):
+ * M2C_EOS_SG (gamma > 1, p_c) or M2C_EOS_MG (rho0 > 0, c0 > 0, s > 1,
+ * Gamma0 > 0 [, e0 [, eta_min]]); anything else is M2C_EINVAL. */
 m2c_status m2c_set_eos(m2c_ctx* ctx, int material, int type, const double* params, int nparams);
 
 /* CFL number of dt = CFL h / max_cells sum_d (|V_d| + c) (the sum runs over the

@@ -740,21 +740,27 @@ size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision) {
 m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[3], double h, const int bc[6],
                          int precision, void* workspace, size_t ws_bytes, void* stream) {
   (void)lo;
-  if (!out) return M2C_EINVAL;
+  if (!out) return set_err(nullptr, M2C_EINVAL, "out is NULL");
   *out = nullptr;
-  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !workspace) return M2C_EINVAL;
-  if ((long long)nx * ny * nz < 2) return M2C_EINVAL;  // no axis to move along: no time step
-  if ((long long)nx * ny * nz >= (1ll << 31)) return M2C_EINVAL;  // 32-bit cell indices in some kernels
-  if (precision != M2C_FP64 && precision != M2C_MIXED) return M2C_EINVAL;
+  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !workspace)
+    return set_err(nullptr, M2C_EINVAL, "grid sizes >= 1, h > 0, bc and workspace required");
+  if ((long long)nx * ny * nz < 2)  // no axis to move along: no time step
+    return set_err(nullptr, M2C_EINVAL, "a grid needs an axis with more than one cell");
+  if ((long long)nx * ny * nz >= (1ll << 31))  // 32-bit cell indices in some kernels
+    return set_err(nullptr, M2C_EINVAL, "a grid holds fewer than 2^31 cells");
+  if (precision != M2C_FP64 && precision != M2C_MIXED) return set_err(nullptr, M2C_EINVAL, "unknown precision");
   for (int a = 0; a < 3; ++a) {
     for (int s = 0; s < 2; ++s)
-      if (bc[2 * a + s] != M2C_BC_TRANSMISSIVE && bc[2 * a + s] != M2C_BC_PERIODIC) return M2C_EINVAL;
-    if ((bc[2 * a] == M2C_BC_PERIODIC) != (bc[2 * a + 1] == M2C_BC_PERIODIC)) return M2C_EINVAL;
+      if (bc[2 * a + s] != M2C_BC_TRANSMISSIVE && bc[2 * a + s] != M2C_BC_PERIODIC)
+        return set_err(nullptr, M2C_EINVAL, "unknown boundary condition");
+    if ((bc[2 * a] == M2C_BC_PERIODIC) != (bc[2 * a + 1] == M2C_BC_PERIODIC))
+      return set_err(nullptr, M2C_EINVAL, "periodic on one side of an axis only");
   }
-  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return M2C_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign)
+    return set_err(nullptr, M2C_EINVAL, "workspace is not 256-byte aligned");
   const long long N = (long long)nx * ny * nz;
   const Layout L = layout_for(N);
-  if (ws_bytes < L.total) return M2C_ENOMEM;
+  if (ws_bytes < L.total) return set_err(nullptr, M2C_ENOMEM, "workspace smaller than m2c_workspace_bytes()");
   m2c_ctx* c = new (std::nothrow) m2c_ctx();
   if (!c) return M2C_ENOMEM;
   unsigned char* ws = static_cast<unsigned char*>(workspace);

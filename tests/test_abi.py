@@ -63,3 +63,21 @@ def test_riemann_entry_rejects_bad_eos_before_any_device_work(left, right, why):
         code = fn(1, ctypes.byref(eL), st(1.0, 0.0, 1e5), ctypes.byref(eR), st(1.0, 0.0, 1e5), out, None, None, 0, None)
         assert code == m2c.M2C_EINVAL
         assert L.m2c_last_error(None).decode().startswith(why)
+
+
+@pytest.mark.parametrize("n,bc,why", [
+    ((1, 1, 1), (0,) * 6, "a grid needs an axis with more than one cell"),
+    ((8, 8, 8), (1, 0, 0, 0, 0, 0), "periodic on one side of an axis only"),
+    ((8, 8, 8), (2, 2, 0, 0, 0, 0), "unknown boundary condition"),
+    ((0, 8, 8), (0,) * 6, "grid sizes >= 1"),
+])
+def test_init_grid_rejects_bad_grids_before_any_device_work(n, bc, why):
+    """The grid checks of m2c_init_grid run on the host before the workspace is touched
+    (the workspace pointer below is never dereferenced)."""
+    from paper_2508_16387_gb300 import m2c
+    L = m2c.lib()
+    ctx = ctypes.c_void_p()
+    code = L.m2c_init_grid(ctypes.byref(ctx), *n, None, 0.1, (ctypes.c_int * 6)(*bc), m2c.FP64,
+                           ctypes.c_void_p(256), 1 << 40, None)
+    assert code == m2c.M2C_EINVAL and not ctx.value
+    assert L.m2c_last_error(None).decode().startswith(why)
