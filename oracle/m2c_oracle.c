@@ -60,7 +60,19 @@ typedef struct {
   int reinit_every; /* 0: never */
   int reinit_iters;
   or_eos_t eos[2]; /* eos[0] where phi >= 0, eos[1] where phi < 0 */
+  /* scheme options (Sec. 4.3, App. C, App. D); the defaults are the paper's
+   * workload choices used everywhere else in this file */
+  int rk;          /* Runge-Kutta order: 2 (default), 3 (TVD RK3), 1 (forward Euler) */
+  int limiter;     /* LIM_VA_MOD (default) or LIM_MC */
+  int flux;        /* FLUX_HLLC (default) or FLUX_LLF */
+  double mc_alpha; /* alpha of the MC limiter (1.2 by default) */
+  double dt_fixed; /* > 0: constant time step instead of the CFL rule */
 } or_grid_t;
+
+#define LIM_VA_MOD 0 /* modified van Albada, App. D */
+#define LIM_MC 1     /* monotonized central, App. D, Eq. theta */
+#define FLUX_HLLC 0  /* App. C.4 */
+#define FLUX_LLF 1   /* local Lax-Friedrichs, App. C.1, Eq. Lax-Friedrichs */
 
 typedef struct {
   double dt;             /* time step of the last step */
@@ -494,6 +506,34 @@ static int hllc(const or_eos_t* q, const double Lp[5], const double Rp[5], int d
   return OR_OK;
 }
 
+/* Local Lax-Friedrichs flux (App. C.1, Eq. Lax-Friedrichs):
+ * Phi = (F(W_L).n + F(W_R).n)/2 - lambda_max (W_R - W_L)/2 with
+ * lambda_max = max(|u_L| + c_L, |u_R| + c_R), u the normal velocities. Inputs
+ * are primitive states; one EOS for the whole face (Reading R15). */
+static int llf(const or_eos_t* q, const double Lp[5], const double Rp[5], int d, double F[5]) {
+  double c2L, c2R, eL, eR;
+  int st = eos_c2(q, Lp[0], Lp[4], &c2L);
+  if (!st) st = eos_c2(q, Rp[0], Rp[4], &c2R);
+  if (!st) st = eos_e(q, Lp[0], Lp[4], &eL);
+  if (!st) st = eos_e(q, Rp[0], Rp[4], &eR);
+  if (st) return st;
+  double EL = eL + 0.5 * ((Lp[1] * Lp[1] + Lp[2] * Lp[2]) + Lp[3] * Lp[3]);
+  double ER = eR + 0.5 * ((Rp[1] * Rp[1] + Rp[2] * Rp[2]) + Rp[3] * Rp[3]);
+  double lam = fmax(fabs(Lp[1 + d]) + sqrt(c2L), fabs(Rp[1 + d]) + sqrt(c2R));
+  double FL[5], FR[5], WL[5], WR[5];
+  phys_flux(Lp, EL, d, FL);
+  phys_flux(Rp, ER, d, FR);
+  WL[0] = Lp[0]; WL[1] = Lp[0] * Lp[1]; WL[2] = Lp[0] * Lp[2]; WL[3] = Lp[0] * Lp[3]; WL[4] = Lp[0] * EL;
+  WR[0] = Rp[0]; WR[1] = Rp[0] * Rp[1]; WR[2] = Rp[0] * Rp[2]; WR[3] = Rp[0] * Rp[3]; WR[4] = Rp[0] * ER;
+  for (int v = 0; v < 5; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * lam * (WR[v] - WL[v]);
+  return OR_OK;
+}
+
+/* The numerical flux function Phi selected for the grid. */
+static int num_flux(const or_grid_t* g, const or_eos_t* q, const double Lp[5], const double Rp[5], int d, double F[5]) {
+  return g->flux == FLUX_LLF ? llf(q, Lp, Rp, d, F) : hllc(q, Lp, Rp, d, F);
+}
+
 /* ------------------------------------------------------------------ */
 /* MUSCL reconstruction with the modified van Albada limiter, App. D    */
 /* ------------------------------------------------------------------ */
@@ -505,6 +545,21 @@ static int hllc(const or_eos_t* q, const double Lp[5], const double Rp[5], int d
 static double va_slope(double a, double b) {
   if (!(a * b > 0.0)) return 0.0;
   return a * b * (a + b) / (a * a + b * b);
+}
+
+/* Monotonized central limiter (App. D, Eq. theta) on the uniform grid
+ * (A = B = 1): phi(theta) = max(0, min(alpha theta, (theta + 1)/2, alpha)) and
+ * sigma = phi(theta) b with theta = a/b. Reading R34: written without the
+ * division, multiplying through by b (the inequalities turn for b < 0), and
+ * sigma = 0 for b = 0 (phi(+-inf) b = 0). */
+static double mc_slope(double a, double b, double alpha) {
+  if (b > 0.0) return fmax(0.0, fmin(fmin(alpha * a, 0.5 * (a + b)), alpha * b));
+  if (b < 0.0) return fmin(0.0, fmax(fmax(alpha * a, 0.5 * (a + b)), alpha * b));
+  return 0.0;
+}
+
+static double limited_slope(const or_grid_t* g, double a, double b) {
+  return g->limiter == LIM_MC ? mc_slope(a, b, g->mc_alpha) : va_slope(a, b);
 }
 
 /* ------------------------------------------------------------------ */
@@ -617,7 +672,7 @@ static void face_states(const or_grid_t* g, const double* P, const unsigned char
   for (int v = 0; v < 5; ++v) {
     double a = P[v * N + c] - P[v * N + cm];
     double b = P[v * N + cp] - P[v * N + c];
-    double s = va_slope(a, b);
+    double s = limited_slope(g, a, b);
     tm[v] = P[v * N + c] - 0.5 * s;
     tp[v] = P[v * N + c] + 0.5 * s;
   }
@@ -627,7 +682,7 @@ static void face_states(const or_grid_t* g, const double* P, const unsigned char
 
 /* Flux through the face between cell a at (i,j,k) and cell b = a + e_d, as seen
  * by cell a (side 0) or by cell b (side 1), Sec. 4.2. Same material: the MUSCL
- * flux Phi(W_ab, W_ba) with HLLC. Different materials (FIVER): the 1D
+ * flux Phi(W_ab, W_ba) with the grid's flux function (HLLC by default). Different materials (FIVER): the 1D
  * two-material Riemann problem of the normal projections gives W*_ab, W*_ba
  * (tangential velocity of each side's own face state, Reading R8), and
  * F_ab = Phi(W_ab, W*_ab; EOS_a), F_ba = Phi(W*_ba, W_ba; EOS_b) (Reading R16:
@@ -640,7 +695,7 @@ static int face_flux(const or_grid_t* g, const double* P, const unsigned char* i
   face_states(g, P, id, bi, bj, bk, d, Qb, Qb_p);
   int ma = id[cell_index(g, i, j, k)], mb = id[cell_index(g, bi, bj, bk)];
   if (iters) *iters = 0;
-  if (ma == mb) return hllc(&g->eos[ma], Qa, Qb, d, F);
+  if (ma == mb) return num_flux(g, &g->eos[ma], Qa, Qb, d, F);
   double wa[3] = {Qa[0], Qa[1 + d], Qa[4]};
   double wb[3] = {Qb[0], Qb[1 + d], Qb[4]};
   double rs[4];
@@ -652,13 +707,13 @@ static int face_flux(const or_grid_t* g, const double* P, const unsigned char* i
     S[0] = rs[2];
     S[1 + d] = rs[1];
     S[4] = rs[0];
-    return hllc(&g->eos[ma], Qa, S, d, F);
+    return num_flux(g, &g->eos[ma], Qa, S, d, F);
   }
   for (int v = 0; v < 5; ++v) S[v] = Qb[v];
   S[0] = rs[3];
   S[1 + d] = rs[1];
   S[4] = rs[0];
-  return hllc(&g->eos[mb], S, Qb, d, F);
+  return num_flux(g, &g->eos[mb], S, Qb, d, F);
 }
 
 /* Third-order upwind-biased derivative of phi along d at cell c (Sec. 4.4,
@@ -902,8 +957,9 @@ static int phase_fix(const or_grid_t* g, double* W, double* phi, const unsigned 
 
 /* ------------------------------------------------------------------ */
 /* One time step, Sec. 2.3 steps (1)-(6) with the second-order TVD      */
-/* Runge-Kutta scheme of Sec. 4.3:                                      */
-/*   W1 = W + dt R(W);  W' = (W + (W1 + dt R(W1)))/2, the same for phi.  */
+/* Runge-Kutta schemes of Sec. 4.3 (TVD RK2 by default, TVD RK3, forward */
+/* Euler); RK2: W1 = W + dt R(W), W' = (W + (W1 + dt R(W1)))/2, and the */
+/* same for phi.                                                         */
 /* ------------------------------------------------------------------ */
 
 typedef struct {
@@ -944,19 +1000,38 @@ static int step_one(const or_grid_t* g, double* W, double* phi, long step_index,
     stats->err_cell = ec;
     return st;
   }
+  if (g->dt_fixed > 0.0) dt = g->dt_fixed; /* Sec. 4.3: a constant time step instead of the CFL rule */
   stats->dt = dt;
-  /* stage 1 */
+  /* stage 1: W1 = W + dt R(W), the same for phi */
   st = stage_residual(g, W, phi, wk->id, wk->P, wk->R, wk->L, stats);
   if (st) return st;
   long nif1 = stats->interface_faces;
-  for (long x = 0; x < 5 * N; ++x) wk->W1[x] = W[x] + dt * wk->R[x];
-  for (long c = 0; c < N; ++c) wk->phi1[c] = phi[c] + dt * wk->L[c];
-  /* stage 2, material ids frozen */
-  st = stage_residual(g, wk->W1, wk->phi1, wk->id, wk->P, wk->R, wk->L, stats);
-  if (st) return st;
+  if (g->rk == 1) { /* forward Euler (Sec. 4.3) */
+    for (long x = 0; x < 5 * N; ++x) W[x] = W[x] + dt * wk->R[x];
+    for (long c = 0; c < N; ++c) phi[c] = phi[c] + dt * wk->L[c];
+  } else {
+    for (long x = 0; x < 5 * N; ++x) wk->W1[x] = W[x] + dt * wk->R[x];
+    for (long c = 0; c < N; ++c) wk->phi1[c] = phi[c] + dt * wk->L[c];
+    /* stage 2, material ids frozen */
+    st = stage_residual(g, wk->W1, wk->phi1, wk->id, wk->P, wk->R, wk->L, stats);
+    if (st) return st;
+    if (g->rk == 3) {
+      /* TVD RK3 (Sec. 4.3): W2 = 3/4 W + 1/4 W1 + 1/4 dt R(W1) (into W1), then
+       * W' = 1/3 W + 2/3 W2 + 2/3 dt R(W2), each sum taken left to right */
+      for (long x = 0; x < 5 * N; ++x) wk->W1[x] = (0.75 * W[x] + 0.25 * wk->W1[x]) + 0.25 * dt * wk->R[x];
+      for (long c = 0; c < N; ++c) wk->phi1[c] = (0.75 * phi[c] + 0.25 * wk->phi1[c]) + 0.25 * dt * wk->L[c];
+      st = stage_residual(g, wk->W1, wk->phi1, wk->id, wk->P, wk->R, wk->L, stats);
+      if (st) return st;
+      for (long x = 0; x < 5 * N; ++x)
+        W[x] = (W[x] / 3.0 + 2.0 / 3.0 * wk->W1[x]) + 2.0 / 3.0 * dt * wk->R[x];
+      for (long c = 0; c < N; ++c) phi[c] = (phi[c] / 3.0 + 2.0 / 3.0 * wk->phi1[c]) + 2.0 / 3.0 * dt * wk->L[c];
+    } else {
+      /* TVD RK2: W' = (W + (W1 + dt R(W1)))/2 */
+      for (long x = 0; x < 5 * N; ++x) W[x] = 0.5 * (W[x] + (wk->W1[x] + dt * wk->R[x]));
+      for (long c = 0; c < N; ++c) phi[c] = 0.5 * (phi[c] + (wk->phi1[c] + dt * wk->L[c]));
+    }
+  }
   stats->interface_faces = nif1;
-  for (long x = 0; x < 5 * N; ++x) W[x] = 0.5 * (W[x] + (wk->W1[x] + dt * wk->R[x]));
-  for (long c = 0; c < N; ++c) phi[c] = 0.5 * (phi[c] + (wk->phi1[c] + dt * wk->L[c]));
   /* (5) reinitialisation when scheduled: after steps reinit_every, 2 reinit_every, ... */
   if (g->reinit_every > 0 && g->reinit_iters > 0 && (step_index + 1) % g->reinit_every == 0)
     reinit(g, phi, g->reinit_iters, wk->tmp0, wk->tmp1);
@@ -1030,8 +1105,9 @@ static void mk_eos(or_eos_t* q, int type, const double* prm) {
   for (int i = 0; i < 6; ++i) q->prm[i] = prm[i];
 }
 
-/* ip = {nx, ny, nz, bc[6], reinit_every, reinit_iters, eos_type0, eos_type1, nthreads}
- * dp = {h, cfl, eos_prm0[6], eos_prm1[6]} */
+/* ip = {nx, ny, nz, bc[6], reinit_every, reinit_iters, eos_type0, eos_type1, nthreads,
+ *       rk, limiter, flux}
+ * dp = {h, cfl, eos_prm0[6], eos_prm1[6], mc_alpha, dt_fixed} */
 static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   for (int a = 0; a < 3; ++a) g->n[a] = ip[a];
   for (int s = 0; s < 6; ++s) g->bc[s] = ip[3 + s];
@@ -1041,6 +1117,11 @@ static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   mk_eos(&g->eos[1], ip[12], dp + 8);
   g->h = dp[0];
   g->cfl = dp[1];
+  g->rk = ip[14];
+  g->limiter = ip[15];
+  g->flux = ip[16];
+  g->mc_alpha = dp[14];
+  g->dt_fixed = dp[15];
 #ifdef _OPENMP
   if (ip[13] > 0) omp_set_num_threads(ip[13]);
 #endif
@@ -1051,6 +1132,11 @@ static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   /* at least one axis with more than one cell: otherwise nothing moves and the time step is undefined */
   if (g->n[0] * g->n[1] * g->n[2] < 2) return OR_EINVAL;
   if (!(g->h > 0.0)) return OR_EINVAL;
+  if (g->rk != 1 && g->rk != 2 && g->rk != 3) return OR_EINVAL;
+  if (g->limiter != LIM_VA_MOD && g->limiter != LIM_MC) return OR_EINVAL;
+  if (g->flux != FLUX_HLLC && g->flux != FLUX_LLF) return OR_EINVAL;
+  if (g->limiter == LIM_MC && !(g->mc_alpha >= 0.0 && g->mc_alpha <= 2.0)) return OR_EINVAL;
+  if (!(g->dt_fixed >= 0.0)) return OR_EINVAL;
   return OR_OK;
 }
 
@@ -1115,6 +1201,14 @@ int or_hllc(int type, const double* prm, const double* qL, const double* qR, int
 }
 
 double or_va_slope(double a, double b) { return va_slope(a, b); }
+
+double or_mc_slope(double a, double b, double alpha) { return mc_slope(a, b, alpha); }
+
+int or_llf(int type, const double* prm, const double* qL, const double* qR, int d, double* F) {
+  or_eos_t q;
+  mk_eos(&q, type, prm);
+  return llf(&q, qL, qR, d, F);
+}
 
 /* Post-shock state of a shock moving in +x into the state w = (rho, u, p) at
  * pressure p1 behind it: out = {rho1, u1, shock speed}. The shocked state is

@@ -25,6 +25,8 @@ EOS_SG = 0
 EOS_MG = 1
 BC_TRANSMISSIVE = 0
 BC_PERIODIC = 1
+LIM_VA_MOD, LIM_MC = 0, 1
+FLUX_HLLC, FLUX_LLF = 0, 1
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 4: "ENOCONV", 5: "ENONPHYS", 6: "EVACUUM"}
 
@@ -52,6 +54,9 @@ def lib():
         L = ctypes.c_long
         _lib.or_va_slope.restype = d
         _lib.or_va_slope.argtypes = [d, d]
+        _lib.or_mc_slope.restype = d
+        _lib.or_mc_slope.argtypes = [d, d, d]
+        _lib.or_llf.argtypes = [i, p, p, p, i, p]
         for name in ("or_eos_pressure", "or_eos_energy", "or_eos_c2"):
             getattr(_lib, name).argtypes = [i, p, d, d, p]
         _lib.or_wave_curve.argtypes = [i, p, p, d, p]
@@ -117,11 +122,18 @@ class Grid:
     reinit_every: int = 10
     reinit_iters: int = 5
     threads: int = 0  # 0: OpenMP default
+    rk: int = 2  # Runge-Kutta order of Sec. 4.3: 2 (TVD RK2), 3 (TVD RK3), 1 (forward Euler)
+    limiter: int = 0  # LIM_VA_MOD or LIM_MC (App. D)
+    flux: int = 0  # FLUX_HLLC or FLUX_LLF (App. C)
+    mc_alpha: float = 1.2  # alpha of the MC limiter
+    dt_fixed: float = 0.0  # > 0: constant time step instead of the CFL rule (Sec. 4.3)
 
     def packed(self):
         ip = np.array(list(self.n) + list(self.bc) + [self.reinit_every, self.reinit_iters,
-                      self.eos[0].type, self.eos[1].type, self.threads], dtype=np.int32)
-        dp = np.concatenate([[self.h, self.cfl], self.eos[0].arr(), self.eos[1].arr()]).astype(np.float64)
+                      self.eos[0].type, self.eos[1].type, self.threads, self.rk, self.limiter, self.flux],
+                      dtype=np.int32)
+        dp = np.concatenate([[self.h, self.cfl], self.eos[0].arr(), self.eos[1].arr(),
+                             [self.mc_alpha, self.dt_fixed]]).astype(np.float64)
         return ip, dp
 
     @property
@@ -131,6 +143,10 @@ class Grid:
 
 def va_slope(a: float, b: float) -> float:
     return lib().or_va_slope(a, b)
+
+
+def mc_slope(a: float, b: float, alpha: float = 1.2) -> float:
+    return lib().or_mc_slope(a, b, alpha)
 
 
 def _eos_call(name, eos: EOS, x: float, y: float) -> float:
@@ -190,6 +206,12 @@ def riemann_batch(eosL: EOS, L: np.ndarray, eosR: EOS, R: np.ndarray):
 def hllc(eos: EOS, qL, qR, d: int) -> np.ndarray:
     F = np.zeros(5)
     _check(lib().or_hllc(eos.type, _ptr(eos.arr()), _ptr(_f64(qL, 5)), _ptr(_f64(qR, 5)), d, _ptr(F)), "hllc")
+    return F
+
+
+def llf(eos: EOS, qL, qR, d: int) -> np.ndarray:
+    F = np.zeros(5)
+    _check(lib().or_llf(eos.type, _ptr(eos.arr()), _ptr(_f64(qL, 5)), _ptr(_f64(qR, 5)), d, _ptr(F)), "llf")
     return F
 
 
