@@ -242,9 +242,10 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kind, n):
-    """Per-launch DRAM bytes of the bulk stage kernel from the committed ncu summary, scaled from
-    256^3 to n^3; None if the kernel sources changed since the counters were taken."""
+def _ncu_per_launch(key, n):
+    """A per-launch counter of the bulk stage kernel from the committed ncu summary, scaled from
+    256^3 to n^3 (both grow with the cells); None if the kernel sources changed since the
+    counters were taken."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.txt")
     try:
         vals = {}
@@ -255,9 +256,30 @@ def ncu_traffic(kind, n):
                     vals[k.strip()] = v.strip()
         if vals.get("kernel_source_sha256_16") != _kernel_source_hash():
             return None
-        return float(vals[f"{kind}_bytes_per_launch_256"]) * (n / 256.0) ** 3
+        return float(vals[key]) * (n / 256.0) ** 3
     except (OSError, KeyError, ValueError):
         return None
+
+
+def ncu_traffic(kind, n):
+    """DRAM read + write bytes per launch of the bulk stage kernel (dram__bytes_read.sum +
+    dram__bytes_write.sum)."""
+    return _ncu_per_launch(f"{kind}_bytes_per_launch_256", n)
+
+
+def issue_roofline(warp_inst, kernel_ms, sms, sm_mhz):
+    """Instruction-issue roofline of a launch: warp instructions per launch (smsp__inst_executed.sum
+    of the ncu capture, scaled to the launch) over the live mean launch time, against the SMs'
+    issue rate, 4 schedulers x 1 warp instruction per clock per SM at the sampled SM clock.
+    None without the counter or the clock."""
+    if not warp_inst or not kernel_ms or not sm_mhz:
+        return None
+    achieved = warp_inst / (kernel_ms * 1e-3) / 1e9
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    return {"achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "G warp-inst/s",
+            "frac": round(achieved / peak, 4), "warp_inst_per_launch": round(warp_inst),
+            "source": "smsp__inst_executed.sum per launch from the ncu capture, scaled by cells; "
+                      "peak = SMs x 4 schedulers x 1/clock x median sampled SM clock"}
 
 
 def cpu_baseline(n=256, steps=8):
@@ -313,7 +335,9 @@ def run_ours(args):
             "kernel": f"k_stage<float,{rows}> (bulk stage)" if args.prec == "mixed"
                       else "k_stage<double,8> (bulk stage)", "peak_source": src,
             "kernel_ms_avg": round(avg, 4), "kernel_share": round(kms / ms, 3) if ms > 0 else None,
-            "step_breakdown_ms": {k: round(v[0] / args.steps, 4) for k, v in time_steps.kernels.items()}}
+            "step_breakdown_ms": {k: round(v[0] / args.steps, 4) for k, v in time_steps.kernels.items()},
+            "issue": issue_roofline(_ncu_per_launch(f"{args.prec}_warp_inst_per_launch_256", args.n), avg, sms,
+                                    clk.summary()["sm_mhz"])}
     launches = sum(launches_per_step(args.warmup + i, s.reinit_every, s.reinit_iters) for i in range(args.steps))
     e2e = None
     if not args.no_e2e:

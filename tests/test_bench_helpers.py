@@ -1,0 +1,24 @@
+"""Host-side helpers of bench.py that need no GPU: the instruction-issue roofline and the
+source check of the committed ncu counters."""
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_issue_roofline_arithmetic():
+    r = bench.issue_roofline(1.2e9, 2.0, 152, 2000.0)
+    # 1.2e9 warp instructions in 2 ms = 600 G/s against 152 x 4 x 2.0 GHz = 1216 G/s
+    assert r["achieved"] == pytest.approx(600.0) and r["peak"] == pytest.approx(1216.0)
+    assert r["frac"] == pytest.approx(600.0 / 1216.0, abs=1e-4)
+    assert bench.issue_roofline(None, 2.0, 152, 2000.0) is None
+    assert bench.issue_roofline(1.2e9, 2.0, 152, None) is None
+
+
+def test_ncu_counters_are_withheld_for_other_sources(monkeypatch):
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "0000000000000000")
+    assert bench.ncu_traffic("mixed", 256) is None
+    assert bench._ncu_per_launch("mixed_warp_inst_per_launch_256", 256) is None
