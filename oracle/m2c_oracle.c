@@ -34,6 +34,7 @@
 
 #define EOS_SG 0 /* stiffened gas, prm = {gamma, p_c}; p_c = 0 is a perfect gas */
 #define EOS_MG 1 /* Mie-Grueneisen, prm = {rho0, c0, s, Gamma0, e0, eta_min} */
+#define EOS_NASG 2 /* Noble-Abel stiffened gas, prm = {gamma, p_c, b, e_c} (Sec. 3.3, Eq. NASG_EOS) */
 
 #define BC_TRANSMISSIVE 0
 #define BC_PERIODIC 1
@@ -121,12 +122,20 @@ static int mg_eta(const or_eos_t* q, double rho, double* eta) {
   return OR_OK;
 }
 
-/* p(rho, e): NASG with b = e_c = 0 (Sec. 3.3, Eq. NASG_EOS) or MG (App. B.3). */
+/* p(rho, e): NASG with b = e_c = 0 (Sec. 3.3, Eq. NASG_EOS), the full NASG
+ * p = (gamma - 1) rho (e - e_c)/(1 - rho b) - gamma p_c (defined for rho b < 1),
+ * or MG (App. B.3). */
 static int eos_p(const or_eos_t* q, double rho, double e, double* p) {
   if (!(rho > 0.0)) return OR_ENONPHYS;
   if (q->type == EOS_SG) {
     double g = q->prm[0], pc = q->prm[1];
     *p = (g - 1.0) * rho * e - g * pc;
+    return OR_OK;
+  }
+  if (q->type == EOS_NASG) {
+    double g = q->prm[0], pc = q->prm[1], b = q->prm[2], ec = q->prm[3];
+    if (!(1.0 - rho * b > 0.0)) return OR_ENONPHYS;
+    *p = (g - 1.0) * rho * (e - ec) / (1.0 - rho * b) - g * pc;
     return OR_OK;
   }
   double eta, pR, dpR, eR, deR;
@@ -145,6 +154,12 @@ static int eos_e(const or_eos_t* q, double rho, double p, double* e) {
     *e = (p + g * pc) / ((g - 1.0) * rho);
     return OR_OK;
   }
+  if (q->type == EOS_NASG) {
+    double g = q->prm[0], pc = q->prm[1], b = q->prm[2], ec = q->prm[3];
+    if (!(1.0 - rho * b > 0.0)) return OR_ENONPHYS;
+    *e = ec + (p + g * pc) * (1.0 - rho * b) / ((g - 1.0) * rho);
+    return OR_OK;
+  }
   double eta, pR, dpR, eR, deR;
   int st = mg_eta(q, rho, &eta);
   if (st) return st;
@@ -161,6 +176,11 @@ static int eos_c2(const or_eos_t* q, double rho, double p, double* c2) {
   if (q->type == EOS_SG) {
     double g = q->prm[0], pc = q->prm[1];
     *c2 = g * (p + pc) / rho;
+  } else if (q->type == EOS_NASG) {
+    /* dp/drho|_e = (p + gamma p_c)/(rho (1 - rho b)), dp/de|_rho = (gamma - 1) rho/(1 - rho b) */
+    double g = q->prm[0], pc = q->prm[1], b = q->prm[2];
+    if (!(1.0 - rho * b > 0.0)) return OR_ENONPHYS;
+    *c2 = g * (p + pc) / (rho * (1.0 - rho * b));
   } else {
     double eta, pR, dpR, eR, deR;
     int st = mg_eta(q, rho, &eta);
@@ -176,7 +196,7 @@ static int eos_c2(const or_eos_t* q, double rho, double p, double* c2) {
 /* Lowest admissible pressure on a side: SG needs p + p_c > 0; MG with a
  * finite tensile cutoff has p_min = K0 eta_min, else no bound. */
 static double eos_plow(const or_eos_t* q) {
-  if (q->type == EOS_SG) return -q->prm[1];
+  if (q->type == EOS_SG || q->type == EOS_NASG) return -q->prm[1];
   if (isfinite(q->prm[5])) return q->prm[0] * q->prm[1] * q->prm[1] * q->prm[5];
   return -INFINITY;
 }
@@ -330,8 +350,40 @@ static int wave_mg(const or_eos_t* q, const side_t* K, double p, double* f, doub
   return OR_OK;
 }
 
+/* NASG wave curves in P = p + p_c and the covolume-reduced specific volume
+ * w = 1/rho - b. Shock: the Hugoniot energy equation e - e_K = (p + p_K)(1/rho_K
+ * - 1/rho)/2 is linear in w and gives w = w_K (gm r + 1)/(r + gm), r = P/P_K,
+ * gm = (gamma - 1)/(gamma + 1), so f = (p - p_K) sqrt(A/(P + gm P_K)) with
+ * A = 2 w_K/(gamma + 1). Rarefaction: the isentrope P w^gamma = const gives
+ * rho c = sqrt(gamma P/w), and the integral of dp/(rho c) is
+ * f = 2 c_K (1 - b rho_K)/(gamma - 1) (r^((gamma-1)/(2 gamma)) - 1). With b = 0
+ * both are the stiffened-gas curves of wave_sg. */
+static int wave_nasg(const or_eos_t* q, const side_t* K, double p, double* f, double* df, double* rs) {
+  double g = q->prm[0], pc = q->prm[1], b = q->prm[2];
+  double P = p + pc, PK = K->p + pc;
+  double wK = 1.0 / K->rho - b;
+  if (!(P >= 0.0) || !(PK > 0.0) || !(wK > 0.0)) return OR_ENONPHYS;
+  double r = P / PK;
+  if (p > K->p) {
+    double gm = (g - 1.0) / (g + 1.0);
+    double A = 2.0 * wK / (g + 1.0);
+    double D = P + gm * PK;
+    double sq = sqrt(A / D);
+    *f = (p - K->p) * sq;
+    *df = sq * (1.0 - 0.5 * (p - K->p) / D);
+    *rs = 1.0 / (b + wK * (gm * r + 1.0) / (r + gm));
+  } else {
+    *f = 2.0 * K->c * (1.0 - b * K->rho) / (g - 1.0) * (pow(r, (g - 1.0) / (2.0 * g)) - 1.0);
+    double w = wK * pow(r, -1.0 / g);
+    *df = sqrt(w / (g * P));
+    *rs = 1.0 / (b + w);
+  }
+  return OR_OK;
+}
+
 static int wave(const or_eos_t* q, const side_t* K, double p, double* f, double* df, double* rs) {
   if (q->type == EOS_SG) return wave_sg(q, K, p, f, df, rs);
+  if (q->type == EOS_NASG) return wave_nasg(q, K, p, f, df, rs);
   return wave_mg(q, K, p, f, df, rs);
 }
 
@@ -1132,6 +1184,8 @@ static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   /* at least one axis with more than one cell: otherwise nothing moves and the time step is undefined */
   if (g->n[0] * g->n[1] * g->n[2] < 2) return OR_EINVAL;
   if (!(g->h > 0.0)) return OR_EINVAL;
+  for (int m = 0; m < 2; ++m)
+    if (g->eos[m].type != EOS_SG && g->eos[m].type != EOS_MG && g->eos[m].type != EOS_NASG) return OR_EINVAL;
   if (g->rk != 1 && g->rk != 2 && g->rk != 3) return OR_EINVAL;
   if (g->limiter != LIM_VA_MOD && g->limiter != LIM_MC) return OR_EINVAL;
   if (g->flux != FLUX_HLLC && g->flux != FLUX_LLF) return OR_EINVAL;

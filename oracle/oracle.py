@@ -23,6 +23,7 @@ LIB = os.path.join(HERE, "libm2c_oracle.so")
 
 EOS_SG = 0
 EOS_MG = 1
+EOS_NASG = 2  # Noble-Abel stiffened gas, prm = (gamma, p_c, b, e_c)
 BC_TRANSMISSIVE = 0
 BC_PERIODIC = 1
 LIM_VA_MOD, LIM_MC = 0, 1
