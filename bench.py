@@ -233,12 +233,18 @@ def peaks():
 
 
 def _kernel_source_hash():
+    """Identity of the bulk kernel's code: sha256 of its sources with comments and whitespace
+    removed (so that a comment edit keeps the counters taken on the same code)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("m2c_stage.cuh", "m2c_stage_fp32.cu", "m2c_stage_fp64.cu", "m2c_device.cuh", "m2c_physics.cuh",
               "m2c_kernels.cuh"):
-        with open(os.path.join(ROOT, "paper_2508_16387_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2508_16387_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(re.sub(r"\s+", "", text).encode())
     return h.hexdigest()[:16]
 
 

@@ -41,8 +41,10 @@ struct StageSmem {
 // shared memory each) or two 512-thread blocks of 16-row tiles.
 //
 // Every thread's share of the plane work (halo cell, face-state items, flux
-// items) and its shared-memory addresses are fixed for the whole launch and
-// computed once; only the plane index changes along the march.
+// items) and its shared-memory addresses are fixed for the whole launch; only
+// the plane index changes along the march. The halo slots are computed once,
+// the face-state and flux items are recomputed from the thread index where
+// they are used (cheaper than holding them in registers across the march).
 template <typename R, int TY>
 __global__ void __launch_bounds__(32 * TY, (sizeof(R) == 8 ? 1 : 1024 / (32 * TY)))
 k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, long long ntiles, int mode,

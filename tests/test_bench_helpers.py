@@ -22,3 +22,20 @@ def test_ncu_counters_are_withheld_for_other_sources(monkeypatch):
     monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "0000000000000000")
     assert bench.ncu_traffic("mixed", 256) is None
     assert bench._ncu_per_launch("mixed_warp_inst_per_launch_256", 256) is None
+
+
+def test_kernel_hash_ignores_comments_and_whitespace(tmp_path, monkeypatch):
+    """A comment or formatting edit keeps the identity of the kernel code; a code edit changes it."""
+    import shutil
+    src = os.path.join(bench.ROOT, "paper_2508_16387_gb300", "csrc")
+    dst = tmp_path / "paper_2508_16387_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench._kernel_source_hash()
+    f = dst / "m2c_stage.cuh"
+    text = f.read_text()
+    f.write_text("// a new comment\n" + text.replace("\n", "\n\n", 3) + "\n/* and another */\n")
+    assert bench._kernel_source_hash() == h0
+    f.write_text(text.replace("kReinitChunk", "kReinitChunk ", 1).replace("const int tid = threadIdx.x",
+                                                                         "const int tid = (int)threadIdx.x", 1))
+    assert bench._kernel_source_hash() != h0
