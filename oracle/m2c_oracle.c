@@ -35,6 +35,7 @@
 #define EOS_SG 0 /* stiffened gas, prm = {gamma, p_c}; p_c = 0 is a perfect gas */
 #define EOS_MG 1 /* Mie-Grueneisen, prm = {rho0, c0, s, Gamma0, e0, eta_min} */
 #define EOS_NASG 2 /* Noble-Abel stiffened gas, prm = {gamma, p_c, b, e_c} (Sec. 3.3, Eq. NASG_EOS) */
+#define EOS_JWL 3  /* Jones-Wilkins-Lee, prm = {omega, A1, A2, R1, R2, rho0} (App. B.2, Eq. JWL_EOS) */
 
 #define BC_TRANSMISSIVE 0
 #define BC_PERIODIC 1
@@ -122,6 +123,23 @@ static int mg_eta(const or_eos_t* q, double rho, double* eta) {
   return OR_OK;
 }
 
+/* JWL (App. B.2, Eq. JWL_EOS): p = omega rho e + f(rho) with
+ * f = sum_i A_i (1 - omega rho/(R_i rho0)) exp(-R_i rho0/rho). Reading R35: the
+ * first exponential, printed with a plus sign, has the minus sign of the
+ * second one and of the temperature law printed with it (with a plus sign the
+ * pressure would grow without bound as rho -> 0). f and df/drho. */
+static void jwl_f(const or_eos_t* q, double rho, double* f, double* df) {
+  double w = q->prm[0], rho0 = q->prm[5];
+  *f = 0.0;
+  *df = 0.0;
+  for (int i = 0; i < 2; ++i) {
+    double A = q->prm[1 + i], R = q->prm[3 + i];
+    double x = R * rho0 / rho, ex = exp(-x), a = 1.0 - w * rho / (R * rho0);
+    *f += A * a * ex;
+    *df += A * ex * (-w / (R * rho0) + a * x / rho);
+  }
+}
+
 /* p(rho, e): NASG with b = e_c = 0 (Sec. 3.3, Eq. NASG_EOS), the full NASG
  * p = (gamma - 1) rho (e - e_c)/(1 - rho b) - gamma p_c (defined for rho b < 1),
  * or MG (App. B.3). */
@@ -136,6 +154,12 @@ static int eos_p(const or_eos_t* q, double rho, double e, double* p) {
     double g = q->prm[0], pc = q->prm[1], b = q->prm[2], ec = q->prm[3];
     if (!(1.0 - rho * b > 0.0)) return OR_ENONPHYS;
     *p = (g - 1.0) * rho * (e - ec) / (1.0 - rho * b) - g * pc;
+    return OR_OK;
+  }
+  if (q->type == EOS_JWL) {
+    double f, df;
+    jwl_f(q, rho, &f, &df);
+    *p = q->prm[0] * rho * e + f;
     return OR_OK;
   }
   double eta, pR, dpR, eR, deR;
@@ -160,6 +184,12 @@ static int eos_e(const or_eos_t* q, double rho, double p, double* e) {
     *e = ec + (p + g * pc) * (1.0 - rho * b) / ((g - 1.0) * rho);
     return OR_OK;
   }
+  if (q->type == EOS_JWL) {
+    double f, df;
+    jwl_f(q, rho, &f, &df);
+    *e = (p - f) / (q->prm[0] * rho);
+    return OR_OK;
+  }
   double eta, pR, dpR, eR, deR;
   int st = mg_eta(q, rho, &eta);
   if (st) return st;
@@ -181,6 +211,11 @@ static int eos_c2(const or_eos_t* q, double rho, double p, double* c2) {
     double g = q->prm[0], pc = q->prm[1], b = q->prm[2];
     if (!(1.0 - rho * b > 0.0)) return OR_ENONPHYS;
     *c2 = g * (p + pc) / (rho * (1.0 - rho * b));
+  } else if (q->type == EOS_JWL) {
+    /* dp/drho|_e = omega e + f'(rho) with omega e = (p - f)/rho, dp/de|_rho = omega rho */
+    double f, df;
+    jwl_f(q, rho, &f, &df);
+    *c2 = ((1.0 + q->prm[0]) * p - f) / rho + df;
   } else {
     double eta, pR, dpR, eR, deR;
     int st = mg_eta(q, rho, &eta);
@@ -197,6 +232,7 @@ static int eos_c2(const or_eos_t* q, double rho, double p, double* c2) {
  * finite tensile cutoff has p_min = K0 eta_min, else no bound. */
 static double eos_plow(const or_eos_t* q) {
   if (q->type == EOS_SG || q->type == EOS_NASG) return -q->prm[1];
+  if (q->type == EOS_JWL) return 0.0; /* Reading R36 */
   if (isfinite(q->prm[5])) return q->prm[0] * q->prm[1] * q->prm[1] * q->prm[5];
   return -INFINITY;
 }
@@ -350,6 +386,120 @@ static int wave_mg(const or_eos_t* q, const side_t* K, double p, double* f, doub
   return OR_OK;
 }
 
+/* JWL Hugoniot through K at pressure p > p_K: the root of
+ * H(rho) = e(rho, p) - e_K - (p + p_K)(1/rho_K - 1/rho)/2 with rho > rho_K, by
+ * Newton safeguarded in a bracket [rho_K, rho_hi] (H(rho_K) > 0; rho_hi starts
+ * at the strong-shock compression rho_K (omega + 2)/omega of a gas with
+ * Grueneisen coefficient omega and doubles until H(rho_hi) < 0), the same
+ * tolerance and extra step as the MG root; d rho/dp by implicit
+ * differentiation. de/drho|_p = -(f'(rho) + omega e)/(omega rho). */
+static int jwl_hugoniot_rho(const or_eos_t* q, const side_t* K, double p, double* rho_out, double* drho_dp) {
+  double w = q->prm[0];
+  double lo = K->rho, hi = K->rho * (w + 2.0) / w;
+  int bracketed = 0;
+  for (int k = 0; k < 60 && !bracketed; ++k) {
+    double e;
+    int st = eos_e(q, hi, p, &e);
+    if (st) return st;
+    if (e - K->e - 0.5 * (p + K->p) * (1.0 / K->rho - 1.0 / hi) < 0.0) bracketed = 1;
+    else { lo = hi; hi = 2.0 * hi; }
+  }
+  if (!bracketed) return OR_ENOCONV;
+  double rho = K->rho + (p - K->p) / (K->c * K->c);
+  if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
+  int done = 0, extra = 0;
+  for (int it = 0; it < HUGONIOT_CAP; ++it) {
+    double e, f, df;
+    int st = eos_e(q, rho, p, &e);
+    if (st) return st;
+    jwl_f(q, rho, &f, &df);
+    double dedr = -(df + w * e) / (w * rho);
+    double H = e - K->e - 0.5 * (p + K->p) * (1.0 / K->rho - 1.0 / rho);
+    double dH = dedr - 0.5 * (p + K->p) / (rho * rho);
+    if (H > 0.0) lo = rho; else hi = rho;
+    double rn = rho - H / dH;
+    if (!(rn >= lo && rn <= hi)) rn = 0.5 * (lo + hi);
+    int conv = fabs(rn - rho) <= HUGONIOT_TOL * rn;
+    rho = rn;
+    if (extra) { done = 1; break; }
+    if (conv) extra = 1;
+  }
+  if (!done) return OR_ENOCONV;
+  double e, f, df;
+  int st = eos_e(q, rho, p, &e);
+  if (st) return st;
+  jwl_f(q, rho, &f, &df);
+  double Hp = 1.0 / (w * rho) - 0.5 * (1.0 / K->rho - 1.0 / rho);
+  double Hr = -(df + w * e) / (w * rho) - 0.5 * (p + K->p) / (rho * rho);
+  *rho_out = rho;
+  *drho_dp = -Hp / Hr;
+  return OR_OK;
+}
+
+/* JWL wave curve. Shock: f = sqrt((p - p_K)(1/rho_K - 1/rho_H(p))). Rarefaction
+ * (Reading R36): the isentrope d rho/dp = 1/c^2, df/dp = 1/(rho c) integrated by
+ * classical RK4 in s = ln p (d rho/ds = p/c^2, df/ds = p/(rho c)) on equal
+ * substeps, 256 per unit of |ln(p/p_K)| and at least 8 (relative error about
+ * 1e-12 over five decades), since detonation products expand over decades of
+ * pressure; it needs p > 0. */
+static int wave_jwl(const or_eos_t* q, const side_t* K, double p, double* f, double* df, double* rs) {
+  if (p == K->p) {
+    *f = 0.0;
+    *df = 1.0 / (K->rho * K->c);
+    *rs = K->rho;
+    return OR_OK;
+  }
+  if (p > K->p) {
+    double rho, drdp;
+    int st = jwl_hugoniot_rho(q, K, p, &rho, &drdp);
+    if (st) return st;
+    double dv = 1.0 / K->rho - 1.0 / rho;
+    double fv = sqrt((p - K->p) * dv);
+    *f = fv;
+    *df = (dv + (p - K->p) * drdp / (rho * rho)) / (2.0 * fv);
+    *rs = rho;
+    return OR_OK;
+  }
+  if (!(p > 0.0) || !(K->p > 0.0)) return OR_ENONPHYS;
+  double span = log(p / K->p);
+  double nd = ceil(256.0 * fabs(span));
+  int ns = nd < 8.0 ? 8 : (int)nd;
+  double hs = span / ns, s0 = log(K->p);
+  double rho = K->rho, fv = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    double si = s0 + i * hs;
+    double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f, pp, c2;
+    int st;
+    pp = exp(si);
+    st = eos_c2(q, rho, pp, &c2);
+    if (st) return st;
+    k1r = pp / c2; k1f = pp / (rho * sqrt(c2));
+    pp = exp(si + 0.5 * hs);
+    double r2 = rho + 0.5 * hs * k1r;
+    st = eos_c2(q, r2, pp, &c2);
+    if (st) return st;
+    k2r = pp / c2; k2f = pp / (r2 * sqrt(c2));
+    double r3 = rho + 0.5 * hs * k2r;
+    st = eos_c2(q, r3, pp, &c2);
+    if (st) return st;
+    k3r = pp / c2; k3f = pp / (r3 * sqrt(c2));
+    pp = exp(si + hs);
+    double r4 = rho + hs * k3r;
+    st = eos_c2(q, r4, pp, &c2);
+    if (st) return st;
+    k4r = pp / c2; k4f = pp / (r4 * sqrt(c2));
+    rho = rho + hs / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
+    fv = fv + hs / 6.0 * (k1f + 2.0 * k2f + 2.0 * k3f + k4f);
+  }
+  double c2;
+  int st = eos_c2(q, rho, p, &c2);
+  if (st) return st;
+  *f = fv;
+  *df = 1.0 / (rho * sqrt(c2));
+  *rs = rho;
+  return OR_OK;
+}
+
 /* NASG wave curves in P = p + p_c and the covolume-reduced specific volume
  * w = 1/rho - b. Shock: the Hugoniot energy equation e - e_K = (p + p_K)(1/rho_K
  * - 1/rho)/2 is linear in w and gives w = w_K (gm r + 1)/(r + gm), r = P/P_K,
@@ -384,6 +534,7 @@ static int wave_nasg(const or_eos_t* q, const side_t* K, double p, double* f, do
 static int wave(const or_eos_t* q, const side_t* K, double p, double* f, double* df, double* rs) {
   if (q->type == EOS_SG) return wave_sg(q, K, p, f, df, rs);
   if (q->type == EOS_NASG) return wave_nasg(q, K, p, f, df, rs);
+  if (q->type == EOS_JWL) return wave_jwl(q, K, p, f, df, rs);
   return wave_mg(q, K, p, f, df, rs);
 }
 
@@ -424,7 +575,8 @@ static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, c
   if (st) return st;
   double plow = fmax(eos_plow(qL), eos_plow(qR));
   double F, dF;
-  if (isfinite(plow) && R.u - L.u >= 0.0) {
+  /* Reading R36: no vacuum test with a JWL side (its rarefaction needs p > 0) */
+  if (isfinite(plow) && R.u - L.u >= 0.0 && qL->type != EOS_JWL && qR->type != EOS_JWL) {
     st = riemann_F(qL, &L, qR, &R, plow, &F, &dF);
     if (st) return st;
     if (F >= 0.0) return OR_EVACUUM;
@@ -1185,7 +1337,9 @@ static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   if (g->n[0] * g->n[1] * g->n[2] < 2) return OR_EINVAL;
   if (!(g->h > 0.0)) return OR_EINVAL;
   for (int m = 0; m < 2; ++m)
-    if (g->eos[m].type != EOS_SG && g->eos[m].type != EOS_MG && g->eos[m].type != EOS_NASG) return OR_EINVAL;
+    if (g->eos[m].type != EOS_SG && g->eos[m].type != EOS_MG && g->eos[m].type != EOS_NASG &&
+        g->eos[m].type != EOS_JWL)
+      return OR_EINVAL;
   if (g->rk != 1 && g->rk != 2 && g->rk != 3) return OR_EINVAL;
   if (g->limiter != LIM_VA_MOD && g->limiter != LIM_MC) return OR_EINVAL;
   if (g->flux != FLUX_HLLC && g->flux != FLUX_LLF) return OR_EINVAL;

@@ -24,6 +24,7 @@ LIB = os.path.join(HERE, "libm2c_oracle.so")
 EOS_SG = 0
 EOS_MG = 1
 EOS_NASG = 2  # Noble-Abel stiffened gas, prm = (gamma, p_c, b, e_c)
+EOS_JWL = 3  # Jones-Wilkins-Lee, prm = (omega, A1, A2, R1, R2, rho0)
 BC_TRANSMISSIVE = 0
 BC_PERIODIC = 1
 LIM_VA_MOD, LIM_MC = 0, 1

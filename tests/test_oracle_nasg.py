@@ -72,10 +72,12 @@ def _rh(eos, ahead, behind):
 @pytest.mark.parametrize("eos,w,p", [(LIQ, (1000.0, 10.0, 1e5), 3e9), (GAS, (1.2, 0.0, 1e5), 2e6)])
 def test_nasg_shock_satisfies_the_jump_conditions(eos, w, p):
     f, df, rs = O.wave_curve(eos, w, p)
-    # a right-facing shock moving into w: the state behind moves at u - f... use the left-facing
-    # form of the wave curve: behind = (rs, u - f, p) for the left wave, checked in its own frame
+    # the left-facing wave through w: the state behind it is (rs, u - f, p)
     for res in _rh(eos, w, (rs, w[1] - f, p)):
         assert res < 1e-11
+    hp = 1e-5 * (p - w[2])   # f'(p) along the Hugoniot against a central difference of f
+    fd = (O.wave_curve(eos, w, p + hp)[0] - O.wave_curve(eos, w, p - hp)[0]) / (2 * hp)
+    assert df == pytest.approx(fd, rel=1e-7)
 
 
 @pytest.mark.parametrize("eos,w,p", [(LIQ, (1000.0, 10.0, 3e8), 1e5), (GAS, (1.2, 0.0, 1e5), 2e3)])
@@ -140,7 +142,6 @@ def test_nasg_two_material_periodic_run_conserves_and_keeps_uniform_flow():
     """A periodic 3D run with a NASG liquid and an SG gas: mass, momentum and energy are conserved
     to rounding in a single-material box and a uniform flow stays uniform bit for bit."""
     n = (10, 8, 6)
-    x, y, z = np.meshgrid(*(np.arange(k) for k in n), indexing="ij")
     shape = (n[2], n[1], n[0])
     g = O.Grid(n=n, h=0.1, eos=(LIQ, AIR), bc=(1,) * 6)
     P = np.zeros((5,) + shape)
