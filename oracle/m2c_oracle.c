@@ -39,6 +39,11 @@
 
 #define BC_TRANSMISSIVE 0
 #define BC_PERIODIC 1
+#define BC_SYMMETRY 2 /* mirror: ghost cells reflect the interior, the normal velocity negated */
+
+#define GEOM_CARTESIAN 0
+#define GEOM_CYLINDRICAL 1 /* x is the radius r, z the axis (Sec. 3.4, Eq. Euler_cylindrical) */
+#define GEOM_SPHERICAL 2   /* x is the radius r (Sec. 3.4, Eq. euler1d_spherical) */
 
 /* Riemann solver controls, Reading R6 */
 #define NEWTON_TOL 1e-12
@@ -69,6 +74,8 @@ typedef struct {
   int flux;        /* FLUX_HLLC (default) or FLUX_LLF */
   double mc_alpha; /* alpha of the MC limiter (1.2 by default) */
   double dt_fixed; /* > 0: constant time step instead of the CFL rule */
+  int geom;        /* GEOM_CARTESIAN (default), GEOM_CYLINDRICAL or GEOM_SPHERICAL */
+  double x0;       /* lower x coordinate: the radius of the first cell's lower face */
 } or_grid_t;
 
 #define LIM_VA_MOD 0 /* modified van Albada, App. D */
@@ -771,10 +778,12 @@ static double limited_slope(const or_grid_t* g, double a, double b) {
 /* ------------------------------------------------------------------ */
 
 /* Boundary conditions applied at every load (Reading R20/R26): a transmissive
- * side clamps the index (zero gradient), a periodic side wraps it. */
+ * side clamps the index (zero gradient), a periodic side wraps it, a symmetry
+ * side mirrors it (the velocity component normal to the side is negated by
+ * prim_at). */
 static inline int map_index(int i, int n, int bclo, int bchi) {
-  if (i < 0) return bclo == BC_PERIODIC ? ((i % n) + n) % n : 0;
-  if (i >= n) return bchi == BC_PERIODIC ? i % n : n - 1;
+  if (i < 0) return bclo == BC_PERIODIC ? ((i % n) + n) % n : (bclo == BC_SYMMETRY ? -1 - i : 0);
+  if (i >= n) return bchi == BC_PERIODIC ? i % n : (bchi == BC_SYMMETRY ? 2 * n - 1 - i : n - 1);
   return i;
 }
 
@@ -788,6 +797,18 @@ static inline long cell_index(const or_grid_t* g, int i, int j, int k) {
 static inline long ncells(const or_grid_t* g) { return (long)g->n[0] * g->n[1] * g->n[2]; }
 
 static const int DIRV[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+/* Primitive state at the unmapped position (i,j,k): the mapped cell's, with the
+ * velocity component normal to every symmetry side it was mirrored across
+ * negated. */
+static void prim_at(const or_grid_t* g, const double* P, int i, int j, int k, double out[5]) {
+  long N = ncells(g), c = cell_index(g, i, j, k);
+  for (int v = 0; v < 5; ++v) out[v] = P[v * N + c];
+  const int x[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a)
+    if ((x[a] < 0 && g->bc[2 * a] == BC_SYMMETRY) || (x[a] >= g->n[a] && g->bc[2 * a + 1] == BC_SYMMETRY))
+      out[1 + a] = -out[1 + a];
+}
 
 static void record_error(int st, long cell, int* err, long* err_cell) {
 #ifdef _OPENMP
@@ -865,20 +886,23 @@ static int all_prims(const or_grid_t* g, const double* W, const unsigned char* i
  * is not admissible (rho <= 0 or c^2 <= 0). */
 static void face_states(const or_grid_t* g, const double* P, const unsigned char* id, int i, int j, int k, int d,
                         double Qm[5], double Qp[5]) {
-  long N = ncells(g);
   long c = cell_index(g, i, j, k);
   long cm = cell_index(g, i - DIRV[d][0], j - DIRV[d][1], k - DIRV[d][2]);
   long cp = cell_index(g, i + DIRV[d][0], j + DIRV[d][1], k + DIRV[d][2]);
   int m = id[c];
-  for (int v = 0; v < 5; ++v) Qm[v] = Qp[v] = P[v * N + c];
+  double Q[5], Qlo[5], Qhi[5];
+  prim_at(g, P, i, j, k, Q);
+  for (int v = 0; v < 5; ++v) Qm[v] = Qp[v] = Q[v];
   if (id[cm] != m || id[cp] != m) return;
+  prim_at(g, P, i - DIRV[d][0], j - DIRV[d][1], k - DIRV[d][2], Qlo);
+  prim_at(g, P, i + DIRV[d][0], j + DIRV[d][1], k + DIRV[d][2], Qhi);
   double tm[5], tp[5];
   for (int v = 0; v < 5; ++v) {
-    double a = P[v * N + c] - P[v * N + cm];
-    double b = P[v * N + cp] - P[v * N + c];
+    double a = Q[v] - Qlo[v];
+    double b = Qhi[v] - Q[v];
     double s = limited_slope(g, a, b);
-    tm[v] = P[v * N + c] - 0.5 * s;
-    tp[v] = P[v * N + c] + 0.5 * s;
+    tm[v] = Q[v] - 0.5 * s;
+    tp[v] = Q[v] + 0.5 * s;
   }
   if (!state_valid(&g->eos[m], tm) || !state_valid(&g->eos[m], tp)) return;
   for (int v = 0; v < 5; ++v) { Qm[v] = tm[v]; Qp[v] = tp[v]; }
@@ -974,6 +998,15 @@ static int stage_residual(const or_grid_t* g, const double* W, const double* phi
         if (st) {
           record_error(st, c, &err, &ec);
           continue;
+        }
+        if (g->geom != GEOM_CARTESIAN) {
+          /* Sec. 3.4: S = -(alpha/r) u_r (rho, rho u, rho v, rho w, rho E + p), alpha = 1
+           * (cylindrical) or 2 (spherical); Reading R37: evaluated at the cell centre
+           * r = x0 + (i + 1/2) h from the stage state, added after the flux sum */
+          double r = g->x0 + (i + 0.5) * g->h;
+          double a = (g->geom == GEOM_SPHERICAL ? 2.0 : 1.0) / r * P[1 * N + c];
+          for (int v = 0; v < 4; ++v) acc[v] = acc[v] - a * W[v * N + c];
+          acc[4] = acc[4] - a * (W[4 * N + c] + P[4 * N + c]);
         }
         for (int v = 0; v < 5; ++v) R[v * N + c] = acc[v];
         double u = P[1 * N + c], v = P[2 * N + c], w = P[3 * N + c];
@@ -1125,7 +1158,9 @@ static int phase_fix(const or_grid_t* g, double* W, double* phi, const unsigned 
           for (int sgn = -1; sgn <= 1; sgn += 2) {
             long nb = cell_index(g, i + sgn * DIRV[d][0], j + sgn * DIRV[d][1], k + sgn * DIRV[d][2]);
             if (id_old[nb] == m && id_new[nb] == m) {
-              for (int v = 0; v < 5; ++v) sum[v] = sum[v] + P[v * N + nb];
+              double q[5];
+              prim_at(g, P, i + sgn * DIRV[d][0], j + sgn * DIRV[d][1], k + sgn * DIRV[d][2], q);
+              for (int v = 0; v < 5; ++v) sum[v] = sum[v] + q[v];
               cnt += 1;
             }
           }
@@ -1136,7 +1171,9 @@ static int phase_fix(const or_grid_t* g, double* W, double* phi, const unsigned 
                 if (!di && !dj && !dk) continue;
                 long nb = cell_index(g, i + di, j + dj, k + dk);
                 if (id_old[nb] == m && id_new[nb] == m) {
-                  for (int v = 0; v < 5; ++v) sum[v] = sum[v] + P[v * N + nb];
+                  double q[5];
+                  prim_at(g, P, i + di, j + dj, k + dk, q);
+                  for (int v = 0; v < 5; ++v) sum[v] = sum[v] + q[v];
                   cnt += 1;
                 }
               }
@@ -1310,8 +1347,8 @@ static void mk_eos(or_eos_t* q, int type, const double* prm) {
 }
 
 /* ip = {nx, ny, nz, bc[6], reinit_every, reinit_iters, eos_type0, eos_type1, nthreads,
- *       rk, limiter, flux}
- * dp = {h, cfl, eos_prm0[6], eos_prm1[6], mc_alpha, dt_fixed} */
+ *       rk, limiter, flux, geom}
+ * dp = {h, cfl, eos_prm0[6], eos_prm1[6], mc_alpha, dt_fixed, x0} */
 static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   for (int a = 0; a < 3; ++a) g->n[a] = ip[a];
   for (int s = 0; s < 6; ++s) g->bc[s] = ip[3 + s];
@@ -1326,13 +1363,23 @@ static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   g->flux = ip[16];
   g->mc_alpha = dp[14];
   g->dt_fixed = dp[15];
+  g->geom = ip[17];
+  g->x0 = dp[16];
 #ifdef _OPENMP
   if (ip[13] > 0) omp_set_num_threads(ip[13]);
 #endif
   for (int a = 0; a < 3; ++a) {
     if (g->n[a] < 1) return OR_EINVAL;
     if ((g->bc[2 * a] == BC_PERIODIC) != (g->bc[2 * a + 1] == BC_PERIODIC)) return OR_EINVAL;
+    for (int sd = 0; sd < 2; ++sd) {
+      int b = g->bc[2 * a + sd];
+      if (b != BC_TRANSMISSIVE && b != BC_PERIODIC && b != BC_SYMMETRY) return OR_EINVAL;
+      if (b == BC_SYMMETRY && g->n[a] < 2) return OR_EINVAL; /* a two-cell mirror needs two cells */
+    }
   }
+  if (g->geom != GEOM_CARTESIAN && g->geom != GEOM_CYLINDRICAL && g->geom != GEOM_SPHERICAL) return OR_EINVAL;
+  if (g->geom != GEOM_CARTESIAN && (!(g->x0 >= 0.0) || g->n[1] != 1)) return OR_EINVAL;
+  if (g->geom == GEOM_SPHERICAL && g->n[2] != 1) return OR_EINVAL;
   /* at least one axis with more than one cell: otherwise nothing moves and the time step is undefined */
   if (g->n[0] * g->n[1] * g->n[2] < 2) return OR_EINVAL;
   if (!(g->h > 0.0)) return OR_EINVAL;

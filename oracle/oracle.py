@@ -27,6 +27,8 @@ EOS_NASG = 2  # Noble-Abel stiffened gas, prm = (gamma, p_c, b, e_c)
 EOS_JWL = 3  # Jones-Wilkins-Lee, prm = (omega, A1, A2, R1, R2, rho0)
 BC_TRANSMISSIVE = 0
 BC_PERIODIC = 1
+BC_SYMMETRY = 2  # mirror side: the normal velocity is negated in the ghost cells
+GEOM_CARTESIAN, GEOM_CYLINDRICAL, GEOM_SPHERICAL = 0, 1, 2  # x is the radius in the last two
 LIM_VA_MOD, LIM_MC = 0, 1
 FLUX_HLLC, FLUX_LLF = 0, 1
 
@@ -129,13 +131,16 @@ class Grid:
     flux: int = 0  # FLUX_HLLC or FLUX_LLF (App. C)
     mc_alpha: float = 1.2  # alpha of the MC limiter
     dt_fixed: float = 0.0  # > 0: constant time step instead of the CFL rule (Sec. 4.3)
+    geom: int = 0  # GEOM_CARTESIAN, GEOM_CYLINDRICAL (x = r, z axial; ny = 1) or GEOM_SPHERICAL (x = r; 1D)
+    x0: float = 0.0  # lower x coordinate (the radius of the first cell's lower face)
 
     def packed(self):
         ip = np.array(list(self.n) + list(self.bc) + [self.reinit_every, self.reinit_iters,
-                      self.eos[0].type, self.eos[1].type, self.threads, self.rk, self.limiter, self.flux],
+                      self.eos[0].type, self.eos[1].type, self.threads, self.rk, self.limiter, self.flux,
+                      self.geom],
                       dtype=np.int32)
         dp = np.concatenate([[self.h, self.cfl], self.eos[0].arr(), self.eos[1].arr(),
-                             [self.mc_alpha, self.dt_fixed]]).astype(np.float64)
+                             [self.mc_alpha, self.dt_fixed, self.x0]]).astype(np.float64)
         return ip, dp
 
     @property
@@ -272,7 +277,7 @@ def run(g: Grid, W: np.ndarray, phi: np.ndarray, nsteps: int, step0: int = 0, t0
     ip, dp = g.packed()
     W = _f64(W).copy()
     phi = _f64(phi).copy()
-    t = np.array([t0])
+    t = np.array([float(t0)])
     st = np.zeros(4, dtype=np.int64)
     dts = np.zeros(max(nsteps, 1))
     _check(lib().or_run(_ptr(ip), _ptr(dp), _ptr(W), _ptr(phi), step0, nsteps, _ptr(t), _ptr(st), _ptr(dts)), "run")

@@ -1,0 +1,138 @@
+"""Pins of the oracle's spherical and cylindrical symmetry forms (Sec. 3.4, Eqs.
+euler1d_spherical and Euler_cylindrical, Reading R37) and of its symmetry (mirror) boundary:
+a half domain with a mirror side equals the mirror-symmetric full domain; the 1D spherical and
+2D cylindrical forms converge to the 3D Cartesian solution of a spherical shock tube (computed
+by the plain 3D scheme on an octant with mirror sides), while the planar 1D form does not. CPU
+only."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+AIR = O.EOS(O.EOS_SG, (1.4, 0.0))
+WATER = O.EOS(O.EOS_SG, (6.12, 3.43e8))
+
+
+def _advance(g, W, phi, T):
+    """Whole CFL steps until t >= T (the last one overshoots by less than one step)."""
+    t, n = 0.0, 0
+    while t < T:
+        r = O.run(g, W, phi, 1, step0=n, t0=t)
+        W, phi, t, n = r.W, r.phi, r.t, n + 1
+    return W, phi, t
+
+
+def _sod(r):
+    """Spherical shock tube: (rho, p) = (1, 10) for r < 0.2, (0.125, 1) outside, at rest."""
+    P = np.zeros((5,) + r.shape)
+    P[0] = np.where(r < 0.2, 1.0, 0.125)
+    P[4] = np.where(r < 0.2, 10.0, 1.0)
+    return P
+
+
+T_END = 0.06
+
+
+def _radial_1d(nr, geom):
+    h = 0.5 / nr
+    g = O.Grid(n=(nr, 1, 1), h=h, eos=(AIR, AIR), bc=(O.BC_SYMMETRY, 0, 0, 0, 0, 0), geom=geom,
+               reinit_every=10 ** 9)
+    r = (np.arange(nr) + 0.5) * h
+    phi = np.ones((1, 1, nr))
+    W, phi, _ = _advance(g, O.prims_to_cons(g, _sod(r)[:, None, None, :], phi), phi, T_END)
+    return r, O.cons_to_prims(g, W, phi)[0, 0, 0]
+
+
+@pytest.fixture(scope="module")
+def spherical_reference():
+    return _radial_1d(400, O.GEOM_SPHERICAL)
+
+
+def _octant_3d(m):
+    h = 0.5 / m
+    S = O.BC_SYMMETRY
+    g = O.Grid(n=(m, m, m), h=h, eos=(AIR, AIR), bc=(S, 0, S, 0, S, 0), reinit_every=10 ** 9)
+    c = (np.arange(m) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(x * x + y * y + z * z)
+    phi = np.ones(r.shape)
+    W, phi, _ = _advance(g, O.prims_to_cons(g, _sod(r), phi), phi, T_END)
+    return r, O.cons_to_prims(g, W, phi)[0]
+
+
+def test_spherical_form_converges_to_the_3d_solution(spherical_reference):
+    """The 3D Cartesian octant (no source term; the sphere's symmetry from three mirror sides)
+    approaches the fine 1D spherical solution as it is refined, and stays far from the planar 1D
+    solution (the same 1D grid without the source term)."""
+    r1, rho1 = spherical_reference
+    rp, rhop = _radial_1d(400, O.GEOM_CARTESIAN)
+    errs, errs_planar = [], []
+    for m in (16, 24, 32):
+        r3, rho3 = _octant_3d(m)
+        mask = r3 < 0.45
+        errs.append(np.abs(rho3 - np.interp(r3, r1, rho1))[mask].mean())
+        errs_planar.append(np.abs(rho3 - np.interp(r3, rp, rhop))[mask].mean())
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 0.01, errs
+    assert min(errs_planar) > 4 * errs[2], (errs, errs_planar)
+
+
+def test_cylindrical_form_converges_to_the_spherical_one(spherical_reference):
+    """The same sphere on the (r, z) half plane of the cylindrical form (mirror sides at r = 0
+    and z = 0) approaches the 1D spherical solution along r_s = sqrt(r^2 + z^2)."""
+    r1, rho1 = spherical_reference
+    errs = []
+    for m in (16, 32, 64):
+        h = 0.5 / m
+        S = O.BC_SYMMETRY
+        g = O.Grid(n=(m, 1, m), h=h, eos=(AIR, AIR), bc=(S, 0, 0, 0, S, 0), geom=O.GEOM_CYLINDRICAL,
+                   reinit_every=10 ** 9)
+        c = (np.arange(m) + 0.5) * h
+        z, x = np.meshgrid(c, c, indexing="ij")
+        rs = np.sqrt(x * x + z * z)[:, None, :]
+        phi = np.ones(rs.shape)
+        W, phi, _ = _advance(g, O.prims_to_cons(g, _sod(rs), phi), phi, T_END)
+        rho = O.cons_to_prims(g, W, phi)[0]
+        mask = rs < 0.45
+        errs.append(np.abs(rho - np.interp(rs, r1, rho1))[mask].mean())
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 0.006, errs
+
+
+def test_spherical_rest_state_stays_at_rest():
+    """At rest the source vanishes and a uniform pressure exerts no net force."""
+    g = O.Grid(n=(32, 1, 1), h=0.01, eos=(AIR, AIR), bc=(O.BC_SYMMETRY, 0, 0, 0, 0, 0),
+               geom=O.GEOM_SPHERICAL, x0=0.0)
+    P = np.zeros((5, 1, 1, 32))
+    P[0] = 1.3
+    P[4] = 2e5
+    phi = np.ones((1, 1, 32))
+    W = O.prims_to_cons(g, P, phi)
+    assert np.array_equal(O.run(g, W, phi, 5).W, W)
+
+
+def test_mirror_side_equals_the_symmetric_full_domain():
+    """A water/air problem symmetric about the plane x = 1/2 (an air bubble centred on it, a
+    pressure step along y): the half domain x > 1/2 with a mirror side at x = 1/2 reproduces the
+    full domain's right half, FIVER faces on the mirror plane included."""
+    n = 16
+    h = 1.0 / n
+    c = (np.arange(n) + 0.5) * h
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    phi = np.sqrt((x - 0.5) ** 2 + (y - 0.45) ** 2 + (z - 0.5) ** 2) - 0.22
+    P = np.zeros((5,) + phi.shape)
+    P[0] = np.where(phi < 0, 1.2, 1000.0)
+    P[2] = np.where(y < 0.25, 40.0, 0.0)
+    P[4] = np.where(y < 0.25, 5e8, 1e5)
+    full = O.Grid(n=(n, n, n), h=h, eos=(WATER, AIR), bc=(0,) * 6, reinit_every=3, reinit_iters=2)
+    half = O.Grid(n=(n // 2, n, n), h=h, eos=(WATER, AIR), bc=(O.BC_SYMMETRY, 0, 0, 0, 0, 0),
+                  reinit_every=3, reinit_iters=2)
+    rf = O.run(full, O.prims_to_cons(full, P, phi), phi, 8)
+    Ph, phih = P[..., n // 2:].copy(), phi[..., n // 2:].copy()
+    rh = O.run(half, O.prims_to_cons(half, Ph, phih), phih, 8)
+    assert rf.stats["interface_faces"] > 0
+    assert rh.t == pytest.approx(rf.t, rel=1e-13)
+    for v in range(5):
+        a, b = rh.W[v], rf.W[v][..., n // 2:]
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(rf.W[v]).max(), v
+    assert np.array_equal(rh.phi < 0, rf.phi[..., n // 2:] < 0)
