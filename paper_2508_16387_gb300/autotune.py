@@ -1,6 +1,6 @@
-"""Autotuner of the bulk stage kernel's launch: tile shape (32 x 4 or 32 x 8
-columns, z-length of a tile), tile schedule (fixed stride or atomic counter)
-and persistent grid size, picked by timing candidates with CUDA events on the
+"""Autotuner of the bulk stage kernel's launch: tile shape (32 x 4, 32 x 8 or,
+on the mixed path, 32 x 16 columns; z-length of a tile), tile schedule (fixed
+stride or atomic counter) and persistent grid size, picked by timing candidates with CUDA events on the
 actual grids. The state is saved before and restored after every trial, so
 tuning leaves the simulation where it was; results never depend on the choice
 (every cell is computed by the same arithmetic under every tiling).
