@@ -134,9 +134,13 @@ def make_grid(M, s, precision, stream=None):
 
 
 def launches_per_step(step_index, reinit_every, reinit_iters):
+    """Kernels m2c_step launches for step `step_index`: stage kernel, FIVER and finish for each of
+    the two stages, phase update and end of step; on a reinitialisation step also one launch per
+    iteration and the launch that copies the last iterate back (it exits at once unless there is
+    a single iteration)."""
     n = 8
     if reinit_every > 0 and (step_index + 1) % reinit_every == 0 and reinit_iters > 0:
-        n += reinit_iters + (1 if reinit_iters == 1 else 0)
+        n += reinit_iters + 1
     return n
 
 

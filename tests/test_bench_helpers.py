@@ -39,3 +39,16 @@ def test_kernel_hash_ignores_comments_and_whitespace(tmp_path, monkeypatch):
     f.write_text(text.replace("kReinitChunk", "kReinitChunk ", 1).replace("const int tid = threadIdx.x",
                                                                          "const int tid = (int)threadIdx.x", 1))
     assert bench._kernel_source_hash() != h0
+
+
+def test_launch_count_matches_the_launch_list():
+    """The 256^3 launch list (ncu, mixed part of `bench.py --steps 10 --warmup 3 --no-cpu --no-e2e
+    --l1-steps 0`) holds 72 stage, 72 FIVER, 72 finish, 36 phase-update, 36 end-of-step, 20
+    reinitialisation and 4 copy launches = 312 for the step indices that run executes: warm-up
+    0-2, the profiled pass 3-12, the timed steps 3-12 again from the restored state, then the
+    FP32-start line's warm-up 13-15, profiled pass 16-20 and timed steps 16-20."""
+    idx = list(range(0, 13)) + list(range(3, 13)) + list(range(13, 21)) + list(range(16, 21))
+    assert len(idx) == 36
+    assert sum(bench.launches_per_step(i, 10, 5) for i in idx) == 72 * 3 + 36 * 2 + 20 + 4
+    assert sum(bench.launches_per_step(i, 10, 5) for i in range(100)) == 860
+    assert bench.launches_per_step(9, 0, 5) == 8 and bench.launches_per_step(9, 10, 0) == 8
