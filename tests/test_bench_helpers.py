@@ -52,3 +52,4 @@ def test_launch_count_matches_the_launch_list():
     assert sum(bench.launches_per_step(i, 10, 5) for i in idx) == 72 * 3 + 36 * 2 + 20 + 4
     assert sum(bench.launches_per_step(i, 10, 5) for i in range(100)) == 860
     assert bench.launches_per_step(9, 0, 5) == 8 and bench.launches_per_step(9, 10, 0) == 8
+
