@@ -31,7 +31,8 @@
  * the device (non-physical state, Riemann non-convergence, list overflow) are
  * latched in the workspace and returned by m2c_sync together with the first
  * offending cell. m2c_last_error() gives a text for the last error of a
- * context. Functions are not thread-safe on one context.
+ * context (NULL: of the last failed call without a context on this thread).
+ * Functions are not thread-safe on one context.
  */
 #ifndef M2C_H
 #define M2C_H
@@ -261,8 +262,10 @@ m2c_status m2c_profile_read_kernels(m2c_ctx* ctx, double ms[6], long launches[6]
 /* Releases a context (the borrowed memory stays with the caller). */
 void m2c_destroy(m2c_ctx* ctx);
 
-/* Text of the last error of a context; with NULL, of the last failed
- * context-free call on this thread (m2c_residual_noalloc). */
+/* Text of the last error of a context; with NULL, of the last failed call on
+ * this thread that has no context (m2c_init_grid before a context exists,
+ * m2c_solve_riemann, m2c_solve_riemann_mixed, m2c_shock_state,
+ * m2c_residual_noalloc). */
 const char* m2c_last_error(const m2c_ctx* ctx);
 const char* m2c_status_string(int status);
 
