@@ -12,6 +12,13 @@
  * design notes. OpenMP is used only over cells whose results are independent
  * of each other, so the result does not depend on the thread count.
  *
+ * Beyond the configuration the GPU solver runs (TVD RK2, modified van Albada,
+ * HLLC, stiffened gas / Mie-Grueneisen, Cartesian), a grid selects the paper's
+ * other choices: TVD RK3 or forward Euler and a constant time step (Sec. 4.3),
+ * the MC limiter (App. D), the local Lax-Friedrichs flux (App. C.1), the NASG
+ * and JWL equations of state (Sec. 3.3, App. B.2), the spherical and
+ * cylindrical forms (Sec. 3.4) and mirror boundaries.
+ *
  * Conventions: SI units. State per cell W = (rho, rho u, rho v, rho w, rho E),
  * primitive P = (rho, u, v, w, p). Arrays are structure-of-arrays with x
  * fastest: field f of cell (i,j,k) is a[f*N + (k*ny + j)*nx + i].
