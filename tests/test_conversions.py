@@ -16,7 +16,8 @@ def test_integer_conversions_match_ieee(tmp_path):
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
     exe = str(tmp_path / "conv_check")
-    subprocess.run([nvcc, "-O2", "-std=c++17", "-x", "cu", "-I", os.path.join(ROOT, "include"),
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-x", "cu", "-Xcompiler", "-fopenmp", "-lgomp",
+                    "-I", os.path.join(ROOT, "include"),
                     "-I", os.path.join(ROOT, "paper_2508_16387_gb300", "csrc"),
                     os.path.join(HERE, "native", "conv_check.cu"), "-o", exe], check=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
