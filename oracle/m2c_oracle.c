@@ -1575,6 +1575,24 @@ int or_run(const int* ip, const double* dp, double* W, double* phi, long step0, 
   return st;
 }
 
+/* The phase update alone (Sec. 2.3 step (6), Reading R17) on (W, phi) with the
+ * material ids id_old of the start of the step; the new ids are sign(phi).
+ * nflip: cells that changed material. */
+int or_phase_fix(const int* ip, const double* dp, double* W, double* phi, const unsigned char* id_old, long* nflip) {
+  or_grid_t g;
+  int st = mk_grid(&g, ip, dp);
+  if (st) return st;
+  long N = ncells(&g);
+  unsigned char* id_new = malloc(N);
+  double* P = malloc(sizeof(double) * 5 * N);
+  if (!id_new || !P) { free(id_new); free(P); return OR_ENOMEM; }
+  for (long c = 0; c < N; ++c) id_new[c] = phi[c] < 0.0;
+  long ec = -1;
+  st = phase_fix(&g, W, phi, id_old, id_new, P, nflip, &ec);
+  free(id_new); free(P);
+  return st;
+}
+
 int or_reinit(const int* ip, const double* dp, double* phi, int iters) {
   or_grid_t g;
   int st = mk_grid(&g, ip, dp);

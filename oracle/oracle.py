@@ -74,6 +74,7 @@ def lib():
         _lib.or_residual.argtypes = [p, p, p, p, p, p, p]
         _lib.or_run.argtypes = [p, p, p, p, L, i, p, p, p]
         _lib.or_reinit.argtypes = [p, p, p, i]
+        _lib.or_phase_fix.argtypes = [p, p, p, p, p, p]
         _lib.or_exact_sample_sg.argtypes = [p, p, p, p, i, p, p, p]
         _lib.or_num_threads.restype = i
     return _lib
@@ -294,6 +295,18 @@ def run_status(g: Grid, W: np.ndarray, phi: np.ndarray, nsteps: int, step0: int 
     st = np.zeros(4, dtype=np.int64)
     code = lib().or_run(_ptr(ip), _ptr(dp), _ptr(W), _ptr(phi), step0, nsteps, _ptr(t), _ptr(st), None)
     return code, int(st[3])
+
+
+def phase_fix(g: Grid, W: np.ndarray, phi: np.ndarray, id_old: np.ndarray):
+    """The phase update alone on copies of (W, phi), given the material ids at the start of
+    the step: returns (W, phi, number of cells that changed material)."""
+    ip, dp = g.packed()
+    W = _f64(W).copy()
+    phi = _f64(phi).copy()
+    ido = np.ascontiguousarray(id_old, dtype=np.uint8)
+    nf = np.zeros(1, dtype=np.int64)
+    _check(lib().or_phase_fix(_ptr(ip), _ptr(dp), _ptr(W), _ptr(phi), _ptr(ido), _ptr(nf)), "phase_fix")
+    return W, phi, int(nf[0])
 
 
 def reinit(g: Grid, phi: np.ndarray, iters: int) -> np.ndarray:

@@ -583,3 +583,71 @@ def test_isolated_flip_keeps_its_material():
     assert r.stats["flipped"] == 1
     assert np.all(r.phi >= 0.0)                              # no sub-cell air fragment is created
     assert np.allclose(r.W, W, rtol=1e-14)                   # uniform water state untouched
+
+
+def test_reinit_holds_the_first_layer_and_moves_the_rest():
+    """Reading R25 (the fixed first layer of Sec. 4.4): cells with a face neighbour of the other
+    sign keep their values bit for bit, so the zero level set between them stays where it was,
+    while the other cells of a level set that is not a distance move towards one."""
+    n = (20, 8, 8)
+    h = 1.0 / 20
+    g = O.Grid(n=n, h=h, eos=(O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)), bc=(0,) * 6)
+    x, y, z = WL.cell_centres(n, h)
+    r = np.sqrt((x - 0.5) ** 2 + (y - 0.2) ** 2 + (z - 0.2) ** 2)
+    phi = (r - 0.3) * (1.0 + 2.0 * (x - 0.5) ** 2 + y)        # same zero set as r - 0.3, not a distance
+    neg = phi < 0
+    first = np.zeros(phi.shape, bool)
+    for ax in range(3):
+        for sh in (1, -1):
+            nb = np.roll(neg, sh, axis=ax)
+            edge = [slice(None)] * 3
+            edge[ax] = 0 if sh == 1 else -1                      # transmissive: the clamped neighbour is itself
+            nb[tuple(edge)] = neg[tuple(edge)]
+            first |= nb != neg
+    out = O.reinit(g, phi, 8)
+    assert first.any() and (~first).any()
+    assert np.array_equal(out[first], phi[first])
+    assert np.array_equal(out < 0, neg)
+    moved = np.abs(out - phi)[~first]
+    assert moved.max() > 0.1 * h
+    # the moved cells come closer to the distance to the sphere
+    dist = r - 0.3
+    far = ~first & (np.abs(dist) < 0.25)
+    assert np.abs(out - dist)[far].mean() < 0.5 * np.abs(phi - dist)[far].mean()
+
+
+def test_phase_update_takes_face_neighbours_before_the_26_neighbourhood():
+    """Reading R17: a cell that changes material takes the mean primitive state of its face
+    neighbours that were and are of the new material; only without any such face neighbour the
+    mean over the 26-neighbourhood's; then its conserved state from the new material's EOS."""
+    n = (5, 5, 5)
+    water, air = O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)
+    g = O.Grid(n=n, h=0.1, eos=(water, air), bc=(0,) * 6)
+    shape = (5, 5, 5)
+
+    def case(face_air):
+        P = np.zeros((5,) + shape)
+        P[0], P[4] = 1000.0, 1e6
+        phi = np.ones(shape)
+        # air neighbours of the centre (2, 2, 2) [z, y, x]: face ones with states A, an edge one with B
+        A = {(2, 2, 1): (1.1, 3.0, 0.0, 0.0, 2e5), (2, 2, 3): (1.3, 5.0, 0.0, 0.0, 4e5)}
+        B = {(2, 3, 3): (2.0, -40.0, 7.0, 0.0, 9e5)}
+        cells = {**(A if face_air else {}), **B}
+        for c, q in cells.items():
+            P[(slice(None),) + c] = q
+            phi[c] = -1.0
+        id_old = (phi < 0).astype(np.uint8)
+        W = O.prims_to_cons(g, P, phi)
+        phi[2, 2, 2] = -0.5                      # the centre changes from water to air
+        W2, phi2, nf = O.phase_fix(g, W, phi, id_old)
+        assert nf == 1 and phi2[2, 2, 2] < 0
+        got = O.cons_to_prims(g, W2, phi2)[(slice(None), 2, 2, 2)]
+        src = A if face_air else B
+        want = np.mean(np.array(list(src.values())), axis=0)
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-9)
+        untouched = np.ones(shape, bool)
+        untouched[2, 2, 2] = False
+        assert np.array_equal(W2[:, untouched], W[:, untouched])
+
+    case(face_air=True)    # face neighbours A present: the edge neighbour B is ignored
+    case(face_air=False)   # no face neighbour of the new material: the 26-neighbourhood (B)
