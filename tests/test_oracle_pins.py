@@ -651,3 +651,28 @@ def test_phase_update_takes_face_neighbours_before_the_26_neighbourhood():
 
     case(face_air=True)    # face neighbours A present: the edge neighbour B is ignored
     case(face_air=False)   # no face neighbour of the new material: the 26-neighbourhood (B)
+
+
+def test_muscl_stencil_stops_at_the_interface():
+    """Reading R11: along an axis where a stencil neighbour has the other material the face
+    states are first order. So the residual of a cell two cells from the interface does not see
+    the state across it (its neighbour's face state towards it is that neighbour's cell state),
+    while the cell next to the interface does (through FIVER)."""
+    n = (8, 1, 1)
+    water, air = O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)
+    g = O.Grid(n=n, h=0.1, eos=(water, air), bc=(0,) * 6)
+    x = (np.arange(8) + 0.5) * 0.1
+    phi = (0.4 - x)[None, None, :]                 # cells 0-3 water (phi > 0), 4-7 air
+    P = np.zeros((5, 1, 1, 8))
+    P[0] = np.where(phi < 0, 1.2, 1000.0) * (1 + 0.05 * np.sin(7 * x))
+    P[1] = 3.0 * np.cos(5 * x)
+    P[4] = np.where(phi < 0, 1e5, 2e5) * (1 + 0.1 * x)
+    W = O.prims_to_cons(g, P, phi)
+    R0, _, _ = O.residual(g, W, phi)
+    P2 = P.copy()
+    P2[0, 0, 0, 4] *= 1.7                          # the first air cell: denser, higher pressure
+    P2[4, 0, 0, 4] *= 3.0
+    W2 = O.prims_to_cons(g, P2, phi)
+    R2, _, _ = O.residual(g, W2, phi)
+    assert np.array_equal(R2[:, 0, 0, 2], R0[:, 0, 0, 2])
+    assert not np.allclose(R2[:, 0, 0, 3], R0[:, 0, 0, 3])
