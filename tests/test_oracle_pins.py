@@ -676,3 +676,20 @@ def test_muscl_stencil_stops_at_the_interface():
     R2, _, _ = O.residual(g, W2, phi)
     assert np.array_equal(R2[:, 0, 0, 2], R0[:, 0, 0, 2])
     assert not np.allclose(R2[:, 0, 0, 3], R0[:, 0, 0, 3])
+
+
+def test_zero_level_set_belongs_to_material_zero():
+    """The material of a cell is 1 where phi < 0 and 0 elsewhere, phi = 0 and phi = -0.0
+    included. Water under tension (p = -1e7 Pa, admissible for the stiffened gas with
+    p_c = 3.43e8) on cells with phi = +-0 stays water: a uniform state is kept bit for bit
+    (as air the state would be non-physical)."""
+    n = (6, 1, 1)
+    g = O.Grid(n=n, h=0.1, eos=(O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)), bc=(1,) * 6)
+    phi = np.array([1.0, 0.5, 0.0, -0.0, 0.5, 1.0])[None, None, :]
+    P = np.zeros((5, 1, 1, 6))
+    P[0] = 1000.0
+    P[4] = -1e7
+    W = O.prims_to_cons(g, P, phi)
+    r = O.run(g, W, phi, 3)
+    assert np.array_equal(r.W, W)
+    assert r.stats["interface_faces"] == 0
