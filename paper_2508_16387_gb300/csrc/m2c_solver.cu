@@ -740,6 +740,7 @@ size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision) {
 m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[3], double h, const int bc[6],
                          int precision, void* workspace, size_t ws_bytes, void* stream) {
   (void)lo;
+  g_noctx_error.clear();
   if (!out) return set_err(nullptr, M2C_EINVAL, "out is NULL");
   *out = nullptr;
   if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !workspace)
@@ -1128,6 +1129,7 @@ m2c_status m2c_get_stats(m2c_ctx* c, m2c_stats* out) {
 static m2c_status solve_riemann_batch(int mixed, int n, const m2c_eos_desc* eosL, const double* L,
                                       const m2c_eos_desc* eosR, const double* R, double* out, int* iters, int* status,
                                       int on_device, void* stream) {
+  g_noctx_error.clear();
   if (n < 0 || !eosL || !eosR || !L || !R || !out) return set_err(nullptr, M2C_EINVAL, "bad batch arguments");
   if (const char* why = eos_desc_error(eosL)) return set_err(nullptr, M2C_EINVAL, std::string("left EOS: ") + why);
   if (const char* why = eos_desc_error(eosR)) return set_err(nullptr, M2C_EINVAL, std::string("right EOS: ") + why);
@@ -1183,6 +1185,7 @@ m2c_status m2c_solve_riemann_mixed(int n, const m2c_eos_desc* eosL, const double
 }
 
 m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]) {
+  g_noctx_error.clear();
   if (!eos || !w || !out) return set_err(nullptr, M2C_EINVAL, "bad shock-state arguments");
   if (const char* why = eos_desc_error(eos)) return set_err(nullptr, M2C_EINVAL, why);
   double prm[6];
@@ -1271,6 +1274,7 @@ size_t m2c_residual_noalloc_scratch_bytes(void) { return m2c::kNaBytes; }
 m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6], const m2c_eos_desc* eos0,
                                 const m2c_eos_desc* eos1, int precision, const double* W, const double* phi,
                                 double* R, double* L, void* stream) {
+  g_noctx_error.clear();  // keeps its capacity: no allocation
   if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !eos0 || !eos1 || !W || !phi || !R || !L)
     return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: bad argument");
   if (precision != M2C_FP64 && precision != M2C_MIXED)

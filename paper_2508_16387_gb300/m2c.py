@@ -98,11 +98,10 @@ def lib():
 
 
 def _check(code: int, where: str, ctx=None):
+    """Raises M2CError with the library's text for the context (or, without one, for the last
+    call on this thread that has no context)."""
     if code != M2C_OK:
-        text = ""
-        if ctx is not None:
-            text = lib().m2c_last_error(ctx).decode()
-        raise M2CError(code, where, text)
+        raise M2CError(code, where, lib().m2c_last_error(ctx).decode())
 
 
 def eos_desc(eos) -> EosDesc:
@@ -336,8 +335,8 @@ class Grid:
 
 class Batch:
     """Several Grid contexts stepped together (one launch per kernel for all of them).
-    tuning = (tile rows 4|8, tile z-length (0 auto), schedule 0 static | 1 dynamic,
-    blocks per SM of a persistent grid (0 = one block per tile))."""
+    tuning = (tile rows 4|8|16 (16: mixed precision only), tile z-length (0 auto),
+    schedule 0 static | 1 dynamic, blocks per SM of a persistent grid (0 = one block per tile))."""
 
     def __init__(self, grids, tuning=(8, 0, 0, 0)):
         import torch

@@ -81,3 +81,19 @@ def test_init_grid_rejects_bad_grids_before_any_device_work(n, bc, why):
                            ctypes.c_void_p(256), 1 << 40, None)
     assert code == m2c.M2C_EINVAL and not ctx.value
     assert L.m2c_last_error(None).decode().startswith(why)
+
+
+def test_binding_raises_with_the_library_text_without_a_context():
+    from paper_2508_16387_gb300 import m2c
+    L = m2c.lib()
+    ctx = ctypes.c_void_p()
+    code = L.m2c_init_grid(ctypes.byref(ctx), 1, 1, 1, None, 0.1, (ctypes.c_int * 6)(*(0,) * 6), m2c.FP64,
+                           ctypes.c_void_p(256), 1 << 40, None)
+    with pytest.raises(m2c.M2CError, match="axis with more than one cell"):
+        m2c._check(code, "m2c_init_grid")
+    # the next call without a context starts with an empty text
+    eos = m2c.eos_desc((m2c.EOS_SG, (1.4, 0.0)))
+    out = (ctypes.c_double * 4)()
+    st = ctypes.c_double * 3
+    assert L.m2c_solve_riemann(0, ctypes.byref(eos), st(), ctypes.byref(eos), st(), out, None, None, 0, None) == 0
+    assert L.m2c_last_error(None).decode() == ""
