@@ -21,10 +21,11 @@
  *
  * Memory ownership. The caller owns all memory. Device arrays passed to the
  * library are borrowed for the life of the context (or of the call, for the
- * one-shot entry points); the library allocates no device memory except the
- * small per-call staging buffers of m2c_solve_riemann and m2c_shock_state when
- * they are given host pointers. All solver scratch lives in one caller-provided
- * device workspace of m2c_workspace_bytes() bytes, 256-byte aligned.
+ * one-shot entry points); the library allocates no device memory. All solver
+ * scratch lives in one caller-provided device workspace of
+ * m2c_workspace_bytes() bytes, 256-byte aligned; the one-shot Riemann and
+ * shock-state calls stage host arrays through a caller-provided workspace of
+ * m2c_riemann_workspace_bytes() bytes.
  *
  * Errors. Every entry point returns an m2c_status; no exception crosses the
  * ABI. Launches are asynchronous on the context's stream; errors raised on
@@ -89,10 +90,18 @@ typedef struct {
   double dt;             /* time step of the next step */
 } m2c_stats;
 
-/* Workspace bytes for an nx*ny*nz grid. */
+/* Workspace bytes for an nx*ny*nz grid (host arithmetic only; 0 if a size is
+ * below 1). The workspace holds what one time step of Sec. 2.3 steps (1)-(6)
+ * needs besides the state: the stage state W(1), phi(1) of the Runge-Kutta
+ * scheme (Sec. 4.3), the reinitialisation scratch (Eq. reinit), one byte of
+ * material flags per cell and the interface work lists of the FIVER flux
+ * (Sec. 4.2); about 84 bytes per cell. */
 size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
 
-/* Creates a context on the calling thread's current CUDA device. At least one
+/* Creates a context on the calling thread's current CUDA device for a
+ * uniform Cartesian mesh of nx*ny*nz cells of edge h (the finite-volume mesh of
+ * Sec. 4.1 with cell-centred control volumes; boundary conditions of Sec. 2.3).
+ * At least one
  * axis must have more than one cell, and nx*ny*nz < 2^31 (M2C_EINVAL otherwise).
  * lo: lower corner (only used to report coordinates), h > 0: cell edge,
  * bc[6]: m2c_bc per side, workspace: device pointer of ws_bytes >=
@@ -129,8 +138,12 @@ m2c_status m2c_set_riemann_start(m2c_ctx* ctx, int fp32_start);
  * planes, else 8. */
 m2c_status m2c_set_tiling(m2c_ctx* ctx, int tile_rows, int tile_z);
 
-/* Borrows the device arrays W (5N doubles) and phi (N doubles) as the state,
- * sets time t and step counter step, and computes the first time step. */
+/* Borrows the device arrays W (5N doubles, the conserved state of Sec. 3.2,
+ * Eq. NSEquation_terms) and phi (N doubles, the level set of Sec. 3.5.1 whose
+ * sign gives the material) as the state, and sets time t and step counter
+ * step; the first time step (Sec. 4.3) is reduced at the next m2c_step. The
+ * arrays stay the caller's and are updated in place by m2c_step. M2C_EINVAL if
+ * an array is NULL or an EOS has not been set. */
 m2c_status m2c_set_state(m2c_ctx* ctx, double* W, double* phi, double t, long step);
 
 /* Fills the borrowed W from device primitive arrays prims (5N: rho, u, v, w, p)
@@ -149,7 +162,12 @@ m2c_status m2c_state_to_prims(m2c_ctx* ctx, double* prims);
 m2c_status m2c_upload_state(m2c_ctx* ctx, const double* W_host, const double* phi_host);
 m2c_status m2c_download_state(m2c_ctx* ctx, double* W_host, double* phi_host);
 
-/* Enqueues nsteps time steps on the context's stream. */
+/* Enqueues nsteps time steps on the context's stream. One step is Sec. 2.3
+ * steps (1)-(6) with the fluid and level-set updates of the TVD Runge-Kutta
+ * scheme (Sec. 4.3): the time step from the CFL number, two stages of the
+ * residual of Sec. 4.2 (Eq. NS_discretized) and of the level-set equation
+ * (Eq. levelset), the scheduled reinitialisation (Eq. reinit) and the phase
+ * update. Asynchronous; device errors are read by m2c_sync. */
 m2c_status m2c_step(m2c_ctx* ctx, int nsteps);
 
 /* Batches: several contexts of one precision stepped together, one launch per
@@ -186,23 +204,33 @@ m2c_status m2c_residual(m2c_ctx* ctx, double* R, double* L);
 
 /* Blocks until the stream is idle; returns the first latched device error,
  * the time, the step counter and the offending cell (-1 if none). Any of the
- * output pointers may be NULL. Clears the latched error. */
+ * output pointers may be NULL. Clears the latched error. The paper's solver
+ * checks state admissibility (rho > 0, c^2 > 0, the EOS domain of App. B) and
+ * Riemann-solver convergence (Sec. 4.2) on the host; here those checks run
+ * on the device and are reported by this call. */
 m2c_status m2c_sync(m2c_ctx* ctx, double* t, long* steps, long* err_cell);
 
 m2c_status m2c_get_stats(m2c_ctx* ctx, m2c_stats* out);
+
+/* Device bytes a host-array call of m2c_solve_riemann, m2c_solve_riemann_mixed
+ * (n problems) or m2c_shock_state (n = 1) stages its arrays through. */
+size_t m2c_riemann_workspace_bytes(int n);
 
 /* Batch of n exact two-material Riemann problems (Sec. 4.2, Eq.
  * 1DRiemannProblem). L and R are SoA (rho[n], u[n], p[n]); out is SoA
  * (p*[n], u*[n], rho*_L[n], rho*_R[n]); iters[n] and status[n] (may be NULL)
  * get the iteration count and per-problem m2c_status. on_device = 1: all
- * arrays are device pointers and the call is asynchronous on stream; 0: host
- * arrays, the call stages them and blocks. Returns the first non-OK status of
- * the batch (host arrays) or M2C_OK (device arrays; read status[]).
+ * arrays are device pointers, workspace is unused (may be NULL) and the call
+ * is asynchronous on stream; 0: host arrays, staged through the caller's
+ * device workspace (256-byte aligned, ws_bytes >= m2c_riemann_workspace_bytes(n);
+ * M2C_ENOMEM if smaller), and the call blocks. Returns the first non-OK
+ * status of the batch (host arrays) or M2C_OK (device arrays; read status[]).
  * M2C_EINVAL, before any device work and with the reason in
  * m2c_last_error(NULL): n < 0, a NULL array or descriptor, or EOS parameters
  * that m2c_set_eos rejects. */
 m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
-                             const double* R, double* out, int* iters, int* status, int on_device, void* stream);
+                             const double* R, double* out, int* iters, int* status, int on_device, void* workspace,
+                             size_t ws_bytes, void* stream);
 
 /* The same batch solved the way the FIVER kernel of the M2C_MIXED path solves
  * it (Sec. 4.2 with the mixed-precision reading): Newton iterations on FP32
@@ -214,13 +242,18 @@ m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, c
  * the FP32 and FP64 steps. Arguments, layout, ownership and errors as for
  * m2c_solve_riemann. */
 m2c_status m2c_solve_riemann_mixed(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
-                                   const double* R, double* out, int* iters, int* status, int on_device, void* stream);
+                                   const double* R, double* out, int* iters, int* status, int on_device,
+                                   void* workspace, size_t ws_bytes, void* stream);
 
 /* Post-shock state of a shock moving in +x into the state w = (rho, u, p) with
- * pressure p1 behind it (the right-facing wave of the exact Riemann solver):
- * out = (rho1, u1, shock speed). Host arrays; blocks. M2C_EINVAL as for
- * m2c_solve_riemann. */
-m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]);
+ * pressure p1 behind it (the right-facing wave of the exact Riemann solver of
+ * Sec. 4.2; the Rankine-Hugoniot state of a planar shock): out = (rho1, u1,
+ * shock speed). Host arrays w and out; the result passes through the caller's
+ * device workspace (256-byte aligned, >= m2c_riemann_workspace_bytes(1)
+ * bytes); enqueued on stream, then blocks. M2C_EINVAL as for
+ * m2c_solve_riemann, and for p1 <= p. */
+m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3], void* workspace,
+                           size_t ws_bytes, void* stream);
 
 /* Allocation-free stage residual. The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory, such as a host
@@ -232,8 +265,12 @@ m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1
  * with no context and no workspace. Its scratch is one file-scope device array
  * of m2c_residual_noalloc_scratch_bytes() bytes (about 10.5 MB), held by every
  * GPU that loads the library until the process exits. Limits and behaviour:
- *  - nx*ny*nz <= M2C_NOALLOC_MAX_CELLS (262144, e.g. 64^3); larger grids are
- *    rejected with M2C_EINVAL before any launch, and m2c_last_error(NULL) says why.
+ *  - nx*ny*nz <= M2C_NOALLOC_MAX_CELLS (262144, e.g. 64^3); larger grids, and
+ *    grids, boundary conditions or EOS that m2c_init_grid or m2c_set_eos would
+ *    reject, are rejected with M2C_EINVAL before any launch, and
+ *    m2c_last_error(NULL) says why.
+ *  - each device that calls it gets its own set-up (the array's address, the
+ *    kernels' shared-memory limits); calls on several devices are allowed.
  *  - the first call on a device looks up the array's device address with that
  *    device current; make that first call before any stream capture.
  *  - every call shares the one array: calls whose work overlaps on the GPU
@@ -259,7 +296,10 @@ m2c_status m2c_profile(m2c_ctx* ctx, int enable);
 m2c_status m2c_profile_read(m2c_ctx* ctx, double* total_ms, long* launches);
 m2c_status m2c_profile_read_kernels(m2c_ctx* ctx, double ms[6], long launches[6]);
 
-/* Releases a context (the borrowed memory stays with the caller). */
+/* Releases a context (host memory of the library only; the borrowed state
+ * and workspace stay with the caller and may be freed after the context's
+ * stream is idle). The paper has no counterpart: this is resource ownership
+ * of the C ABI. */
 void m2c_destroy(m2c_ctx* ctx);
 
 /* Text of the last error of a context; with NULL, of the last failed call on

@@ -59,9 +59,12 @@ __host__ inline EosP<R> make_eos(int type, const double* prm) {
 
 __host__ inline EosDev make_eos_dev(int type, const double* prm) { return make_eos<double>(type, prm); }
 
-// Division, reciprocal and square root of the working precision: IEEE for FP64;
-// for the FP32 half of the mixed path the hardware approximations (a few ulp),
-// which are far below the FP32 rounding already accepted there.
+// Division, reciprocal and square root of the working precision. FP64: the
+// quotient and reciprocal of div_nr / rcp_nr below (a binary32 seed refined by
+// Newton-Raphson steps; the quotient takes a residual correction and equals the
+// IEEE quotient, the reciprocal is within an ulp), IEEE square root. FP32 half
+// of the mixed path: the hardware approximations (a few ulp), far below the
+// FP32 rounding already accepted there.
 __device__ __forceinline__ double rcp_nr(double b);
 __device__ __forceinline__ double div_nr(double a, double b);
 template <typename R>
@@ -259,10 +262,17 @@ __device__ __forceinline__ double rcp_nr(double b) {
   if (nr_range(b)) return rcp_nr_in_range(b);
   return 1.0 / b;
 }
+// The corrected quotient is the IEEE one when it is a normal number and its
+// residual a - b q does not underflow: with |b| in the seed range that holds
+// for |a| in [2^-897, 2^898). A zero a gives the signed zero a (1/b); any other
+// a outside that range (a quotient that could overflow or underflow, an
+// infinity, a NaN) takes the IEEE operation.
 __device__ __forceinline__ double div_nr(double a, double b) {
   if (nr_range(b)) {
     const double x = rcp_nr_in_range(b), q = a * x;
-    return fma(fma(-b, q, a), x, q);
+    const unsigned ha = hi_of(a), ea = (ha >> 20) & 0x7ffu;
+    if (ea - 126u < 1795u) return fma(fma(-b, q, a), x, q);
+    if (((ha & 0x7fffffffu) | lo_of(a)) == 0u) return q;
   }
   return a / b;
 }

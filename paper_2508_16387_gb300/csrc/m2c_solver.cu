@@ -526,6 +526,24 @@ const char* eos_desc_error(const m2c_eos_desc* e) {
   return eos_param_error(e->type, e->params, e->type == M2C_EOS_SG ? 2 : 6);
 }
 
+// Checks of a grid's sizes, cell edge and boundary conditions shared by
+// m2c_init_grid and m2c_residual_noalloc: nullptr when valid, else the reason.
+const char* grid_args_error(int nx, int ny, int nz, double h, const int* bc) {
+  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc) return "grid sizes >= 1, h > 0 and bc required";
+  if ((long long)nx * ny * nz < 2)  // no axis to move along: no time step
+    return "a grid needs an axis with more than one cell";
+  if ((long long)nx * ny * nz >= (1ll << 31))  // 32-bit cell indices in some kernels
+    return "a grid holds fewer than 2^31 cells";
+  for (int a = 0; a < 3; ++a) {
+    for (int s = 0; s < 2; ++s)
+      if (bc[2 * a + s] != M2C_BC_TRANSMISSIVE && bc[2 * a + s] != M2C_BC_PERIODIC)
+        return "unknown boundary condition";
+    if ((bc[2 * a] == M2C_BC_PERIODIC) != (bc[2 * a + 1] == M2C_BC_PERIODIC))
+      return "periodic on one side of an axis only";
+  }
+  return nullptr;
+}
+
 m2c_status cuda_check(m2c_ctx* c, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return M2C_OK;
   return set_err(c, M2C_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -546,15 +564,21 @@ void setup_all_stage_kernels() {
 
 namespace m2c {
 
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  return dev < kMaxDevices ? dev : kMaxDevices - 1;
+}
+
 int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+  static int n[kMaxDevices] = {};
+  const int dev = current_device();
+  if (!n[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n[dev] = v > 0 ? v : 1;
   }
-  return n;
+  return n[dev];
 }
 
 }  // namespace m2c
@@ -743,20 +767,9 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   g_noctx_error.clear();
   if (!out) return set_err(nullptr, M2C_EINVAL, "out is NULL");
   *out = nullptr;
-  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !workspace)
-    return set_err(nullptr, M2C_EINVAL, "grid sizes >= 1, h > 0, bc and workspace required");
-  if ((long long)nx * ny * nz < 2)  // no axis to move along: no time step
-    return set_err(nullptr, M2C_EINVAL, "a grid needs an axis with more than one cell");
-  if ((long long)nx * ny * nz >= (1ll << 31))  // 32-bit cell indices in some kernels
-    return set_err(nullptr, M2C_EINVAL, "a grid holds fewer than 2^31 cells");
+  if (const char* why = grid_args_error(nx, ny, nz, h, bc)) return set_err(nullptr, M2C_EINVAL, why);
+  if (!workspace) return set_err(nullptr, M2C_EINVAL, "workspace required");
   if (precision != M2C_FP64 && precision != M2C_MIXED) return set_err(nullptr, M2C_EINVAL, "unknown precision");
-  for (int a = 0; a < 3; ++a) {
-    for (int s = 0; s < 2; ++s)
-      if (bc[2 * a + s] != M2C_BC_TRANSMISSIVE && bc[2 * a + s] != M2C_BC_PERIODIC)
-        return set_err(nullptr, M2C_EINVAL, "unknown boundary condition");
-    if ((bc[2 * a] == M2C_BC_PERIODIC) != (bc[2 * a + 1] == M2C_BC_PERIODIC))
-      return set_err(nullptr, M2C_EINVAL, "periodic on one side of an axis only");
-  }
   if (reinterpret_cast<uintptr_t>(workspace) % kAlign)
     return set_err(nullptr, M2C_EINVAL, "workspace is not 256-byte aligned");
   const long long N = (long long)nx * ny * nz;
@@ -1126,14 +1139,39 @@ m2c_status m2c_get_stats(m2c_ctx* c, m2c_stats* out) {
   return M2C_OK;
 }
 
+// Staging layout of the host-array Riemann entry points in the caller's
+// workspace: L (3n), R (3n), out (4n) doubles, iters (n) and status (n) ints.
+static size_t riemann_ws_layout(long long n, size_t off[5]) {
+  size_t o = 0;
+  off[0] = o; o = align_up(o + sizeof(double) * 3 * (size_t)n);
+  off[1] = o; o = align_up(o + sizeof(double) * 3 * (size_t)n);
+  off[2] = o; o = align_up(o + sizeof(double) * 4 * (size_t)n);
+  off[3] = o; o = align_up(o + sizeof(int) * (size_t)n);
+  off[4] = o; o = align_up(o + sizeof(int) * (size_t)n);
+  return o;
+}
+
+size_t m2c_riemann_workspace_bytes(int n) {
+  if (n < 1) n = 1;
+  size_t off[5];
+  return riemann_ws_layout(n, off);
+}
+
 static m2c_status solve_riemann_batch(int mixed, int n, const m2c_eos_desc* eosL, const double* L,
                                       const m2c_eos_desc* eosR, const double* R, double* out, int* iters, int* status,
-                                      int on_device, void* stream) {
+                                      int on_device, void* workspace, size_t ws_bytes, void* stream) {
   g_noctx_error.clear();
   if (n < 0 || !eosL || !eosR || !L || !R || !out) return set_err(nullptr, M2C_EINVAL, "bad batch arguments");
   if (const char* why = eos_desc_error(eosL)) return set_err(nullptr, M2C_EINVAL, std::string("left EOS: ") + why);
   if (const char* why = eos_desc_error(eosR)) return set_err(nullptr, M2C_EINVAL, std::string("right EOS: ") + why);
   if (n == 0) return M2C_OK;
+  size_t off[5];
+  if (!on_device) {
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign)
+      return set_err(nullptr, M2C_EINVAL, "host arrays need a 256-byte aligned device workspace");
+    if (ws_bytes < riemann_ws_layout(n, off))
+      return set_err(nullptr, M2C_ENOMEM, "workspace smaller than m2c_riemann_workspace_bytes(n)");
+  }
   double pl[6] = {0, 0, 0, 0, 0, -INFINITY}, pr[6] = {0, 0, 0, 0, 0, -INFINITY};
   for (int i = 0; i < 6; ++i) {
     pl[i] = eosL->params[i];
@@ -1146,62 +1184,68 @@ static m2c_status solve_riemann_batch(int mixed, int n, const m2c_eos_desc* eosL
   const int blocks = (int)std::min<long long>((n + threads - 1) / threads, 4ll * sm_count());
   if (on_device) {
     k_riemann_batch<<<blocks, threads, 0, s>>>(n, qL, L, qR, R, out, iters, status, mixed, qLf, qRf);
-    return cudaGetLastError() == cudaSuccess ? M2C_OK : M2C_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? M2C_OK : set_err(nullptr, M2C_ECUDA, "Riemann batch launch");
   }
-  double *dL = nullptr, *dR = nullptr, *dO = nullptr;
-  int *dI = nullptr, *dS = nullptr;
-  m2c_status st = M2C_OK;
-  if (cudaMalloc(&dL, sizeof(double) * 3 * n) != cudaSuccess || cudaMalloc(&dR, sizeof(double) * 3 * n) != cudaSuccess ||
-      cudaMalloc(&dO, sizeof(double) * 4 * n) != cudaSuccess || cudaMalloc(&dI, sizeof(int) * n) != cudaSuccess ||
-      cudaMalloc(&dS, sizeof(int) * n) != cudaSuccess) {
-    st = M2C_ECUDA;
-  } else {
-    cudaMemcpyAsync(dL, L, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(dR, R, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  double* dL = reinterpret_cast<double*>(ws + off[0]);
+  double* dR = reinterpret_cast<double*>(ws + off[1]);
+  double* dO = reinterpret_cast<double*>(ws + off[2]);
+  int* dI = reinterpret_cast<int*>(ws + off[3]);
+  int* dS = reinterpret_cast<int*>(ws + off[4]);
+  std::vector<int> hs(n);
+  cudaError_t e = cudaMemcpyAsync(dL, L, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dR, R, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
     k_riemann_batch<<<blocks, threads, 0, s>>>(n, qL, dL, qR, dR, dO, dI, dS, mixed, qLf, qRf);
-    std::vector<int> hs(n);
-    cudaMemcpyAsync(out, dO, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(hs.data(), dS, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
-    if (iters) cudaMemcpyAsync(iters, dI, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) st = M2C_ECUDA;
-    if (status) std::memcpy(status, hs.data(), sizeof(int) * n);
-    if (st == M2C_OK)
-      for (int i = 0; i < n; ++i)
-        if (hs[i]) { st = (m2c_status)hs[i]; break; }
+    e = cudaGetLastError();
   }
-  cudaFree(dL); cudaFree(dR); cudaFree(dO); cudaFree(dI); cudaFree(dS);
-  return st;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dO, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), dS, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && iters) e = cudaMemcpyAsync(iters, dI, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_err(nullptr, M2C_ECUDA, std::string("Riemann batch: ") + cudaGetErrorString(e));
+  if (status) std::memcpy(status, hs.data(), sizeof(int) * n);
+  for (int i = 0; i < n; ++i)
+    if (hs[i]) return set_err(nullptr, (m2c_status)hs[i], "problem " + std::to_string(i) + ": " + m2c_status_string(hs[i]));
+  return M2C_OK;
 }
 
 m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
-                             const double* R, double* out, int* iters, int* status, int on_device, void* stream) {
-  return solve_riemann_batch(0, n, eosL, L, eosR, R, out, iters, status, on_device, stream);
+                             const double* R, double* out, int* iters, int* status, int on_device, void* workspace,
+                             size_t ws_bytes, void* stream) {
+  return solve_riemann_batch(0, n, eosL, L, eosR, R, out, iters, status, on_device, workspace, ws_bytes, stream);
 }
 
 m2c_status m2c_solve_riemann_mixed(int n, const m2c_eos_desc* eosL, const double* L, const m2c_eos_desc* eosR,
                                    const double* R, double* out, int* iters, int* status, int on_device,
-                                   void* stream) {
-  return solve_riemann_batch(1, n, eosL, L, eosR, R, out, iters, status, on_device, stream);
+                                   void* workspace, size_t ws_bytes, void* stream) {
+  return solve_riemann_batch(1, n, eosL, L, eosR, R, out, iters, status, on_device, workspace, ws_bytes, stream);
 }
 
-m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3]) {
+m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1, double out[3], void* workspace,
+                           size_t ws_bytes, void* stream) {
   g_noctx_error.clear();
   if (!eos || !w || !out) return set_err(nullptr, M2C_EINVAL, "bad shock-state arguments");
   if (const char* why = eos_desc_error(eos)) return set_err(nullptr, M2C_EINVAL, why);
+  if (!workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign)
+    return set_err(nullptr, M2C_EINVAL, "a 256-byte aligned device workspace is required");
+  if (ws_bytes < m2c_riemann_workspace_bytes(1))
+    return set_err(nullptr, M2C_ENOMEM, "workspace smaller than m2c_riemann_workspace_bytes(1)");
   double prm[6];
   for (int i = 0; i < 6; ++i) prm[i] = eos->params[i];
   const EosDev q = make_eos_dev(eos->type, prm);
-  double* d = nullptr;
-  if (cudaMalloc(&d, 4 * sizeof(double)) != cudaSuccess) return M2C_ECUDA;
+  double* d = static_cast<double*>(workspace);
   int* ds = reinterpret_cast<int*>(d + 3);
-  k_shock_state<<<1, 1>>>(q, w[0], w[1], w[2], p1, d, ds);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_shock_state<<<1, 1, 0, s>>>(q, w[0], w[1], w[2], p1, d, ds);
   double h[4];
-  cudaError_t e = cudaMemcpy(h, d, 4 * sizeof(double), cudaMemcpyDeviceToHost);
-  cudaFree(d);
-  if (e != cudaSuccess) return M2C_ECUDA;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_err(nullptr, M2C_ECUDA, std::string("shock state: ") + cudaGetErrorString(e));
   int st;
   std::memcpy(&st, &h[3], sizeof(int));
-  if (st) return (m2c_status)st;
+  if (st) return set_err(nullptr, (m2c_status)st, m2c_status_string(st));
   out[0] = h[0]; out[1] = h[1]; out[2] = h[2];
   return M2C_OK;
 }
@@ -1241,7 +1285,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 }  // namespace m2c
 
 namespace {
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[kMaxDevices] = {};
 m2c_status noalloc_fail(m2c_status st, const std::string& msg) {
@@ -1275,17 +1318,21 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
                                 const m2c_eos_desc* eos1, int precision, const double* W, const double* phi,
                                 double* R, double* L, void* stream) {
   g_noctx_error.clear();  // keeps its capacity: no allocation
-  if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !bc || !eos0 || !eos1 || !W || !phi || !R || !L)
-    return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: bad argument");
+  if (!eos0 || !eos1 || !W || !phi || !R || !L) return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: bad argument");
+  if (const char* why = grid_args_error(nx, ny, nz, h, bc))
+    return noalloc_fail(M2C_EINVAL, std::string("m2c_residual_noalloc: ") + why);
   if (precision != M2C_FP64 && precision != M2C_MIXED)
     return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: bad precision");
+  // the EOS rules of m2c_set_eos: an unknown type or a parameter outside its
+  // range is rejected before any device work
+  if (const char* why = eos_desc_error(eos0))
+    return noalloc_fail(M2C_EINVAL, std::string("m2c_residual_noalloc: material 0 EOS: ") + why);
+  if (const char* why = eos_desc_error(eos1))
+    return noalloc_fail(M2C_EINVAL, std::string("m2c_residual_noalloc: material 1 EOS: ") + why);
   const long long N = (long long)nx * ny * nz;
   if (N > m2c::kNoAllocMaxCells)
     return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: " + std::to_string(N) + " cells exceed the maximum of " +
                                         std::to_string(m2c::kNoAllocMaxCells));
-  for (int a = 0; a < 3; ++a)
-    if ((bc[2 * a] == M2C_BC_PERIODIC) != (bc[2 * a + 1] == M2C_BC_PERIODIC))
-      return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: periodic sides must come in pairs");
   void* base = nullptr;
   m2c_status st = noalloc_scratch(&base);
   if (st) return st;

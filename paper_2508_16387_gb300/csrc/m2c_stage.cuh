@@ -472,16 +472,16 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   }
 }
 
+// The shared-memory opt-in is a per-device attribute of the kernel: it is set
+// once on every device the calling threads make current.
 template <typename R, int TY>
 void stage_smem_setup() {
-  static bool done = false;
-  if (done) return;
+  static bool done[kMaxDevices] = {};
+  const int dev = current_device();
+  if (done[dev]) return;
   cudaFuncSetAttribute(k_stage<R, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<R, TY>::bytes);
-  done = true;
+  done[dev] = true;
 }
-
-
-
 
 template <typename R, int TY>
 cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,

@@ -14,6 +14,10 @@ struct LaunchPlan {
   unsigned long long* counter = nullptr;
 };
 
+// Host-side state kept per device (index of the current device, clamped to
+// kMaxDevices - 1) and the current device's SM count.
+constexpr int kMaxDevices = 64;
+int current_device();
 int sm_count();
 
 // Launch of k_stage<R, lp.ty> over ntiles tiles of ngrid grids (FP32: 4, 8 or

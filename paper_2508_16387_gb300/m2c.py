@@ -77,9 +77,12 @@ def lib():
         L.m2c_residual.argtypes = [p, p, p]
         L.m2c_sync.argtypes = [p, p, p, p]
         L.m2c_get_stats.argtypes = [p, ctypes.POINTER(Stats)]
-        L.m2c_solve_riemann.argtypes = [i, ctypes.POINTER(EosDesc), p, ctypes.POINTER(EosDesc), p, p, p, p, i, p]
+        L.m2c_riemann_workspace_bytes.restype = z
+        L.m2c_riemann_workspace_bytes.argtypes = [i]
+        L.m2c_solve_riemann.argtypes = [i, ctypes.POINTER(EosDesc), p, ctypes.POINTER(EosDesc), p, p, p, p, i, p, z,
+                                        p]
         L.m2c_solve_riemann_mixed.argtypes = L.m2c_solve_riemann.argtypes
-        L.m2c_shock_state.argtypes = [ctypes.POINTER(EosDesc), p, d, p]
+        L.m2c_shock_state.argtypes = [ctypes.POINTER(EosDesc), p, d, p, p, z, p]
         L.m2c_residual_noalloc_scratch_bytes.restype = z
         L.m2c_residual_noalloc_scratch_bytes.argtypes = []
         L.m2c_residual_noalloc.argtypes = [i, i, i, d, p, ctypes.POINTER(EosDesc), ctypes.POINTER(EosDesc), i,
@@ -150,13 +153,25 @@ def m2c_solve_riemann(eosL, L, eosR, R, stream=None, mixed=False):
     eL, eR = eos_desc(eosL), eos_desc(eosR)
     fn = lib().m2c_solve_riemann_mixed if mixed else lib().m2c_solve_riemann
     code = fn(n, ctypes.byref(eL), _ptr(L.contiguous()), ctypes.byref(eR), _ptr(R.contiguous()), _ptr(out),
-              _ptr(iters), _ptr(status), 1, _stream_handle(stream))
+              _ptr(iters), _ptr(status), 1, None, 0, _stream_handle(stream))
     _check(code, "m2c_solve_riemann_mixed" if mixed else "m2c_solve_riemann")
     return out, iters, status
 
 
-def m2c_solve_riemann_host(eosL, L, eosR, R):
-    """Host-array variant: L, R numpy (3, n); returns (code, out (4, n), iters, status)."""
+def _device_workspace(nbytes):
+    """A 256-byte aligned device buffer of nbytes (torch owns it): (tensor, pointer)."""
+    import torch
+    t = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    return t, ctypes.c_void_p(t.data_ptr() + (-t.data_ptr()) % 256)
+
+
+def m2c_riemann_workspace_bytes(n) -> int:
+    return lib().m2c_riemann_workspace_bytes(n)
+
+
+def m2c_solve_riemann_host(eosL, L, eosR, R, mixed=False):
+    """Host-array variant: L, R numpy (3, n); returns (code, out (4, n), iters, status).
+    The library stages the arrays through a device workspace owned here."""
     import numpy as np
     L = np.ascontiguousarray(L, dtype=np.float64)
     R = np.ascontiguousarray(R, dtype=np.float64)
@@ -166,8 +181,11 @@ def m2c_solve_riemann_host(eosL, L, eosR, R):
     status = np.zeros(n, dtype=np.int32)
     eL, eR = eos_desc(eosL), eos_desc(eosR)
     vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-    code = lib().m2c_solve_riemann(n, ctypes.byref(eL), vp(L), ctypes.byref(eR), vp(R), vp(out), vp(iters),
-                                   vp(status), 0, None)
+    nb = m2c_riemann_workspace_bytes(n)
+    ws, wp = _device_workspace(nb)
+    fn = lib().m2c_solve_riemann_mixed if mixed else lib().m2c_solve_riemann
+    code = fn(n, ctypes.byref(eL), vp(L), ctypes.byref(eR), vp(R), vp(out), vp(iters), vp(status), 0, wp, nb, None)
+    del ws
     return code, out, iters, status
 
 
@@ -176,8 +194,12 @@ def m2c_shock_state(eos, w, p1):
     e = eos_desc(eos)
     w = np.ascontiguousarray(w, dtype=np.float64)
     out = np.zeros(3)
+    nb = m2c_riemann_workspace_bytes(1)
+    ws, wp = _device_workspace(nb)
     _check(lib().m2c_shock_state(ctypes.byref(e), w.ctypes.data_as(ctypes.c_void_p), p1,
-                                 out.ctypes.data_as(ctypes.c_void_p)), "m2c_shock_state")
+                                 out.ctypes.data_as(ctypes.c_void_p), wp, nb, _stream_handle(None)),
+           "m2c_shock_state")
+    del ws
     return tuple(out)
 
 

@@ -1,11 +1,13 @@
 // Device check of the FP64 reciprocal and quotient of the bulk kernels
 // (rcp_nr, div_nr) against the IEEE operations: random operands over the
 // Newton range and beyond it, short mantissas, all-ones mantissas (the inputs
-// where a faithful reciprocal may miss by an ulp) and exact quotients. Prints
-// the number of quotients that differ from a / b and the worst reciprocal
-// error in ulps.
+// where a faithful reciprocal may miss by an ulp), exact quotients, quotients
+// that overflow or underflow (into the subnormal range and to zero) and signed
+// zero numerators. Prints the number of quotients whose bits differ from
+// a / b (NaNs compare equal) and the worst reciprocal error in ulps.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <random>
 
 #include "m2c_physics.cuh"
@@ -37,7 +39,18 @@ int main() {
     if (i % 8 == 1) hb[i] = std::ldexp(1.0 + (double)(g() % 64) / 64.0, (int)(g() % 40) - 20);
     if (i % 8 == 2) hb[i] = std::nextafter(std::ldexp(1.0, (int)(g() % 40) - 19), 0.0);
     if (i % 8 == 3) ha[i] = hb[i] * (double)(g() % 1000);
+    if (i % 16 == 4) ha[i] = std::ldexp(1.0 + (double)(g() >> 11) * 0x1p-53, 880 + (int)(g() % 143));
+    if (i % 16 == 12) ha[i] = std::ldexp(1.0 + (double)(g() >> 11) * 0x1p-53, -1074 + (int)(g() % 200));
+    if (i % 16 == 5) ha[i] = (g() & 1) ? 0.0 : -0.0;
   }
+  ha[7] = 1e308; hb[7] = 0.5;    // overflows to infinity
+  ha[8] = -1e308; hb[8] = 1e-30;
+  ha[9] = 1e-300; hb[9] = 1e30;  // subnormal quotient
+  ha[10] = 4.9e-324; hb[10] = 3.0;
+  ha[11] = -0.0; hb[11] = 7.0;   // signed zeros
+  ha[12] = 0.0; hb[12] = -7.0;
+  ha[13] = INFINITY; hb[13] = 2.0;
+  ha[14] = NAN; hb[14] = 2.0;
   hb[0] = 0.0; hb[1] = -0.0; hb[2] = INFINITY; hb[3] = NAN; hb[4] = 0x1p-125; hb[5] = 0x1p125; hb[6] = 1e-300;
   double *da, *db, *dx, *dy, *dq, *dd;
   const size_t bytes = sizeof(double) * n;
@@ -61,7 +74,8 @@ int main() {
   long ndiv = 0;
   double worst_rcp = 0.0;
   for (int i = 0; i < n; ++i) {
-    if (ulps(hq[i], hd[i]) != 0.0) ++ndiv;
+    const bool same = std::memcmp(&hq[i], &hd[i], sizeof(double)) == 0 || (std::isnan(hq[i]) && std::isnan(hd[i]));
+    if (!same) ++ndiv;
     const double u = ulps(hx[i], hy[i]);
     if (!(u <= worst_rcp)) worst_rcp = u;
   }

@@ -60,7 +60,8 @@ def test_riemann_entry_rejects_bad_eos_before_any_device_work(left, right, why):
     st = ctypes.c_double * 3
     out = (ctypes.c_double * 4)()
     for fn in (L.m2c_solve_riemann, L.m2c_solve_riemann_mixed):
-        code = fn(1, ctypes.byref(eL), st(1.0, 0.0, 1e5), ctypes.byref(eR), st(1.0, 0.0, 1e5), out, None, None, 0, None)
+        code = fn(1, ctypes.byref(eL), st(1.0, 0.0, 1e5), ctypes.byref(eR), st(1.0, 0.0, 1e5), out, None, None, 0,
+                  None, 0, None)
         assert code == m2c.M2C_EINVAL
         assert L.m2c_last_error(None).decode().startswith(why)
 
@@ -95,5 +96,6 @@ def test_binding_raises_with_the_library_text_without_a_context():
     eos = m2c.eos_desc((m2c.EOS_SG, (1.4, 0.0)))
     out = (ctypes.c_double * 4)()
     st = ctypes.c_double * 3
-    assert L.m2c_solve_riemann(0, ctypes.byref(eos), st(), ctypes.byref(eos), st(), out, None, None, 0, None) == 0
+    assert L.m2c_solve_riemann(0, ctypes.byref(eos), st(), ctypes.byref(eos), st(), out, None, None, 0, None, 0,
+                               None) == 0
     assert L.m2c_last_error(None).decode() == ""

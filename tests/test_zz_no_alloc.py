@@ -7,12 +7,12 @@ residual with its scratch in one library-held device array. This file is
 collected last so that a run stopping at its first failure has already run
 every other test; it passes alone in a fresh process and after the others.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
 from paper_2508_16387_gb300 import workloads as WL
-
-pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -41,6 +41,7 @@ def _case(M, n, seed, water, precision):
     return code, R.cpu().numpy(), L.cpu().numpy(), R_ctx.cpu().numpy(), L_ctx.cpu().numpy()
 
 
+@pytest.mark.gpu
 def test_noalloc_residual_matches_context_residual_twice_in_a_row(m2c):
     # two calls in a row on different grids and materials: the second call must not see the
     # first call's counters or lists, which stay in the shared array
@@ -55,6 +56,7 @@ def test_noalloc_residual_matches_context_residual_twice_in_a_row(m2c):
         assert np.abs(L - L_ctx).max() <= 1e-11 * max(np.abs(L_ctx).max(), 1.0)
 
 
+@pytest.mark.gpu
 def test_noalloc_rejects_grids_above_its_maximum(m2c):
     import torch
     n = (128, 64, 33)   # 270336 cells > 262144
@@ -64,3 +66,26 @@ def test_noalloc_rejects_grids_above_its_maximum(m2c):
     assert code == 1
     assert b"exceed" in m2c.lib().m2c_last_error(None)
     assert m2c.m2c_residual_noalloc_scratch_bytes() < 16 * 2 ** 20
+
+
+@pytest.mark.parametrize("eos0,eos1,bc,why", [
+    ((7, (1.4, 0.0)), WL.AIR_PG, (0,) * 6, "material 0 EOS: unknown EOS type"),
+    (WL.WATER_SG, (0, (0.9, 0.0)), (0,) * 6, "material 1 EOS: SG needs gamma > 1"),
+    ((1, (1000.0, 1483.0, 0.5, 0.28, 0.0, -float("inf"))), WL.AIR_PG, (0,) * 6,
+     "material 0 EOS: MG needs rho0, c0 > 0, s > 1"),
+    (WL.WATER_SG, WL.AIR_PG, (0, 0, 9, 9, 0, 0), "unknown boundary condition"),
+    (WL.WATER_SG, WL.AIR_PG, (1, 0, 0, 0, 0, 0), "periodic on one side of an axis only"),
+])
+def test_noalloc_rejects_bad_eos_and_boundaries_before_any_device_work(eos0, eos1, bc, why):
+    """The EOS and boundary rules of m2c_set_eos and m2c_init_grid apply to the allocation-free
+    entry point too: a bad EOS type or parameter, or an unknown boundary type, is rejected on the
+    host with the reason in m2c_last_error(NULL) (the array pointers are never dereferenced, so
+    this runs without a GPU)."""
+    from paper_2508_16387_gb300 import m2c as M
+    L = M.lib()
+    e0, e1 = M.eos_desc(eos0), M.eos_desc(eos1)
+    fake = ctypes.c_void_p(256)
+    code = L.m2c_residual_noalloc(8, 8, 8, 0.125, (ctypes.c_int * 6)(*bc), ctypes.byref(e0), ctypes.byref(e1),
+                                  M.FP64, fake, fake, fake, fake, None)
+    assert code == M.M2C_EINVAL
+    assert L.m2c_last_error(None).decode().startswith("m2c_residual_noalloc: " + why)
