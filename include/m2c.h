@@ -122,6 +122,38 @@ m2c_status m2c_set_eos(m2c_ctx* ctx, int material, int type, const double* param
  * reinit_every-th step, reinit_iters pseudo-time iterations (0 disables). */
 m2c_status m2c_set_scheme(m2c_ctx* ctx, double cfl, int reinit_every, int reinit_iters);
 
+/* Scheme options beyond the default of m2c_init_grid (TVD RK2, the modified van
+ * Albada limiter, HLLC, the CFL time step): the paper's other choices.
+ *  rk: Runge-Kutta scheme of Sec. 4.3: 2 = TVD RK2 (default), 3 = TVD RK3
+ *      (W2 = 3/4 W + 1/4 W1 + 1/4 dt R(W1), W' = 1/3 W + 2/3 W2 + 2/3 dt R(W2);
+ *      its second stage state needs the workspace of m2c_workspace_bytes_rk(.., 3),
+ *      M2C_ENOMEM if the context's workspace is smaller), 1 = forward Euler.
+ *  limiter: M2C_LIM_VAN_ALBADA (App. D, the modified limiter) or M2C_LIM_MC
+ *      (App. D, Eq. theta: phi = max(0, min(alpha theta, (1 + theta)/2, alpha)),
+ *      alpha = mc_alpha, 1 <= alpha <= 2).
+ *  flux: M2C_FLUX_HLLC (App. C.4) or M2C_FLUX_LLF (App. C.1, Eq.
+ *      Lax-Friedrichs: the local Lax-Friedrichs flux with the largest |u_n| + c of
+ *      the two face states); the FIVER flux of an interface face uses it too.
+ *  dt_fixed: > 0 = a constant time step instead of the CFL rule (Sec. 4.3).
+ * Any non-default option selects the general instantiation of the bulk kernel
+ * (8-row tiles; its results equal the default kernel's for default options).
+ * M2C_EINVAL for a value outside these sets. */
+typedef enum { M2C_LIM_VAN_ALBADA = 0, M2C_LIM_MC = 1 } m2c_limiter;
+typedef enum { M2C_FLUX_HLLC = 0, M2C_FLUX_LLF = 1 } m2c_flux;
+typedef struct {
+  int rk;
+  int limiter;
+  int flux;
+  double mc_alpha;
+  double dt_fixed;
+} m2c_options;
+m2c_status m2c_set_options(m2c_ctx* ctx, const m2c_options* opt);
+
+/* Workspace bytes for an nx*ny*nz grid stepped with the Runge-Kutta scheme of
+ * order rk (Sec. 4.3): rk = 1 or 2 as m2c_workspace_bytes, rk = 3 adds the
+ * second stage state (48 bytes per cell). The RK2 layout is a prefix of it. */
+size_t m2c_workspace_bytes_rk(int nx, int ny, int nz, int precision, int rk);
+
 /* M2C_MIXED grids only (M2C_EINVAL otherwise for fp32_start = 1). fp32_start
  * = 0 (default): the FIVER kernel runs the FP64 Newton iteration of
  * m2c_solve_riemann. fp32_start = 1: it starts the iteration on FP32 wave
@@ -235,7 +267,7 @@ m2c_status m2c_solve_riemann(int n, const m2c_eos_desc* eosL, const double* L, c
 /* The same batch solved the way the FIVER kernel of the M2C_MIXED path solves
  * it (Sec. 4.2 with the mixed-precision reading): Newton iterations on FP32
  * wave curves from the same start, then one FP64 Newton step on the FP64 wave
- * curves (two when the first moves p by more than 1e-7 |p|); u* and the star
+ * curves (two when the first moves p by more than 1e-9 |p|); u* and the star
  * densities follow to first order in the last step. Problems whose FP32
  * iteration fails, signals a vacuum or ends more than 1e-5 |p| from the FP64
  * step are solved by the FP64 iteration of m2c_solve_riemann. iters counts

@@ -269,6 +269,8 @@ static int mg_de_drho_p(const or_eos_t* q, double rho, double* de_drho) {
 
 typedef struct {
   double rho, u, p, c, e;
+  int nrk; /* RK4 substeps of this side's rarefaction curve fixed for one Riemann
+            * problem (Reading R6); 0: chosen per evaluation from |p - p_K| */
 } side_t;
 
 /* Wave curve of one side: velocity change f_K(p) across the K-wave that takes
@@ -344,10 +346,12 @@ static int mg_isentrope_rhs(const or_eos_t* q, double p, double rho, double* drh
   return OR_OK;
 }
 
-/* Substeps of the RK4 isentrope integration over [p, p_K] (Reading R6): 64 equal
- * substeps when the interval spans at least 5% of the reference bulk modulus
- * K0 = rho0 c0^2, proportionally fewer (at least one) for weaker waves, so the
- * substep length never exceeds 0.05 K0 / 64. */
+/* Substeps of the RK4 isentrope integration over a pressure span dp (Reading
+ * R6): 64 equal substeps when the span is at least 5% of the reference bulk
+ * modulus K0 = rho0 c0^2, proportionally fewer (at least one) for weaker waves,
+ * so the substep length never exceeds 0.05 K0 / 64. Within one Riemann problem
+ * the count is fixed before the iteration from a bound of the span (see
+ * rarefaction_substeps), so that the wave curve is a smooth function of p. */
 static int rk4_substeps(const or_eos_t* q, double dp) {
   double K0 = q->prm[0] * q->prm[1] * q->prm[1];
   double n = ceil(RK4_SUBSTEPS * fabs(dp) / (RK4_SPAN_FRAC * K0));
@@ -377,7 +381,7 @@ static int wave_mg(const or_eos_t* q, const side_t* K, double p, double* f, doub
     *rs = rho;
     return OR_OK;
   }
-  int ns = rk4_substeps(q, p - K->p);
+  int ns = K->nrk > 0 ? K->nrk : rk4_substeps(q, p - K->p);
   double hs = (p - K->p) / ns;
   double rho = K->rho, fv = 0.0;
   for (int i = 0; i < ns; ++i) {
@@ -477,7 +481,7 @@ static int wave_jwl(const or_eos_t* q, const side_t* K, double p, double* f, dou
   if (!(p > 0.0) || !(K->p > 0.0)) return OR_ENONPHYS;
   double span = log(p / K->p);
   double nd = ceil(256.0 * fabs(span));
-  int ns = nd < 8.0 ? 8 : (int)nd;
+  int ns = K->nrk > 0 ? K->nrk : (nd < 8.0 ? 8 : (int)nd);
   double hs = span / ns, s0 = log(K->p);
   double rho = K->rho, fv = 0.0;
   for (int i = 0; i < ns; ++i) {
@@ -556,11 +560,33 @@ static int make_side(const or_eos_t* q, const double w[3], side_t* K) {
   K->rho = w[0];
   K->u = w[1];
   K->p = w[2];
+  K->nrk = 0;
   double c2;
   int st = eos_c2(q, K->rho, K->p, &c2);
   if (st) return st;
   K->c = sqrt(c2);
   return eos_e(q, K->rho, K->p, &K->e);
+}
+
+/* Reading R6: within one Riemann problem the substep count of side K's
+ * rarefaction curve is fixed before the iteration (so that every evaluation
+ * lies on one smooth curve of p) from an upper bound of the pressure drop
+ * across it. The star pressure is at least p_lo = max(p_low, min(p_J, p_ac))
+ * with p_ac = (Z_R p_L + Z_L p_R - Z_L Z_R (u_R - u_L))/(Z_L + Z_R), Z = rho c:
+ * if the other side J carries a shock, p* > p_J; if it carries a rarefaction
+ * too, each rarefaction curve lies below its acoustic tangent,
+ * |f_K(p)| >= |p - p_K|/Z_K (rho c falls along an isentrope as p falls), and
+ * F(p*) = 0 then gives p* >= p_ac. MG: the count of rk4_substeps for the span
+ * p_K - p_lo. JWL: 256 per unit of ln(p_K/p_lo) and at least 8, with p_lo
+ * kept at or above 1e-6 p_K. Other EOS: closed forms, no substeps. */
+static int rarefaction_substeps(const or_eos_t* q, const side_t* K, double p_lo) {
+  if (q->type == EOS_MG) return rk4_substeps(q, fmax(K->p - p_lo, 0.0));
+  if (q->type == EOS_JWL) {
+    double lo = fmax(p_lo, 1e-6 * K->p);
+    double nd = ceil(256.0 * log(K->p / lo));
+    return nd < 8.0 ? 8 : (int)nd;
+  }
+  return 0;
 }
 
 /* F(p) = f_L(p) + f_R(p) + (u_R - u_L), increasing in p. */
@@ -588,6 +614,10 @@ static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, c
   if (!st) st = make_side(qR, wR, &R);
   if (st) return st;
   double plow = fmax(eos_plow(qL), eos_plow(qR));
+  double ZL = L.rho * L.c, ZR = R.rho * R.c;
+  double pac = (ZR * L.p + ZL * R.p - ZL * ZR * (R.u - L.u)) / (ZL + ZR);
+  L.nrk = rarefaction_substeps(qL, &L, fmax(plow, fmin(R.p, pac)));
+  R.nrk = rarefaction_substeps(qR, &R, fmax(plow, fmin(L.p, pac)));
   double F, dF;
   /* Reading R36: no vacuum test with a JWL side (its rarefaction needs p > 0) */
   if (isfinite(plow) && R.u - L.u >= 0.0 && qL->type != EOS_JWL && qR->type != EOS_JWL) {

@@ -67,13 +67,21 @@ __device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w
 // material (otherwise first order, Reading R11); a non-admissible face state
 // makes the whole axis first order (Reading R12). bad: even the cell state is
 // not admissible.
-template <typename R>
+// The general kernels (GEN) take the limiter of the grid: lim = M2C_LIM_MC with
+// alpha, else van Albada.
+template <typename R, bool GEN = false>
 __device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], const R P[5], const R Pp[5], bool same,
-                                           FaceState<R>& Qm, FaceState<R>& Qp, bool& bad) {
+                                           FaceState<R>& Qm, FaceState<R>& Qp, bool& bad, int lim = 0,
+                                           R alpha = (R)0) {
   if (same) {
     R s[5];
+    if (GEN && lim == M2C_LIM_MC) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) s[v] = va_slope<R>(P[v] - Pm[v], Pp[v] - P[v]);
+      for (int v = 0; v < 5; ++v) s[v] = mc_slope<R>(P[v] - Pm[v], Pp[v] - P[v], alpha);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s[v] = va_slope<R>(P[v] - Pm[v], Pp[v] - P[v]);
+    }
     const R hf = (R)0.5;
     const bool okm = make_face<R>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2], P[3] - hf * s[3],
                                   P[4] - hf * s[4], Qm);

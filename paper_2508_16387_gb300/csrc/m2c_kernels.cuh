@@ -29,16 +29,17 @@ struct IfCell {
 // Control block of one grid, in the workspace.
 struct Ctrl {
   unsigned long long lam[2];  // bit pattern of max_cells sum_d (|V_d| + c), by step parity
-  int nface[2];               // interface faces of stage 1 / stage 2
-  int ncell[2];               // interface cells of stage 1 / stage 2
+  int nface[3];               // interface faces of the stages of a step (slot of list_slot())
+  int ncell[3];               // interface cells, by the same slots
   int nflip;                  // cells that changed material in the current step
   int err;                    // first latched m2c_status
+  int pad0;
   long long err_cell;
   double t;
   long long step;
   long long stat_faces, stat_cells, stat_flips;
   double stat_dt;
-  int pad[6];
+  int pad[4];
 };
 
 // Everything a kernel needs to know about one grid.
@@ -72,10 +73,42 @@ struct Grid {
   int reinit_every, reinit_iters;
   // M2C_MIXED only: 1 = the FIVER Newton iteration starts on FP32 wave curves
   // and finishes with FP64 steps (riemann_solve_mixed); 0 = FP64 throughout
-  int riemann_fp32_start, pad2;
+  int riemann_fp32_start;
+  // scheme options beyond the default (TVD RK2, modified van Albada, HLLC, CFL
+  // time step): general = 1 when any differs, which selects the general
+  // instantiation of the bulk kernel
+  int general;
+  int rk;             // Runge-Kutta order: 2 (TVD RK2), 3 (TVD RK3), 1 (forward Euler), Sec. 4.3
+  int limiter;        // M2C_LIM_VAN_ALBADA or M2C_LIM_MC (App. D)
+  int flux;           // M2C_FLUX_HLLC or M2C_FLUX_LLF (App. C)
+  int pad2;
+  double mc_alpha;    // alpha of the MC limiter
+  double dt_fixed;    // > 0: constant time step instead of the CFL rule
+  double* W2;         // TVD RK3: the second stage state (workspace)
+  double* phi2;
 };
 
-enum StageMode { kStage1 = 0, kStage2 = 1, kResidual = 2 };
+// Kernel modes: one Runge-Kutta stage each (the general bulk kernel only runs
+// kStage2of3 and kStage3), or the residual alone.
+//   kStage1     W1 = W + dt R(W)                                  (all schemes)
+//   kStage2     W' = (W + (W1 + dt R(W1))) / 2                    (RK2, last)
+//   kStage2of3  W2 = (3/4 W + 1/4 W1) + 1/4 dt R(W1)              (RK3)
+//   kStage3     W' = (1/3 W + 2/3 W2) + 2/3 dt R(W2)              (RK3, last)
+enum StageMode { kStage1 = 0, kStage2 = 1, kResidual = 2, kStage2of3 = 3, kStage3 = 4 };
+
+// The state a stage reads (its own cell and the stencil), its work-list slot,
+// and whether it is the last stage of a step (which writes the new state in
+// place, detects flips and reduces the next time step).
+__device__ __forceinline__ const double* stage_W(const Grid& g, int mode) {
+  return (mode == kStage2 || mode == kStage2of3) ? g.W1 : (mode == kStage3 ? g.W2 : g.W);
+}
+__device__ __forceinline__ const double* stage_phi(const Grid& g, int mode) {
+  return (mode == kStage2 || mode == kStage2of3) ? g.phi1 : (mode == kStage3 ? g.phi2 : g.phi);
+}
+__device__ __forceinline__ int list_slot(int mode) {
+  return (mode == kStage2 || mode == kStage2of3) ? 1 : (mode == kStage3 ? 2 : 0);
+}
+__device__ __forceinline__ bool last_stage(int mode) { return mode == kStage2 || mode == kStage3; }
 
 __device__ __forceinline__ int map_index(int i, int n, int lo_bc, int hi_bc) {
   if (i < 0) return lo_bc == M2C_BC_PERIODIC ? ((i % n) + n) % n : 0;
@@ -94,7 +127,10 @@ __device__ __forceinline__ void latch_error(Ctrl* c, int code, long long cell) {
   if (atomicCAS(&c->err, 0, code) == 0) c->err_cell = cell;
 }
 
+// Time step (Sec. 4.3): from the CFL number and the wave-speed maximum, or the
+// grid's constant time step.
 __device__ __forceinline__ double lam_to_dt(const Grid& g, unsigned long long bits) {
+  if (g.dt_fixed > 0.0) return g.dt_fixed;
   double lam = __longlong_as_double((long long)bits);
   return g.cfl * g.h / lam;
 }

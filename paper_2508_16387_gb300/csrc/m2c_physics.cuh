@@ -362,6 +362,17 @@ __device__ __forceinline__ R va_slope(R a, R b) {
   return rdiv<R>(ab * (a + b), a * a + b * b);
 }
 
+// Monotonized central slope (App. D, Eq. theta) on the uniform grid, written
+// without the division by b: sigma = phi(a/b) b with
+// phi = max(0, min(alpha theta, (theta + 1)/2, alpha)); the inequalities turn
+// for b < 0, and b = 0 gives 0.
+template <typename R>
+__device__ __forceinline__ R mc_slope(R a, R b, R alpha) {
+  if (b > (R)0) return fmax((R)0, fmin(fmin(alpha * a, (R)0.5 * (a + b)), alpha * b));
+  if (b < (R)0) return fmin((R)0, fmax(fmax(alpha * a, (R)0.5 * (a + b)), alpha * b));
+  return (R)0;
+}
+
 // A reconstructed face state with its sound speed and total energy per mass.
 template <typename R>
 struct FaceState {
@@ -422,12 +433,41 @@ __device__ __forceinline__ void hllc(const FaceState<R>& L, const FaceState<R>& 
   for (int v = 0; v < 5; ++v) F[v] = F[v] + SK * (ws[v] - wk[v]);
 }
 
+// Local Lax-Friedrichs flux (App. C.1, Eq. Lax-Friedrichs):
+// F = (F(W_L) + F(W_R))/2 - lambda (W_R - W_L)/2 with
+// lambda = max(|u_L| + c_L, |u_R| + c_R), u the normal velocities.
+template <int D, typename R>
+__device__ __forceinline__ void llf(const FaceState<R>& L, const FaceState<R>& Rt, R F[5]) {
+  const R lam = fmax(fabs(comp<D>(L)) + L.c, fabs(comp<D>(Rt)) + Rt.c);
+  R FL[5], FR[5];
+  phys_flux<D>(L, FL);
+  phys_flux<D>(Rt, FR);
+  const R wL[5] = {L.rho, L.rho * L.u, L.rho * L.v, L.rho * L.w, L.rho * L.E};
+  const R wR[5] = {Rt.rho, Rt.rho * Rt.u, Rt.rho * Rt.v, Rt.rho * Rt.w, Rt.rho * Rt.E};
+  const R hl = (R)0.5 * lam;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) F[v] = (R)0.5 * (FL[v] + FR[v]) - hl * (wR[v] - wL[v]);
+}
+
+// The grid's numerical flux: HLLC, or (general kernels, flux = M2C_FLUX_LLF) LLF.
+template <int D, typename R, bool GEN>
+__device__ __forceinline__ void num_flux(const FaceState<R>& L, const FaceState<R>& Rt, R F[5], int flux) {
+  if constexpr (GEN) {
+    if (flux == M2C_FLUX_LLF) {
+      llf<D, R>(L, Rt, F);
+      return;
+    }
+  }
+  hllc<D, R>(L, Rt, F);
+}
+
 // ---------------------------------------------------------------------------
 // Exact two-material Riemann problem (Sec. 4.2, Eq. 1DRiemannProblem with the
 // interface conditions of Sec. 3.5.1), FP64. Newton on p* from the PVRS guess,
 // stop when |dp| <= 1e-12 |p| and take one more step; 50 steps then bisection.
 // SG wave curves in closed form; MG shock from the Hugoniot root, MG
-// rarefaction by RK4 on 64 equal pressure substeps.
+// rarefaction by RK4 on equal pressure substeps whose number is fixed once
+// per problem (fix_substeps) from a bound of the wave's pressure span.
 // ---------------------------------------------------------------------------
 constexpr double kNewtonTol = 1e-12;
 constexpr int kNewtonCap = 50;
@@ -438,6 +478,7 @@ constexpr int kRk4Steps = 64;
 
 struct Side {
   double rho, u, p, c, e;
+  int nrk;  // RK4 substeps of this side's MG rarefaction curve in one problem; 0: per evaluation
 };
 
 __device__ inline bool make_side(const EosDev& q, double rho, double u, double p, Side& K) {
@@ -449,12 +490,38 @@ __device__ inline bool make_side(const EosDev& q, double rho, double u, double p
   K.p = p;
   K.c = sqrt(c2);
   K.e = e;
+  K.nrk = 0;
   return true;
 }
 
 __device__ inline double eos_plow(const EosDev& q) {
   if (q.type == M2C_EOS_SG) return -q.pc;
   return isfinite(q.eta_min) ? q.pmin : -INFINITY;
+}
+
+// Equal RK4 substeps over a pressure span dp of an MG isentrope: 64 for a span
+// of at least 5% of K0 = rho0 c0^2, proportionally fewer (at least one) below.
+__device__ inline int mg_substeps(const EosDev& q, double dp) {
+  double nsd = ceil(__ddiv_rn(kRk4Steps * fabs(dp), q.rk4_span));
+  nsd = nsd >= 1.0 ? (nsd > kRk4Steps ? (double)kRk4Steps : nsd) : 1.0;
+  return (int)nsd;
+}
+
+// The substep count of each MG side's rarefaction curve, fixed once per
+// problem before the iteration so that the curve is one smooth function of p:
+// the count for an upper bound of the pressure drop across the wave,
+// p_K - max(p_low, min(p_J, p_ac)), with the acoustic estimate
+// p_ac = (Z_R p_L + Z_L p_R - Z_L Z_R (u_R - u_L)) / (Z_L + Z_R), Z = rho c
+// (a shock on the other side J keeps p* above p_J; a rarefaction there too
+// keeps p* above p_ac, since each rarefaction curve lies below its acoustic
+// tangent). Written without contracted multiply-adds.
+__device__ inline void fix_substeps(const EosDev& qL, Side& L, const EosDev& qR, Side& Rs, double plow) {
+  const double ZL = __dmul_rn(L.rho, L.c), ZR = __dmul_rn(Rs.rho, Rs.c);
+  const double num = __dsub_rn(__dadd_rn(__dmul_rn(ZR, L.p), __dmul_rn(ZL, Rs.p)),
+                               __dmul_rn(__dmul_rn(ZL, ZR), __dsub_rn(Rs.u, L.u)));
+  const double pac = __ddiv_rn(num, __dadd_rn(ZL, ZR));
+  if (qL.type == M2C_EOS_MG) L.nrk = mg_substeps(qL, fmax(__dsub_rn(L.p, fmax(plow, fmin(Rs.p, pac))), 0.0));
+  if (qR.type == M2C_EOS_MG) Rs.nrk = mg_substeps(qR, fmax(__dsub_rn(Rs.p, fmax(plow, fmin(L.p, pac))), 0.0));
 }
 
 __device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
@@ -557,10 +624,8 @@ __device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& 
     if (drs) *drs = drdp;
     return M2C_OK;
   }
-  // equal substeps, 64 for an interval of at least 5% of K0, fewer (>= 1) for weaker waves
-  double nsd = ceil(kRk4Steps * fabs(p - K.p) / q.rk4_span);
-  nsd = nsd >= 1.0 ? (nsd > kRk4Steps ? (double)kRk4Steps : nsd) : 1.0;
-  const int ns = (int)nsd;
+  // equal substeps: fixed for the problem (fix_substeps), else chosen for this span
+  const int ns = K.nrk > 0 ? K.nrk : mg_substeps(q, p - K.p);
   const double hs = (p - K.p) / ns;
   double rho = K.rho, fv = 0.0;
   for (int i = 0; i < ns; ++i) {
@@ -619,6 +684,7 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
   iters = 0;
   if (!make_side(qL, rl, ul, pl, L) || !make_side(qR, rr, ur, pr, Rs)) return M2C_ENONPHYS;
   const double plow = fmax(eos_plow(qL), eos_plow(qR));
+  fix_substeps(qL, L, qR, Rs, plow);
   double F, dF;
   int st;
   // vacuum test (F(p_low) >= 0); both wave curves increase with p and vanish at
@@ -709,7 +775,7 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
 // a stiff MG material, |p - p_K| <= 1e-5 rho_K c_K^2, take the acoustic
 // curve, which is all an FP32 start can resolve there), then one FP64 Newton
 // step from the FP32 root on the FP64 wave curves (two if the first moves p by
-// more than 1e-7 |p|) gives p*; u* and the star densities follow from the last
+// more than 1e-9 |p|) gives p*; u* and the star densities follow from the last
 // FP64 evaluation to first order in the step. An FP32 failure, a vacuum
 // signal, a slope that is not finite, or a step larger than 1e-5 |p| leaves
 // the problem to the FP64 iteration above.
@@ -890,6 +956,7 @@ static __device__ __noinline__ int riemann_solve_mixed(const EosP<float>& qLf, c
   if (riemann_newton_f(qLf, d2f(rl), d2f(ul), d2f(pl), qRf, d2f(rr), d2f(ur), d2f(pr), p32, it32) &&
       make_side(qL, rl, ul, pl, L) && make_side(qR, rr, ur, pr, Rs)) {
     const double plow = fmax(eos_plow(qL), eos_plow(qR));
+    fix_substeps(qL, L, qR, Rs, plow);
     double p = f2d(p32);
     for (int k = 0; k < 2; ++k) {
       double fL, dfL, rL, dL = 0.0, fR, dfR, rR, dR = 0.0;
@@ -901,7 +968,7 @@ static __device__ __noinline__ int riemann_solve_mixed(const EosP<float>& qLf, c
       if (!(isfinite(dF) && dF > 0.0 && isfinite(dL) && isfinite(dR) && fabs(dp) <= 1e-5 * fabs(p) &&
             p + dp > plow))
         break;
-      if (k == 1 || fabs(dp) <= 1e-7 * fabs(p)) {
+      if (k == 1 || fabs(dp) <= 1e-9 * fabs(p)) {
         out.p = p + dp;
         out.u = 0.5 * (L.u + Rs.u) + 0.5 * (fR - fL) + 0.5 * (dfR - dfL) * dp;
         out.rhoL = rL + dL * dp;

@@ -43,7 +43,12 @@ namespace m2c {
 template <int D>
 __device__ __forceinline__ void fiver_fluxes(const FaceState<double>& A, const FaceState<double>& SA,
                                              const FaceState<double>& SB, const FaceState<double>& B, double Fa[5],
-                                             double Fb[5]) {
+                                             double Fb[5], int flux) {
+  if (flux == M2C_FLUX_LLF) {
+    llf<D, double>(A, SA, Fa);
+    llf<D, double>(SB, B, Fb);
+    return;
+  }
   hllc<D, double>(A, SA, Fa);
   hllc<D, double>(SB, B, Fb);
 }
@@ -54,9 +59,9 @@ constexpr int kFiverThreads = 32;
 __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restrict__ grids, int mode) {
   const Grid& G = grids[blockIdx.y];
   Ctrl* ctrl = G.ctrl;
-  const int slot = mode == kStage2 ? 1 : 0;
+  const int slot = list_slot(mode);
   const int n = min(ctrl->nface[slot], G.face_cap);
-  const double* __restrict__ Ws = mode == kStage2 ? G.W1 : G.W;
+  const double* __restrict__ Ws = stage_W(G, mode);
   const long long N = G.N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const IfFace f = G.faces[i];
@@ -109,9 +114,9 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
       okf = make_face<double>(qb, Sb[0], Sb[1], Sb[2], Sb[3], Sb[4], SB) && okf;
       okf = make_face<double>(qb, Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], B) && okf;
       if (!okf) st = M2C_ENONPHYS;
-      if (d == 0) fiver_fluxes<0>(A, SA, SB, B, Fa, Fb);
-      else if (d == 1) fiver_fluxes<1>(A, SA, SB, B, Fa, Fb);
-      else fiver_fluxes<2>(A, SA, SB, B, Fa, Fb);
+      if (d == 0) fiver_fluxes<0>(A, SA, SB, B, Fa, Fb, G.flux);
+      else if (d == 1) fiver_fluxes<1>(A, SA, SB, B, Fa, Fb, G.flux);
+      else fiver_fluxes<2>(A, SA, SB, B, Fa, Fb, G.flux);
     }
     if (st != M2C_OK) {
       latch_error(ctrl, st, ca);
@@ -134,12 +139,13 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
 }
 
 // Interface cells: residual from the six stored face fluxes in the fixed
-// association ((x) + (y)) + (z), then the stage update.
+// association ((x) + (y)) + (z), then the stage update of the mode (the same
+// formulas as the bulk kernel's).
 __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, int mode) {
   __shared__ double s_red[32];
   const Grid& G = grids[blockIdx.y];
   Ctrl* ctrl = G.ctrl;
-  const int slot = mode == kStage2 ? 1 : 0;
+  const int slot = list_slot(mode);
   const int n = min(ctrl->ncell[slot], G.cell_cap);
   const long long N = G.N;
   const long long step = ctrl->step;
@@ -159,9 +165,19 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
     } else if (mode == kStage1) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) G.W1[v * N + c] = G.W[v * N + c] + dt * res[v];
-    } else {
+    } else if (mode == kStage2of3) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * res[v]));
+      for (int v = 0; v < 5; ++v)
+        G.W2[v * N + c] = (0.75 * G.W[v * N + c] + 0.25 * G.W1[v * N + c]) + 0.25 * dt * res[v];
+    } else {
+      if (mode == kStage3) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          G.W[v * N + c] = (G.W[v * N + c] / 3.0 + 2.0 / 3.0 * G.W2[v * N + c]) + 2.0 / 3.0 * dt * res[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) G.W[v * N + c] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * res[v]));
+      }
       const int id0 = G.id[c] & 1;
       const bool flip = lt0(G.phi[c]) != (id0 == 1);
       if (!flip) {
@@ -172,7 +188,38 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
       }
     }
   }
-  if (mode == kStage2) block_max_to(lam_max, &ctrl->lam[(step + 1) & 1], s_red);
+  if (last_stage(mode)) block_max_to(lam_max, &ctrl->lam[(step + 1) & 1], s_red);
+}
+
+// Forward Euler (Sec. 4.3): the one stage wrote W1 = W + dt R(W); the step
+// takes it as the new state, detects the cells whose level set changed sign
+// and reduces the next time step, as the last stage of the other schemes does.
+__global__ void __launch_bounds__(256) k_commit_euler(const Grid* __restrict__ grids) {
+  __shared__ double s_red[32];
+  const Grid& G = grids[blockIdx.y];
+  Ctrl* ctrl = G.ctrl;
+  const long long N = G.N;
+  double lam_max = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) G.W[v * N + c] = G.W1[v * N + c];
+    const double pn = G.phi1[c];
+    G.phi[c] = pn;
+    const int id0 = G.id[c] & 1;
+    const bool neg = lt0(pn);
+    G.id[c] = (uint8_t)(id0 | (neg ? 4 : 0));
+    if (neg != (id0 == 1)) {
+      const int s = atomicAdd(&ctrl->nflip, 1);
+      if (s < G.flip_cap) G.flips[s] = c;
+      else latch_error(ctrl, M2C_EOVERFLOW, c);
+    } else {
+      bool ok;
+      const double lam = wave_sum(G, id0, G.W, N, c, ok);
+      if (!ok) latch_error(ctrl, M2C_ENONPHYS, c);
+      lam_max = fmax(lam_max, lam);
+    }
+  }
+  block_max_to(lam_max, &ctrl->lam[(ctrl->step + 1) & 1], s_red);
 }
 
 // ---------------------------------------------------------------------------
@@ -351,8 +398,8 @@ __global__ void k_end_step(const Grid* __restrict__ grids, int ngrid) {
   c->stat_faces = c->nface[0];
   c->stat_cells = c->ncell[0];
   c->stat_flips = c->nflip;
-  c->nface[0] = c->nface[1] = 0;
-  c->ncell[0] = c->ncell[1] = 0;
+  c->nface[0] = c->nface[1] = c->nface[2] = 0;
+  c->ncell[0] = c->ncell[1] = c->ncell[2] = 0;
   c->nflip = 0;
   c->lam[s & 1] = 0ull;  // slot of step s + 2
   c->step = s + 1;
@@ -457,6 +504,7 @@ struct m2c_ctx {
   long long host_step;
   bool has_state, eos_set[2], dirty, lam_valid;
   bool profiling, profile_bulk_only;
+  size_t ws_bytes;      // size of the caller's workspace
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pairs around launches while profiling
   std::vector<int> ev_kind;
   size_t ev_used;
@@ -469,11 +517,13 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t grid, tiles, ctrl, W1, phi1, phiC, id, slot, faces, cells, flips, total;
+  size_t grid, tiles, ctrl, W1, phi1, phiC, id, slot, faces, cells, flips, W2, phi2, total;
   int face_cap, cell_cap, flip_cap;
 };
 
-Layout layout_for(long long N) {
+// rk = 3 appends the second stage state of TVD RK3 (W2, phi2) to the layout of
+// the other schemes, which stays a prefix.
+Layout layout_for(long long N, int rk = 2) {
   Layout L{};
   L.face_cap = (int)std::min<long long>(std::max<long long>(4096, N / 4), 1ll << 30);
   L.cell_cap = (int)std::min<long long>(std::max<long long>(2048, N / 8), 1ll << 30);
@@ -490,6 +540,11 @@ Layout layout_for(long long N) {
   L.faces = o; o = align_up(o + sizeof(IfFace) * (size_t)L.face_cap);
   L.cells = o; o = align_up(o + sizeof(IfCell) * (size_t)L.cell_cap);
   L.flips = o; o = align_up(o + sizeof(long long) * (size_t)L.flip_cap);
+  L.W2 = L.phi2 = 0;
+  if (rk == 3) {
+    L.W2 = o; o = align_up(o + sizeof(double) * 5 * N);
+    L.phi2 = o; o = align_up(o + sizeof(double) * N);
+  }
   L.total = o;
   return L;
 }
@@ -549,8 +604,10 @@ m2c_status cuda_check(m2c_ctx* c, cudaError_t e, const char* what) {
   return set_err(c, M2C_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// gen: the general instantiation (8-row tiles), for grids with scheme options.
 cudaError_t launch_stage(int prec, const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
-                         const LaunchPlan& lp, cudaStream_t s) {
+                         const LaunchPlan& lp, cudaStream_t s, bool gen = false) {
+  if (gen) return launch_stage_gen(prec, grids, tiles, ngrid, ntiles, mode, lp, s);
   if (prec == M2C_FP64) return launch_stage_fp64(grids, tiles, ngrid, ntiles, mode, lp, s);
   return launch_stage_fp32(grids, tiles, ngrid, ntiles, mode, lp, s);
 }
@@ -558,6 +615,7 @@ cudaError_t launch_stage(int prec, const Grid* grids, const long long* tiles, in
 void setup_all_stage_kernels() {
   setup_stage_fp64();
   setup_stage_fp32();
+  setup_stage_gen();
 }
 
 }  // namespace
@@ -667,9 +725,11 @@ cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s, int kind = 
 
 // reinit: enqueue the reinitialisation kernels (each grid decides on the device
 // whether its own step is due); reinit_iters: the largest iteration count.
+// rk: the Runge-Kutta scheme of all grids (Sec. 4.3); gen: launch the general
+// bulk kernel.
 cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int ngrid, long long ntiles, int prec,
                          const LaunchPlan& lp, bool reinit, int reinit_iters, long long nmax, cudaStream_t s,
-                         StageEvents* pe = nullptr) {
+                         StageEvents* pe = nullptr, int rk = 2, bool gen = false) {
   cudaError_t e;
   const dim3 lg((unsigned)(2 * sm_count()), (unsigned)ngrid);
   const dim3 fg((unsigned)(8 * sm_count()), (unsigned)ngrid);
@@ -680,11 +740,20 @@ cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;          \
     if ((e = record_pair(pe, false, s)) != cudaSuccess) return e;   \
   } while (0)
-  for (int stage = 0; stage < 2; ++stage) {
-    const int mode = stage == 0 ? kStage1 : kStage2;
-    M2C_TIMED(kKStage, e = launch_stage(prec, dev_grids, dev_tiles, ngrid, ntiles, mode, lp, s); if (e) return e);
+  static const int kModesRk1[1] = {kStage1};
+  static const int kModesRk2[2] = {kStage1, kStage2};
+  static const int kModesRk3[3] = {kStage1, kStage2of3, kStage3};
+  const int* modes = rk == 1 ? kModesRk1 : (rk == 3 ? kModesRk3 : kModesRk2);
+  const int nstage = rk == 1 ? 1 : (rk == 3 ? 3 : 2);
+  for (int stage = 0; stage < nstage; ++stage) {
+    const int mode = modes[stage];
+    M2C_TIMED(kKStage, e = launch_stage(prec, dev_grids, dev_tiles, ngrid, ntiles, mode, lp, s, gen); if (e) return e);
     M2C_TIMED(kKFiver, (k_fiver<<<fg, kFiverThreads, 0, s>>>(dev_grids, mode)));
     M2C_TIMED(kKFinish, (k_finish<<<lg, 128, 0, s>>>(dev_grids, mode)));
+  }
+  if (rk == 1) {
+    const dim3 cg((unsigned)std::min<long long>((nmax + 255) / 256, 8ll * sm_count()), (unsigned)ngrid);
+    M2C_TIMED(kKFinish, (k_commit_euler<<<cg, 256, 0, s>>>(dev_grids)));
   }
   if (reinit && reinit_iters > 0) {
     const dim3 rg((unsigned)std::min<long long>((nmax + 255) / 256, 8ll * sm_count()), (unsigned)ngrid);
@@ -716,6 +785,7 @@ static cudaError_t ensure_lam(m2c_ctx* c) {
 namespace {
 
 double lam_to_dt_host(const Grid& g, unsigned long long bits) {
+  if (g.dt_fixed > 0.0) return g.dt_fixed;
   double lam;
   std::memcpy(&lam, &bits, sizeof(lam));
   return lam > 0.0 ? g.cfl * g.h / lam : 0.0;
@@ -736,6 +806,8 @@ struct m2c_batch {
   cudaStream_t stream = nullptr;
   long long step = 0, nmax = 1;
   int reinit_every = 10, reinit_iters = 5, graph_steps = 0;
+  int rk = 2;        // Runge-Kutta scheme of every grid
+  bool gen = false;  // some grid has scheme options: the general bulk kernel
 };
 
 extern "C" {
@@ -759,6 +831,12 @@ size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision) {
   (void)precision;
   if (nx < 1 || ny < 1 || nz < 1) return 0;
   return layout_for((long long)nx * ny * nz).total;
+}
+
+size_t m2c_workspace_bytes_rk(int nx, int ny, int nz, int precision, int rk) {
+  (void)precision;
+  if (nx < 1 || ny < 1 || nz < 1 || rk < 1 || rk > 3) return 0;
+  return layout_for((long long)nx * ny * nz, rk).total;
 }
 
 m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[3], double h, const int bc[6],
@@ -795,6 +873,18 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   g.flips = reinterpret_cast<long long*>(ws + L.flips);
   g.face_cap = L.face_cap; g.cell_cap = L.cell_cap; g.flip_cap = L.flip_cap;
   g.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  g.rk = 2;
+  g.limiter = M2C_LIM_VAN_ALBADA;
+  g.flux = M2C_FLUX_HLLC;
+  g.mc_alpha = 1.2;
+  g.dt_fixed = 0.0;
+  g.general = 0;
+  const Layout L3 = layout_for(N, 3);
+  if (ws_bytes >= L3.total) {  // room for the second stage state of TVD RK3
+    g.W2 = reinterpret_cast<double*>(ws + L3.W2);
+    g.phi2 = reinterpret_cast<double*>(ws + L3.phi2);
+  }
+  c->ws_bytes = ws_bytes;
   c->dev_grid = reinterpret_cast<Grid*>(ws + L.grid);
   c->dev_tiles = reinterpret_cast<long long*>(ws + L.tiles);
   c->stream = static_cast<cudaStream_t>(stream);
@@ -849,6 +939,32 @@ m2c_status m2c_set_scheme(m2c_ctx* c, double cfl, int reinit_every, int reinit_i
   return push_grid(c);
 }
 
+m2c_status m2c_set_options(m2c_ctx* c, const m2c_options* o) {
+  if (!c) return M2C_EINVAL;
+  if (!o) return set_err(c, M2C_EINVAL, "options are NULL");
+  if (o->rk < 1 || o->rk > 3) return set_err(c, M2C_EINVAL, "rk must be 1, 2 or 3");
+  if (o->limiter != M2C_LIM_VAN_ALBADA && o->limiter != M2C_LIM_MC) return set_err(c, M2C_EINVAL, "unknown limiter");
+  if (o->flux != M2C_FLUX_HLLC && o->flux != M2C_FLUX_LLF) return set_err(c, M2C_EINVAL, "unknown flux");
+  if (o->limiter == M2C_LIM_MC && !(o->mc_alpha >= 1.0 && o->mc_alpha <= 2.0))
+    return set_err(c, M2C_EINVAL, "the MC limiter needs 1 <= alpha <= 2");
+  if (!(o->dt_fixed >= 0.0) || !std::isfinite(o->dt_fixed)) return set_err(c, M2C_EINVAL, "dt_fixed must be >= 0");
+  if (o->rk == 3 && !c->host.W2)
+    return set_err(c, M2C_ENOMEM, "TVD RK3 needs a workspace of m2c_workspace_bytes_rk(nx, ny, nz, precision, 3)");
+  Grid& g = c->host;
+  g.rk = o->rk;
+  g.limiter = o->limiter;
+  g.flux = o->flux;
+  g.mc_alpha = o->limiter == M2C_LIM_MC ? o->mc_alpha : 1.2;
+  g.dt_fixed = o->dt_fixed;
+  g.general = (g.rk == 3 || g.limiter != M2C_LIM_VAN_ALBADA || g.flux != M2C_FLUX_HLLC) ? 1 : 0;
+  if (g.general && c->ty != 8) {  // the general kernel runs 8-row tiles
+    c->ty = 8;
+    set_tiling(g, 8, default_tz(g, 8));
+  }
+  c->lam_valid = false;  // a constant time step replaces the reduced one from the next step
+  return push_grid(c);
+}
+
 m2c_status m2c_set_riemann_start(m2c_ctx* c, int fp32_start) {
   if (!c || (fp32_start != 0 && fp32_start != 1)) return M2C_EINVAL;
   if (fp32_start && c->host.prec != M2C_MIXED)
@@ -860,6 +976,8 @@ m2c_status m2c_set_riemann_start(m2c_ctx* c, int fp32_start) {
 m2c_status m2c_set_tiling(m2c_ctx* c, int tile_rows, int tile_z) {
   if (!c || (tile_rows != 4 && tile_rows != 8 && tile_rows != 16) || tile_z < 0) return M2C_EINVAL;
   if (tile_rows == 16 && c->host.prec == M2C_FP64) return set_err(c, M2C_EINVAL, "FP64 tiles have 4 or 8 rows");
+  if (c->host.general && tile_rows != 8)
+    return set_err(c, M2C_EINVAL, "grids with scheme options run 8-row tiles");
   c->ty = tile_rows;
   set_tiling(c->host, c->ty, tile_z > 0 ? tile_z : default_tz(c->host, c->ty));
   return push_grid(c);
@@ -941,7 +1059,8 @@ m2c_status m2c_step(m2c_ctx* c, int nsteps) {
     LaunchPlan lp;
     lp.ty = c->ty;
     cudaError_t e = enqueue_step(c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), c->host.prec, lp, re,
-                                 c->reinit_iters, c->host.N, c->stream, c->profiling ? &pe : nullptr);
+                                 c->reinit_iters, c->host.N, c->stream, c->profiling ? &pe : nullptr, c->host.rk,
+                                 c->host.general != 0);
     if (e != cudaSuccess) return cuda_check(c, e, "step launch");
     ++c->host_step;
   }
@@ -960,7 +1079,10 @@ m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace
   for (int i = 0; i < k; ++i) {
     if (!v[i] || !v[i]->has_state) return M2C_EINVAL;
     if (v[i]->host.prec != v[0]->host.prec) return set_err(v[0], M2C_EINVAL, "one precision per batch");
+    if (v[i]->host.rk != v[0]->host.rk) return set_err(v[0], M2C_EINVAL, "one Runge-Kutta scheme per batch");
   }
+  bool gen = false;
+  for (int i = 0; i < k; ++i) gen = gen || v[i]->host.general != 0;
   int ty = 8, tz = 0, sched = 0, bpsm = 0;
   if (tuning) {
     ty = tuning[0] == 4 ? 4 : (tuning[0] == 16 && v[0]->host.prec == M2C_MIXED ? 16 : 8);
@@ -968,6 +1090,7 @@ m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace
     sched = tuning[2] == 1 ? 1 : 0;
     bpsm = std::max(0, tuning[3]);
   }
+  if (gen) ty = 8;  // the general kernel runs 8-row tiles
   m2c_batch* b = new (std::nothrow) m2c_batch();
   if (!b) return M2C_ENOMEM;
   // largest grids first, so that the longest tiles start early
@@ -995,6 +1118,8 @@ m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace
   b->lp.blocks_per_sm = bpsm;
   b->lp.counter = b->counter;
   b->prec = v[0]->host.prec;
+  b->rk = v[0]->host.rk;
+  b->gen = gen;
   b->stream = v[0]->stream;
   b->step = v[0]->host_step;
   b->reinit_every = v[0]->reinit_every;
@@ -1028,7 +1153,7 @@ static m2c_status batch_enqueue(m2c_batch* b, int nsteps, cudaStream_t s) {
     // grids of a batch may be at different steps: the reinitialisation kernels
     // are enqueued every step and each grid checks its own schedule
     cudaError_t e = enqueue_step(b->dev, b->dtiles, k, b->tiles[k], b->prec, b->lp, b->reinit_iters > 0,
-                                 b->reinit_iters, b->nmax, s);
+                                 b->reinit_iters, b->nmax, s, nullptr, b->rk, b->gen);
     if (e != cudaSuccess) return cuda_check(b->ctx[0], e, "batch step launch");
     ++b->step;
     for (m2c_ctx* c : b->ctx) ++c->host_step;
@@ -1094,15 +1219,15 @@ m2c_status m2c_residual(m2c_ctx* c, double* R, double* L) {
   LaunchPlan lp;
   lp.ty = c->ty;
   cudaError_t e = launch_stage(c->host.prec, c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), kResidual, lp,
-                               c->stream);
+                               c->stream, c->host.general != 0);
   if (e == cudaSuccess) {
     const dim3 lg((unsigned)(2 * sm_count()), 1);
     k_fiver<<<dim3((unsigned)(8 * sm_count()), 1), kFiverThreads, 0, c->stream>>>(c->dev_grid, kResidual);
     k_finish<<<lg, 128, 0, c->stream>>>(c->dev_grid, kResidual);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(&c->host.ctrl->nface[0], 0, 2 * sizeof(int), c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&c->host.ctrl->ncell[0], 0, 2 * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->host.ctrl->nface[0], 0, 3 * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->host.ctrl->ncell[0], 0, 3 * sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return cuda_check(c, e, "residual");
 }

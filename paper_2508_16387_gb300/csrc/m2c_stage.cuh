@@ -45,7 +45,11 @@ struct StageSmem {
 // the plane index changes along the march. The halo slots are computed once,
 // the face-state and flux items are recomputed from the thread index where
 // they are used (cheaper than holding them in registers across the march).
-template <typename R, int TY>
+//
+// GEN = false is the default scheme (TVD RK2, modified van Albada, HLLC); GEN =
+// true is the general instantiation, which takes the grid's scheme options at
+// run time (limiter, flux, the stages of TVD RK3) at some cost in registers.
+template <typename R, int TY, bool GEN>
 __global__ void __launch_bounds__(32 * TY, (sizeof(R) == 8 ? 1 : 1024 / (32 * TY)))
 k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, long long ntiles, int mode,
         int sched, unsigned long long* __restrict__ tile_counter) {
@@ -155,11 +159,16 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   const int x0 = bx * TX, y0 = by * TY, k0 = bz * G.tz, k1 = min(k0 + G.tz, nz);
   const R ih = (R)G.inv_h;
   const R i6h = (R)(1.0 / (6.0 * G.h));
-  const double* __restrict__ Ws = mode == kStage2 ? G.W1 : G.W;
-  const double* __restrict__ phis = mode == kStage2 ? G.phi1 : G.phi;
+  const double* __restrict__ Ws = GEN ? stage_W(G, mode) : (mode == kStage2 ? G.W1 : G.W);
+  const double* __restrict__ phis = GEN ? stage_phi(G, mode) : (mode == kStage2 ? G.phi1 : G.phi);
   const uint8_t* __restrict__ idg = G.id;
   Ctrl* ctrl = G.ctrl;
-  const int slot = mode == kStage2 ? 1 : 0;
+  const int slot = GEN ? list_slot(mode) : (mode == kStage2 ? 1 : 0);
+  // material ids are frozen after the first stage of a step
+  const bool ids_frozen = GEN ? (mode != kStage1 && mode != kResidual) : mode == kStage2;
+  const bool final_stage = GEN ? last_stage(mode) : mode == kStage2;
+  const int lim = GEN ? G.limiter : 0, flx = GEN ? G.flux : 0;
+  const R alpha = GEN ? (R)G.mc_alpha : (R)0;
   const long long step = ctrl->step;
 
   if (tid < 2) {
@@ -187,7 +196,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   // material at the start of the step and the stage state of cell index c
   auto load = [&](long long c, R P[5], R& ph, int& idv) {
     const double phd = phis[c];
-    if (mode == kStage2) {
+    if (ids_frozen) {
       idv = idg[c] & 1;
     } else {
       idv = lt0(phd) ? 1 : 0;
@@ -211,10 +220,10 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     load(plane(k0) + own_base, P0, ph[2], id0);
     load(plane(k0 + 1) + own_base, P1, ph[3], id1);
     FaceState<R> QaP, Q0M;
-    cell_faces<R>(s_eos[ida], Pb, Pa, P0, idb == ida && id0 == ida, Qtmp, QaP, bad);
-    cell_faces<R>(s_eos[id0], Pa, P0, P1, ida == id0 && id1 == id0, Q0M, QzP, bad);
+    cell_faces<R, GEN>(s_eos[ida], Pb, Pa, P0, idb == ida && id0 == ida, Qtmp, QaP, bad, lim, alpha);
+    cell_faces<R, GEN>(s_eos[id0], Pa, P0, P1, ida == id0 && id1 == id0, Q0M, QzP, bad, lim, alpha);
     if (ida == id0) {
-      hllc<2, R>(QaP, Q0M, Fzm);
+      num_flux<2, R, GEN>(QaP, Q0M, Fzm, flx);
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fzm[v] = (R)0;
@@ -232,9 +241,9 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     uint8_t* const s_id = s_id0 + buf * PL;
     // ---- own column: plane k+2, z face states of cell k+1, z flux of face k+1/2
     load(plane(k + 2) + own_base, P2, ph[4], id2);
-    cell_faces<R>(s_eos[id1], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad);
+    cell_faces<R, GEN>(s_eos[id1], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad, lim, alpha);
     if (id0 == id1) {
-      hllc<2, R>(QzP, QzM1, Fzp);
+      num_flux<2, R, GEN>(QzP, QzM1, Fzp, flx);
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fzp[v] = (R)0;
@@ -275,7 +284,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       const bool same = s_id[c0 - so] == ic && s_id[c0 + so] == ic;
       bool b = false;
       FaceState<R>* out = s_st + 2 * (tid + s * NT);
-      cell_faces<R>(s_eos[ic], Pm, P, Pp, same, out[0], out[1], b);
+      cell_faces<R, GEN>(s_eos[ic], Pm, P, Pp, same, out[0], out[1], b, lim, alpha);
       bad = bad || b;
     }
     __syncthreads();
@@ -296,9 +305,9 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
 #pragma unroll
         for (int v = 0; v < 5; ++v) F[v] = (R)0;
       } else if (dir == 0) {
-        hllc<0, R>(QL, QR, F);
+        num_flux<0, R, GEN>(QL, QR, F, flx);
       } else {
-        hllc<1, R>(QL, QR, F);
+        num_flux<1, R, GEN>(QL, QR, F, flx);
       }
       R* o = (dir ? s_fy : s_fx) + outo;
       const int stride = dir ? SFY : SFX;
@@ -352,8 +361,20 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
 #pragma unroll
             for (int v = 0; v < 5; ++v) G.W1[v * N + c] = G.W[v * N + c] + dt * to_d<R>(res[v]);
           }
+        } else if (GEN && mode == kStage2of3) {
+          // TVD RK3, second stage (Sec. 4.3): W2 = (3/4 W + 1/4 W1) + 1/4 dt R(W1)
+          G.phi2[c] = (0.75 * G.phi[c] + 0.25 * G.phi1[c]) + 0.25 * dt * to_d<R>(Lphi);
+          if (!is_if) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+              G.W2[v * N + c] = (0.75 * G.W[v * N + c] + 0.25 * G.W1[v * N + c]) + 0.25 * dt * to_d<R>(res[v]);
+          }
         } else {
-          const double pn = 0.5 * (G.phi[c] + (G.phi1[c] + dt * to_d<R>(Lphi)));
+          // last stage: TVD RK2 W' = (W + (W1 + dt R(W1)))/2, or TVD RK3
+          // W' = (1/3 W + 2/3 W2) + 2/3 dt R(W2)
+          const bool rk3 = GEN && mode == kStage3;
+          const double pn = rk3 ? (G.phi[c] / 3.0 + 2.0 / 3.0 * G.phi2[c]) + 2.0 / 3.0 * dt * to_d<R>(Lphi)
+                                : 0.5 * (G.phi[c] + (G.phi1[c] + dt * to_d<R>(Lphi)));
           G.phi[c] = pn;
           const bool neg = lt0(pn);
           flip = neg != (id0 == 1);
@@ -363,7 +384,8 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
             double wn[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              wn[v] = 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * to_d<R>(res[v])));
+              wn[v] = rk3 ? (G.W[v * N + c] / 3.0 + 2.0 / 3.0 * G.W2[v * N + c]) + 2.0 / 3.0 * dt * to_d<R>(res[v])
+                          : 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * to_d<R>(res[v])));
               G.W[v * N + c] = wn[v];
             }
             if (!flip) {
@@ -435,7 +457,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
             }
           }
         }
-        if (mode == kStage2) {
+        if (final_stage) {
           const unsigned m = __ballot_sync(0xffffffffu, flip);
           if (m) {
             int base = 0;
@@ -467,26 +489,27 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   // failures are latched once per tile, with the thread's column at the tile's first plane
   if (bad) latch_error(ctrl, M2C_ENONPHYS, cell_of(G, gx, gy, k0));
   if (ovf) latch_error(ctrl, M2C_EOVERFLOW, cell_of(G, gx, gy, k0));
-  if (mode == kStage2) block_max_to(to_d<R>(lam_max), &ctrl->lam[(step + 1) & 1], s_red);
+  if (final_stage) block_max_to(to_d<R>(lam_max), &ctrl->lam[(step + 1) & 1], s_red);
   __syncthreads();  // the next tile reuses the shared memory
   }
 }
 
 // The shared-memory opt-in is a per-device attribute of the kernel: it is set
 // once on every device the calling threads make current.
-template <typename R, int TY>
+template <typename R, int TY, bool GEN>
 void stage_smem_setup() {
   static bool done[kMaxDevices] = {};
   const int dev = current_device();
   if (done[dev]) return;
-  cudaFuncSetAttribute(k_stage<R, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<R, TY>::bytes);
+  cudaFuncSetAttribute(k_stage<R, TY, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)StageSmem<R, TY>::bytes);
   done[dev] = true;
 }
 
-template <typename R, int TY>
+template <typename R, int TY, bool GEN>
 cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
                            const LaunchPlan& lp, cudaStream_t s) {
-  stage_smem_setup<R, TY>();
+  stage_smem_setup<R, TY, GEN>();
   long long nb = ntiles;
   if (lp.blocks_per_sm > 0) nb = std::min<long long>(ntiles, (long long)lp.blocks_per_sm * sm_count());
   if (nb < 1) nb = 1;
@@ -494,8 +517,8 @@ cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid,
     cudaError_t e = cudaMemsetAsync(lp.counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
   }
-  k_stage<R, TY><<<(unsigned)nb, 32 * TY, StageSmem<R, TY>::bytes, s>>>(grids, tiles, ngrid, ntiles, mode,
-                                                                         lp.sched, lp.counter);
+  k_stage<R, TY, GEN><<<(unsigned)nb, 32 * TY, StageSmem<R, TY>::bytes, s>>>(grids, tiles, ngrid, ntiles, mode,
+                                                                              lp.sched, lp.counter);
   return cudaGetLastError();
 }
 

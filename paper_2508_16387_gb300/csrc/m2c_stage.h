@@ -28,5 +28,9 @@ cudaError_t launch_stage_fp64(const Grid* grids, const long long* tiles, int ngr
                               const LaunchPlan& lp, cudaStream_t s);
 void setup_stage_fp32();
 void setup_stage_fp64();
+// The general instantiation (k_stage<R, 8, true>) of either precision.
+cudaError_t launch_stage_gen(int prec, const Grid* grids, const long long* tiles, int ngrid, long long ntiles,
+                             int mode, const LaunchPlan& lp, cudaStream_t s);
+void setup_stage_gen();
 
 }  // namespace m2c

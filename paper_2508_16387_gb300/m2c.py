@@ -22,6 +22,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENONP
 EOS_SG, EOS_MG = 0, 1
 FP64, MIXED = 0, 1
 BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
+LIM_VAN_ALBADA, LIM_MC = 0, 1
+FLUX_HLLC, FLUX_LLF = 0, 1
 
 
 class M2CError(RuntimeError):
@@ -32,6 +34,11 @@ class M2CError(RuntimeError):
 
 class EosDesc(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("params", ctypes.c_double * 6)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("rk", ctypes.c_int), ("limiter", ctypes.c_int), ("flux", ctypes.c_int),
+                ("mc_alpha", ctypes.c_double), ("dt_fixed", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -53,6 +60,9 @@ def lib():
         p, i, d, z, L_ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_long
         L.m2c_workspace_bytes.restype = z
         L.m2c_workspace_bytes.argtypes = [i, i, i, i]
+        L.m2c_workspace_bytes_rk.restype = z
+        L.m2c_workspace_bytes_rk.argtypes = [i, i, i, i, i]
+        L.m2c_set_options.argtypes = [p, ctypes.POINTER(Options)]
         L.m2c_batch_workspace_bytes.restype = z
         L.m2c_batch_workspace_bytes.argtypes = [i]
         L.m2c_batch_create.argtypes = [ctypes.POINTER(p), p, i, p, z, p]
@@ -135,6 +145,10 @@ def _stream_handle(stream):
 
 def m2c_workspace_bytes(nx, ny, nz, precision=FP64) -> int:
     return lib().m2c_workspace_bytes(nx, ny, nz, precision)
+
+
+def m2c_workspace_bytes_rk(nx, ny, nz, precision=FP64, rk=2) -> int:
+    return lib().m2c_workspace_bytes_rk(nx, ny, nz, precision, rk)
 
 
 def m2c_batch_workspace_bytes(k) -> int:
@@ -229,7 +243,10 @@ class Grid:
     """A context with its borrowed device state and workspace (torch tensors)."""
 
     def __init__(self, n, h, bc, eos, precision=FP64, cfl=0.5, reinit_every=10, reinit_iters=5,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, options=None):
+        """options: None (TVD RK2, modified van Albada, HLLC, CFL time step) or a dict of
+        m2c_set_options fields (rk, limiter, flux, mc_alpha, dt_fixed); rk = 3 sizes the
+        workspace for the second stage state."""
         import torch
         self.torch = torch
         self.n = tuple(n)
@@ -239,7 +256,9 @@ class Grid:
         self.precision = precision
         self.device = torch.device(device)
         self.stream = stream
-        wsb = m2c_workspace_bytes(nx, ny, nz, precision)
+        opts = dict(rk=2, limiter=LIM_VAN_ALBADA, flux=FLUX_HLLC, mc_alpha=1.2, dt_fixed=0.0)
+        opts.update(options or {})
+        wsb = m2c_workspace_bytes_rk(nx, ny, nz, precision, opts["rk"])
         self.workspace = torch.empty(wsb + 256, dtype=torch.uint8, device=self.device)
         off = (-self.workspace.data_ptr()) % 256
         self._ws_ptr = ctypes.c_void_p(self.workspace.data_ptr() + off)
@@ -257,6 +276,12 @@ class Grid:
             arr = (ctypes.c_double * 6)(*(list(prm) + [0.0] * (6 - len(prm))))
             _check(lib().m2c_set_eos(ctx, m, t, arr, len(prm)), "m2c_set_eos", ctx)
         _check(lib().m2c_set_scheme(ctx, cfl, reinit_every, reinit_iters), "m2c_set_scheme", ctx)
+        if options:
+            self.set_options(**opts)
+
+    def set_options(self, rk=2, limiter=LIM_VAN_ALBADA, flux=FLUX_HLLC, mc_alpha=1.2, dt_fixed=0.0):
+        o = Options(rk, limiter, flux, mc_alpha, dt_fixed)
+        _check(lib().m2c_set_options(self.ctx, ctypes.byref(o)), "m2c_set_options", self.ctx)
 
     def __del__(self):
         ctx = getattr(self, "ctx", None)
