@@ -61,8 +61,16 @@ typedef enum {
  *   params = {gamma, p_c}; p_c = 0 is a perfect gas.
  * M2C_EOS_MG: Mie-Grueneisen (App. B.3): p = p_R(eta) + rho0 Gamma0 (e - e_R(eta)),
  *   eta = 1 - rho0/rho; params = {rho0, c0, s, Gamma0, e0, eta_min}; eta_min = -inf
- *   (or fewer than 6 params) turns the tensile cutoff off. */
-typedef enum { M2C_EOS_SG = 0, M2C_EOS_MG = 1 } m2c_eos_type;
+ *   (or fewer than 6 params) turns the tensile cutoff off.
+ * M2C_EOS_NASG: Noble-Abel stiffened gas (Sec. 3.3, Eq. NASG_EOS):
+ *   p = (gamma-1) rho (e - e_c)/(1 - rho b) - gamma p_c, defined for rho b < 1;
+ *   params = {gamma, p_c, b, e_c}.
+ * M2C_EOS_JWL: Jones-Wilkins-Lee (App. B.2, Eq. JWL_EOS):
+ *   p = omega rho e + sum_i A_i (1 - omega rho/(R_i rho0)) exp(-R_i rho0/rho) (the first
+ *   exponential, printed with a plus sign, is read with the minus sign of the second);
+ *   params = {omega, A1, A2, R1, R2, rho0}.
+ * A grid with a NASG or JWL material runs the general bulk kernel (8-row tiles). */
+typedef enum { M2C_EOS_SG = 0, M2C_EOS_MG = 1, M2C_EOS_NASG = 2, M2C_EOS_JWL = 3 } m2c_eos_type;
 
 /* M2C_FP64: every operation in FP64. M2C_MIXED: reconstruction, HLLC, the
  * level-set residual and the reinitialisation update in FP32; the pressure
@@ -72,8 +80,12 @@ typedef enum { M2C_EOS_SG = 0, M2C_EOS_MG = 1 } m2c_eos_type;
 typedef enum { M2C_FP64 = 0, M2C_MIXED = 1 } m2c_precision;
 
 /* Boundary conditions per side (x-, x+, y-, y+, z-, z+): transmissive
- * (zero-gradient ghost values) or periodic (both sides of an axis). */
-typedef enum { M2C_BC_TRANSMISSIVE = 0, M2C_BC_PERIODIC = 1 } m2c_bc;
+ * (zero-gradient ghost values), periodic (both sides of an axis), or symmetry
+ * (a mirror plane: the ghost cells are the mirror images of the cells inside,
+ * with the velocity component normal to the side negated; the axis of the
+ * spherical and cylindrical forms of Sec. 3.4 and the mirror planes of a
+ * symmetric problem; needs at least 2 cells along the axis). */
+typedef enum { M2C_BC_TRANSMISSIVE = 0, M2C_BC_PERIODIC = 1, M2C_BC_SYMMETRY = 2 } m2c_bc;
 
 typedef struct {
   int type;          /* m2c_eos_type */
@@ -112,9 +124,11 @@ size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
 m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[3], double h, const int bc[6],
                          int precision, void* workspace, size_t ws_bytes, void* stream);
 
-/* Material 0 (phi >= 0) or 1 (phi < 0) gets an EOS (App. B.1, B.3):
- * M2C_EOS_SG (gamma > 1, p_c) or M2C_EOS_MG (rho0 > 0, c0 > 0, s > 1,
- * Gamma0 > 0 [, e0 [, eta_min]]); anything else is M2C_EINVAL. */
+/* Material 0 (phi >= 0) or 1 (phi < 0) gets an EOS (Sec. 3.3, App. B.1-B.3):
+ * M2C_EOS_SG (gamma > 1, p_c), M2C_EOS_MG (rho0 > 0, c0 > 0, s > 1,
+ * Gamma0 > 0 [, e0 [, eta_min]]), M2C_EOS_NASG (gamma > 1, p_c, b >= 0, e_c)
+ * or M2C_EOS_JWL (omega > 0, A1, A2, R1 > 0, R2 > 0, rho0 > 0); anything else
+ * is M2C_EINVAL. */
 m2c_status m2c_set_eos(m2c_ctx* ctx, int material, int type, const double* params, int nparams);
 
 /* CFL number of dt = CFL h / max_cells sum_d (|V_d| + c) (the sum runs over the
@@ -135,17 +149,39 @@ m2c_status m2c_set_scheme(m2c_ctx* ctx, double cfl, int reinit_every, int reinit
  *      Lax-Friedrichs: the local Lax-Friedrichs flux with the largest |u_n| + c of
  *      the two face states); the FIVER flux of an interface face uses it too.
  *  dt_fixed: > 0 = a constant time step instead of the CFL rule (Sec. 4.3).
- * Any non-default option selects the general instantiation of the bulk kernel
- * (8-row tiles; its results equal the default kernel's for default options).
- * M2C_EINVAL for a value outside these sets. */
+ *  geom: M2C_GEOM_CARTESIAN (default), or the reduced forms of Sec. 3.4 in
+ *      which the grid's x axis is the radius r, r_i = x0 + (i + 1/2) h:
+ *      M2C_GEOM_SPHERICAL (Eq. euler1d_spherical; ny = nz = 1) or
+ *      M2C_GEOM_CYLINDRICAL (Eq. Euler_cylindrical; ny = 1, z the axial
+ *      coordinate). The geometric source S = -(alpha/r) u_r (rho, rho u, rho v,
+ *      rho w, rho E + p), alpha = 2 or 1, is evaluated at the cell centre from
+ *      the stage state and added to the residual after the flux sum; the
+ *      level-set equation keeps its Cartesian form. A symmetry side at r = 0
+ *      (x0 = 0) is the axis or centre. x0 >= 0.
+ *  band_beta, band_gamma: the narrow-band level set of Sec. 4.4 (the local
+ *      level set of Peng et al., J. Comput. Phys. 155, 1999), tube radii in
+ *      cells, 0 < band_beta < band_gamma; band_gamma = 0 (default) solves the
+ *      level-set equation in the whole domain. The advection velocity is scaled
+ *      by c = 1 for |phi| <= beta, (|phi| - gamma)^2 (2|phi| + gamma - 3 beta)/
+ *      (gamma - beta)^3 between the radii and 0 beyond; after the Runge-Kutta
+ *      update and the scheduled reinitialisation phi is clipped to
+ *      [-gamma, gamma].
+ * Any non-default option, and any symmetry side, selects the general
+ * instantiation of the bulk kernel (8-row tiles). M2C_EINVAL for a value
+ * outside these sets. */
 typedef enum { M2C_LIM_VAN_ALBADA = 0, M2C_LIM_MC = 1 } m2c_limiter;
 typedef enum { M2C_FLUX_HLLC = 0, M2C_FLUX_LLF = 1 } m2c_flux;
+typedef enum { M2C_GEOM_CARTESIAN = 0, M2C_GEOM_CYLINDRICAL = 1, M2C_GEOM_SPHERICAL = 2 } m2c_geom;
 typedef struct {
   int rk;
   int limiter;
   int flux;
   double mc_alpha;
   double dt_fixed;
+  int geom;
+  double x0;
+  double band_beta;
+  double band_gamma;
 } m2c_options;
 m2c_status m2c_set_options(m2c_ctx* ctx, const m2c_options* opt);
 

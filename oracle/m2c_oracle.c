@@ -83,6 +83,7 @@ typedef struct {
   double dt_fixed; /* > 0: constant time step instead of the CFL rule */
   int geom;        /* GEOM_CARTESIAN (default), GEOM_CYLINDRICAL or GEOM_SPHERICAL */
   double x0;       /* lower x coordinate: the radius of the first cell's lower face */
+  double band_beta, band_gamma; /* narrow-band level set: tube radii in cells (gamma = 0: full domain) */
 } or_grid_t;
 
 #define LIM_VA_MOD 0 /* modified van Albada, App. D */
@@ -981,6 +982,34 @@ static int face_flux(const or_grid_t* g, const double* P, const unsigned char* i
   return num_flux(g, &g->eos[mb], S, Qb, d, F);
 }
 
+/* Narrow-band level set (Sec. 4.4: the level-set equation solved in a band
+ * around the zero level set; Reading R38, the local level set of Peng et al.,
+ * J. Comput. Phys. 155, 1999): the advection velocity is scaled by the cutoff
+ * c(phi) = 1 for |phi| <= beta, (|phi| - gamma)^2 (2|phi| + gamma - 3 beta) /
+ * (gamma - beta)^3 for beta < |phi| < gamma, 0 beyond, with beta and gamma the
+ * tube radii (in cells times h), phi the cell's value in the stage; at the end
+ * of the step (after the Runge-Kutta update and the scheduled
+ * reinitialisation) phi is clipped to [-gamma, gamma], so that the level set
+ * beyond the tube is a plateau at +-gamma that the tube's reinitialisation
+ * pulls back to distances as the interface approaches. gamma = 0 is the full
+ * domain. A reinitialisation restricted to |phi| < gamma would freeze the
+ * plateau cells and, with the zero velocity at gamma, hold the tube's outer
+ * edge in place (a sphere carried seven cells lagged a cell behind). */
+static double band_cutoff(const or_grid_t* g, double phi) {
+  double beta = g->band_beta * g->h, gamma = g->band_gamma * g->h, a = fabs(phi);
+  if (a <= beta) return 1.0;
+  if (a >= gamma) return 0.0;
+  double d = gamma - beta;
+  return (a - gamma) * (a - gamma) * (2.0 * a + gamma - 3.0 * beta) / (d * d * d);
+}
+
+static void band_clip(const or_grid_t* g, double* phi) {
+  if (!(g->band_gamma > 0.0)) return;
+  long N = ncells(g);
+  double gamma = g->band_gamma * g->h;
+  for (long c = 0; c < N; ++c) phi[c] = fmax(-gamma, fmin(gamma, phi[c]));
+}
+
 /* Third-order upwind-biased derivative of phi along d at cell c (Sec. 4.4,
  * Reading R18): for velocity >= 0, (2 phi_{+1} + 3 phi_0 - 6 phi_{-1} + phi_{-2})/(6h);
  * otherwise (-phi_{+2} + 6 phi_{+1} - 3 phi_0 - 2 phi_{-1})/(6h). */
@@ -1051,6 +1080,7 @@ static int stage_residual(const or_grid_t* g, const double* W, const double* phi
         double Dy = ls_derivative(g, phi, i, j, k, 1, v);
         double Dz = ls_derivative(g, phi, i, j, k, 2, w);
         Lphi[c] = -((u * Dx + v * Dy) + w * Dz);
+        if (g->band_gamma > 0.0) Lphi[c] = band_cutoff(g, phi[c]) * Lphi[c];
       }
   if (stats) {
     stats->interface_faces = nif;
@@ -1313,6 +1343,7 @@ static int step_one(const or_grid_t* g, double* W, double* phi, long step_index,
   /* (5) reinitialisation when scheduled: after steps reinit_every, 2 reinit_every, ... */
   if (g->reinit_every > 0 && g->reinit_iters > 0 && (step_index + 1) % g->reinit_every == 0)
     reinit(g, phi, g->reinit_iters, wk->tmp0, wk->tmp1);
+  band_clip(g, phi); /* narrow band (Reading R38) */
   /* (6) phase update */
   for (long c = 0; c < N; ++c) wk->id2[c] = phi[c] < 0.0;
   long nf = 0;
@@ -1402,6 +1433,8 @@ static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   g->dt_fixed = dp[15];
   g->geom = ip[17];
   g->x0 = dp[16];
+  g->band_beta = dp[17];
+  g->band_gamma = dp[18];
 #ifdef _OPENMP
   if (ip[13] > 0) omp_set_num_threads(ip[13]);
 #endif
@@ -1429,6 +1462,7 @@ static int mk_grid(or_grid_t* g, const int* ip, const double* dp) {
   if (g->flux != FLUX_HLLC && g->flux != FLUX_LLF) return OR_EINVAL;
   if (g->limiter == LIM_MC && !(g->mc_alpha >= 0.0 && g->mc_alpha <= 2.0)) return OR_EINVAL;
   if (!(g->dt_fixed >= 0.0)) return OR_EINVAL;
+  if (g->band_gamma > 0.0 && !(g->band_beta > 0.0 && g->band_beta < g->band_gamma)) return OR_EINVAL;
   return OR_OK;
 }
 
@@ -1493,6 +1527,15 @@ int or_hllc(int type, const double* prm, const double* qL, const double* qR, int
 }
 
 double or_va_slope(double a, double b) { return va_slope(a, b); }
+
+double or_band_cutoff(double beta, double gamma, double h, double phi) {
+  or_grid_t g;
+  memset(&g, 0, sizeof(g));
+  g.band_beta = beta;
+  g.band_gamma = gamma;
+  g.h = h;
+  return band_cutoff(&g, phi);
+}
 
 double or_mc_slope(double a, double b, double alpha) { return mc_slope(a, b, alpha); }
 

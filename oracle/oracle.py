@@ -60,6 +60,8 @@ def lib():
         _lib.or_va_slope.argtypes = [d, d]
         _lib.or_mc_slope.restype = d
         _lib.or_mc_slope.argtypes = [d, d, d]
+        _lib.or_band_cutoff.restype = d
+        _lib.or_band_cutoff.argtypes = [d, d, d, d]
         _lib.or_llf.argtypes = [i, p, p, p, i, p]
         for name in ("or_eos_pressure", "or_eos_energy", "or_eos_c2"):
             getattr(_lib, name).argtypes = [i, p, d, d, p]
@@ -134,6 +136,8 @@ class Grid:
     dt_fixed: float = 0.0  # > 0: constant time step instead of the CFL rule (Sec. 4.3)
     geom: int = 0  # GEOM_CARTESIAN, GEOM_CYLINDRICAL (x = r, z axial; ny = 1) or GEOM_SPHERICAL (x = r; 1D)
     x0: float = 0.0  # lower x coordinate (the radius of the first cell's lower face)
+    band_beta: float = 0.0  # narrow-band level set (Reading R38): inner tube radius in cells
+    band_gamma: float = 0.0  # outer tube radius in cells; 0 = the full domain
 
     def packed(self):
         ip = np.array(list(self.n) + list(self.bc) + [self.reinit_every, self.reinit_iters,
@@ -141,7 +145,8 @@ class Grid:
                       self.geom],
                       dtype=np.int32)
         dp = np.concatenate([[self.h, self.cfl], self.eos[0].arr(), self.eos[1].arr(),
-                             [self.mc_alpha, self.dt_fixed, self.x0]]).astype(np.float64)
+                             [self.mc_alpha, self.dt_fixed, self.x0, self.band_beta, self.band_gamma]]
+                            ).astype(np.float64)
         return ip, dp
 
     @property
@@ -155,6 +160,11 @@ def va_slope(a: float, b: float) -> float:
 
 def mc_slope(a: float, b: float, alpha: float = 1.2) -> float:
     return lib().or_mc_slope(a, b, alpha)
+
+
+def band_cutoff(beta: float, gamma: float, h: float, phi: float) -> float:
+    """Narrow-band cutoff of the level-set velocity (Reading R38); beta, gamma in cells."""
+    return lib().or_band_cutoff(beta, gamma, h, phi)
 
 
 def _eos_call(name, eos: EOS, x: float, y: float) -> float:

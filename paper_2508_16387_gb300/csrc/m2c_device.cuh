@@ -13,9 +13,9 @@ namespace m2c {
 
 // FP64 path: u = (rho u)/rho, e = (rho E - rho|V|^2/2)/rho, p = p(rho, e).
 // Mixed path: the same with FP32 velocities and kinetic energy; rho e and, for
-// the stiffened gas, the pressure (a difference of large numbers when p_c is
-// large) in FP64, then rounded to FP32.
-template <typename R>
+// the stiffened gas and NASG, the pressure (a difference of large numbers when
+// p_c is large) in FP64, then rounded to FP32. EXT: NASG and JWL materials too.
+template <typename R, bool EXT = false>
 __device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& qd, double rho, double m1, double m2,
                                                double m3, double E, R P[5]) {
   if constexpr (sizeof(R) == 8) {
@@ -24,7 +24,7 @@ __device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& q
     const double ke = 0.5 * ((m1 * u + m2 * v) + m3 * w);
     const double e = (E - ke) * inv;
     double p = 0.0;
-    const bool ok = eos_p<double>(q, rho, inv, e, p);
+    const bool ok = eos_p<double, EXT>(q, rho, inv, e, p);
     P[0] = rho; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
     return ok && rho > 0.0;
   } else {
@@ -38,24 +38,28 @@ __device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& q
     bool ok = true;
     if (q.type == M2C_EOS_SG) {
       p = d2f(qd.gm1 * rhoe - qd.gpc);
+    } else if (EXT && q.type == M2C_EOS_NASG) {
+      const double d = 1.0 - rho * qd.b;
+      ok = d > 0.0;
+      p = d2f(div_nr(qd.gm1 * (rhoe - rho * qd.ec), d) - qd.gpc);
     } else {
-      ok = eos_p<float>(q, rf, inv, d2f(rhoe) * inv, p);
+      ok = eos_p<float, EXT>(q, rf, inv, d2f(rhoe) * inv, p);
     }
     P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
     return ok && gt0(rho);
   }
 }
 
-template <typename R>
+template <typename R, bool EXT = false>
 __device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd, const double* __restrict__ W,
                                              long long N, long long c, R P[5]) {
-  return cons_to_prim_v<R>(q, qd, W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c], P);
+  return cons_to_prim_v<R, EXT>(q, qd, W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c], P);
 }
 
-template <typename R>
+template <typename R, bool EXT = false>
 __device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w, R p, FaceState<R>& F) {
   R e = (R)0, c2 = (R)0;
-  const bool ok = eos_e_c2<R>(q, rho, rrcp<R>(rho), p, e, c2);
+  const bool ok = eos_e_c2<R, EXT>(q, rho, rrcp<R>(rho), p, e, c2);
   F.rho = rho; F.u = u; F.v = v; F.w = w; F.p = p;
   F.c = ok ? rsqrt_pos<R>(c2) : (R)0;
   F.E = e + (R)0.5 * ((u * u + v * v) + w * w);
@@ -83,25 +87,25 @@ __device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], cons
       for (int v = 0; v < 5; ++v) s[v] = va_slope<R>(P[v] - Pm[v], Pp[v] - P[v]);
     }
     const R hf = (R)0.5;
-    const bool okm = make_face<R>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2], P[3] - hf * s[3],
-                                  P[4] - hf * s[4], Qm);
-    const bool okp = make_face<R>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2], P[3] + hf * s[3],
-                                  P[4] + hf * s[4], Qp);
+    const bool okm = make_face<R, GEN>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2],
+                                       P[3] - hf * s[3], P[4] - hf * s[4], Qm);
+    const bool okp = make_face<R, GEN>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2],
+                                       P[3] + hf * s[3], P[4] + hf * s[4], Qp);
     if (okm && okp) return;
   }
-  if (!make_face<R>(q, P[0], P[1], P[2], P[3], P[4], Qm)) bad = true;
+  if (!make_face<R, GEN>(q, P[0], P[1], P[2], P[3], P[4], Qm)) bad = true;
   Qp = Qm;
 }
 
 // Wave-speed sum of a state, sum over the axes with more than one cell of
 // |V_d| + c (the CFL reading of the design notes), in precision R (the mixed
 // path takes the time step from FP32 wave speeds of the FP64 state).
-template <typename R>
+template <typename R, bool EXT = false>
 __device__ __forceinline__ R wave_sum_v(const Grid& g, const EosP<R>& q, const EosDev& qd, const double w[5], bool& ok) {
   R P[5];
-  ok = cons_to_prim_v<R>(q, qd, w[0], w[1], w[2], w[3], w[4], P);
+  ok = cons_to_prim_v<R, EXT>(q, qd, w[0], w[1], w[2], w[3], w[4], P);
   R e, c2;
-  ok = ok && eos_e_c2<R>(q, P[0], rrcp<R>(P[0]), P[4], e, c2);
+  ok = ok && eos_e_c2<R, EXT>(q, P[0], rrcp<R>(P[0]), P[4], e, c2);
   const R cs = ok ? rsqrt_pos<R>(c2) : (R)0;
   R lam = (R)0;
   if (g.active[0]) lam = lam + (fabs(P[1]) + cs);
@@ -114,7 +118,7 @@ template <typename R>
 __device__ __forceinline__ double wave_sum_r(const Grid& g, const EosP<R>& q, const EosDev& qd, const double* W,
                                              long long N, long long c, bool& ok) {
   const double w[5] = {W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c]};
-  return to_d<R>(wave_sum_v<R>(g, q, qd, w, ok));
+  return to_d<R>(wave_sum_v<R, true>(g, q, qd, w, ok));
 }
 
 // The same in the grid's precision, for material m: every wave-speed maximum
@@ -124,6 +128,19 @@ __device__ __forceinline__ double wave_sum(const Grid& g, int m, const double* W
                                            bool& ok) {
   if (g.prec == M2C_MIXED) return wave_sum_r<float>(g, g.eosf[m], g.eos[m], W, N, c, ok);
   return wave_sum_r<double>(g, g.eos[m], g.eos[m], W, N, c, ok);
+}
+
+// Narrow-band level set (Sec. 4.4; the local level set of Peng et al., J.
+// Comput. Phys. 155, 1999): the advection velocity is scaled by
+// c = 1 for |phi| <= beta, (|phi| - gamma)^2 (2|phi| + gamma - 3 beta)/(gamma - beta)^3
+// between the tube radii, 0 beyond gamma.
+template <typename R>
+__device__ __forceinline__ R band_cutoff(R beta, R gamma, R phi) {
+  const R a = fabs(phi);
+  if (a <= beta) return (R)1;
+  if (a >= gamma) return (R)0;
+  const R d = gamma - beta, x = a - gamma;
+  return rdiv<R>(x * x * ((R)2 * a + gamma - (R)3 * beta), d * d * d);
 }
 
 __device__ __forceinline__ double warp_max(double v) {

@@ -84,6 +84,10 @@ struct Grid {
   int pad2;
   double mc_alpha;    // alpha of the MC limiter
   double dt_fixed;    // > 0: constant time step instead of the CFL rule
+  int geom;           // M2C_GEOM_CARTESIAN, _CYLINDRICAL or _SPHERICAL (Sec. 3.4): x is the radius
+  int pad3;
+  double x0;          // radius of the lower face of the first cell along x
+  double band_beta, band_gamma;  // narrow-band level set: tube radii (lengths); gamma = 0: full domain
   double* W2;         // TVD RK3: the second stage state (workspace)
   double* phi2;
 };
@@ -110,10 +114,19 @@ __device__ __forceinline__ int list_slot(int mode) {
 }
 __device__ __forceinline__ bool last_stage(int mode) { return mode == kStage2 || mode == kStage3; }
 
+// Index of the cell whose state a ghost position i (outside [0, n)) takes:
+// transmissive = the nearest cell (zero gradient), periodic = wrapped, symmetry =
+// the mirror image across the side (its velocity component along the axis is
+// negated by the caller, see mirrored()).
 __device__ __forceinline__ int map_index(int i, int n, int lo_bc, int hi_bc) {
-  if (i < 0) return lo_bc == M2C_BC_PERIODIC ? ((i % n) + n) % n : 0;
-  if (i >= n) return hi_bc == M2C_BC_PERIODIC ? i % n : n - 1;
+  if (i < 0) return lo_bc == M2C_BC_PERIODIC ? ((i % n) + n) % n : (lo_bc == M2C_BC_SYMMETRY ? -1 - i : 0);
+  if (i >= n) return hi_bc == M2C_BC_PERIODIC ? i % n : (hi_bc == M2C_BC_SYMMETRY ? 2 * n - 1 - i : n - 1);
   return i;
+}
+
+// 1 when position i lies across a symmetry side of its axis.
+__device__ __forceinline__ int mirrored(int i, int n, int lo_bc, int hi_bc) {
+  return ((i < 0 && lo_bc == M2C_BC_SYMMETRY) || (i >= n && hi_bc == M2C_BC_SYMMETRY)) ? 1 : 0;
 }
 
 __device__ __forceinline__ long long cell_of(const Grid& g, int i, int j, int k) {

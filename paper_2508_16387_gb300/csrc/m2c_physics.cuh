@@ -15,15 +15,22 @@ namespace m2c {
 // ---------------------------------------------------------------------------
 // Equation of state parameters in device memory. SG: p = (g - 1) rho e - g pc
 // (NASG of Sec. 3.3 with b = e_c = 0). MG: App. B.3 with the compression,
-// tension and cutoff branches of the reference curves.
+// tension and cutoff branches of the reference curves. NASG (Sec. 3.3, Eq.
+// NASG_EOS): p = (g - 1) rho (e - e_c)/(1 - rho b) - g pc. JWL (App. B.2, Eq.
+// JWL_EOS with the sign of its first exponential read as that of the second):
+// p = w rho e + sum_i A_i (1 - w rho/(R_i rho0)) exp(-R_i rho0/rho).
+// The NASG and JWL branches are compiled only where EXT is set (the general
+// bulk kernel, the interface and Riemann kernels).
 // ---------------------------------------------------------------------------
 template <typename R>
 struct EosP {
-  int type;  // M2C_EOS_SG or M2C_EOS_MG
+  int type;  // m2c_eos_type
   int pad;
-  R g, pc, gm1, gpc, inv_gm1;                // SG
+  R g, pc, gm1, gpc, inv_gm1;                // SG and NASG
   R rho0, c0, s, G0, e0, eta_min;            // MG
   R K0, rg, inv_rg, inv_2rho0, eta_max, pmin, rk4_span;  // MG derived
+  R b, ec;                                   // NASG
+  R om, A1, A2, R1r, R2r, c1, c2;            // JWL: w, A_i, R_i rho0, w/(R_i rho0)
 };
 using EosDev = EosP<double>;
 
@@ -38,6 +45,23 @@ __host__ inline EosP<R> make_eos(int type, const double* prm) {
     e.gm1 = (R)(prm[0] - 1.0);
     e.gpc = (R)(prm[0] * prm[1]);
     e.inv_gm1 = (R)(1.0 / (prm[0] - 1.0));
+  } else if (type == M2C_EOS_NASG) {
+    e.g = (R)prm[0];
+    e.pc = (R)prm[1];
+    e.gm1 = (R)(prm[0] - 1.0);
+    e.gpc = (R)(prm[0] * prm[1]);
+    e.inv_gm1 = (R)(1.0 / (prm[0] - 1.0));
+    e.b = (R)prm[2];
+    e.ec = (R)prm[3];
+  } else if (type == M2C_EOS_JWL) {
+    e.om = (R)prm[0];
+    e.A1 = (R)prm[1];
+    e.A2 = (R)prm[2];
+    e.R1r = (R)(prm[3] * prm[5]);
+    e.R2r = (R)(prm[4] * prm[5]);
+    e.c1 = (R)(prm[0] / (prm[3] * prm[5]));
+    e.c2 = (R)(prm[0] / (prm[4] * prm[5]));
+    e.rho0 = (R)prm[5];
   } else {
     const double K0 = prm[0] * prm[1] * prm[1], rg = prm[0] * prm[3];
     e.rho0 = (R)prm[0];
@@ -315,12 +339,36 @@ __device__ __forceinline__ void mg_ref(const EosP<R>& q, R eta, R& pR, R& dpR, R
   }
 }
 
-// p(rho, e) given 1/rho; false if the state is outside the EOS domain.
+// JWL: f(rho) = sum_i A_i (1 - w rho/(R_i rho0)) exp(-R_i rho0/rho) and f'(rho).
 template <typename R>
+__device__ __forceinline__ void jwl_f(const EosP<R>& q, R rho, R inv_rho, R& f, R& df) {
+  const R x1 = q.R1r * inv_rho, x2 = q.R2r * inv_rho;
+  const R e1 = exp(-x1), e2 = exp(-x2);
+  const R a1 = (R)1 - q.c1 * rho, a2 = (R)1 - q.c2 * rho;
+  f = q.A1 * a1 * e1 + q.A2 * a2 * e2;
+  df = q.A1 * e1 * (-q.c1 + a1 * x1 * inv_rho) + q.A2 * e2 * (-q.c2 + a2 * x2 * inv_rho);
+}
+
+// p(rho, e) given 1/rho; false if the state is outside the EOS domain.
+template <typename R, bool EXT = false>
 __device__ __forceinline__ bool eos_p(const EosP<R>& q, R rho, R inv_rho, R e, R& p) {
   if (q.type == M2C_EOS_SG) {
     p = q.gm1 * rho * e - q.gpc;
     return true;
+  }
+  if constexpr (EXT) {
+    if (q.type == M2C_EOS_NASG) {
+      const R d = (R)1 - rho * q.b;
+      if (!(d > (R)0)) return false;
+      p = rdiv<R>(q.gm1 * rho * (e - q.ec), d) - q.gpc;
+      return true;
+    }
+    if (q.type == M2C_EOS_JWL) {
+      R f, df;
+      jwl_f<R>(q, rho, inv_rho, f, df);
+      p = q.om * rho * e + f;
+      return true;
+    }
   }
   R eta = (R)1 - q.rho0 * inv_rho;
   if (!(eta < q.eta_max)) return false;
@@ -332,13 +380,25 @@ __device__ __forceinline__ bool eos_p(const EosP<R>& q, R rho, R inv_rho, R e, R
 
 // e(rho, p) and c^2(rho, p) together (App. B.3 and App. C.2: c^2 = dp/drho|_e + p/rho^2 dp/de|_rho).
 // False if rho <= 0, c^2 <= 0 or the state is outside the EOS domain.
-template <typename R>
+template <typename R, bool EXT = false>
 __device__ __forceinline__ bool eos_e_c2(const EosP<R>& q, R rho, R inv_rho, R p, R& e, R& c2) {
   if (!(rho > (R)0)) return false;
   if (q.type == M2C_EOS_SG) {
     R pb = p + q.pc;
     e = (p + q.gpc) * q.inv_gm1 * inv_rho;
     c2 = q.g * pb * inv_rho;
+  } else if (EXT && q.type == M2C_EOS_NASG) {
+    // e = e_c + (p + g pc)(1 - rho b)/((g - 1) rho), c^2 = g (p + pc)/(rho (1 - rho b))
+    const R d = (R)1 - rho * q.b;
+    if (!(d > (R)0)) return false;
+    e = q.ec + (p + q.gpc) * d * q.inv_gm1 * inv_rho;
+    c2 = rdiv<R>(q.g * (p + q.pc) * inv_rho, d);
+  } else if (EXT && q.type == M2C_EOS_JWL) {
+    // e = (p - f)/(w rho), c^2 = ((1 + w) p - f)/rho + f'
+    R f, df;
+    jwl_f<R>(q, rho, inv_rho, f, df);
+    e = rdiv<R>((p - f) * inv_rho, q.om);
+    c2 = ((R)1 + q.om) * p * inv_rho - f * inv_rho + df;
   } else {
     R eta = (R)1 - q.rho0 * inv_rho;
     if (!(eta < q.eta_max)) return false;
@@ -484,7 +544,7 @@ struct Side {
 __device__ inline bool make_side(const EosDev& q, double rho, double u, double p, Side& K) {
   if (!(rho > 0.0)) return false;
   double e, c2;
-  if (!eos_e_c2<double>(q, rho, 1.0 / rho, p, e, c2)) return false;
+  if (!eos_e_c2<double, true>(q, rho, 1.0 / rho, p, e, c2)) return false;
   K.rho = rho;
   K.u = u;
   K.p = p;
@@ -494,8 +554,11 @@ __device__ inline bool make_side(const EosDev& q, double rho, double u, double p
   return true;
 }
 
+// Lowest admissible pressure of a side: p + p_c > 0 (SG, NASG), p > 0 (JWL,
+// whose rarefaction is integrated in ln p), the MG tensile cutoff if any.
 __device__ inline double eos_plow(const EosDev& q) {
-  if (q.type == M2C_EOS_SG) return -q.pc;
+  if (q.type == M2C_EOS_SG || q.type == M2C_EOS_NASG) return -q.pc;
+  if (q.type == M2C_EOS_JWL) return 0.0;
   return isfinite(q.eta_min) ? q.pmin : -INFINITY;
 }
 
@@ -505,6 +568,15 @@ __device__ inline int mg_substeps(const EosDev& q, double dp) {
   double nsd = ceil(__ddiv_rn(kRk4Steps * fabs(dp), q.rk4_span));
   nsd = nsd >= 1.0 ? (nsd > kRk4Steps ? (double)kRk4Steps : nsd) : 1.0;
   return (int)nsd;
+}
+
+// JWL rarefactions are integrated in ln p (detonation products expand over
+// decades): 256 substeps per unit of ln(p_K/p_lo), at least 8, with p_lo kept
+// at or above 1e-6 p_K.
+__device__ inline int jwl_substeps(double pK, double p_lo) {
+  const double lo = fmax(p_lo, 1e-6 * pK);
+  const double nd = ceil(256.0 * log(pK / lo));
+  return nd < 8.0 ? 8 : (int)nd;
 }
 
 // The substep count of each MG side's rarefaction curve, fixed once per
@@ -520,8 +592,11 @@ __device__ inline void fix_substeps(const EosDev& qL, Side& L, const EosDev& qR,
   const double num = __dsub_rn(__dadd_rn(__dmul_rn(ZR, L.p), __dmul_rn(ZL, Rs.p)),
                                __dmul_rn(__dmul_rn(ZL, ZR), __dsub_rn(Rs.u, L.u)));
   const double pac = __ddiv_rn(num, __dadd_rn(ZL, ZR));
-  if (qL.type == M2C_EOS_MG) L.nrk = mg_substeps(qL, fmax(__dsub_rn(L.p, fmax(plow, fmin(Rs.p, pac))), 0.0));
-  if (qR.type == M2C_EOS_MG) Rs.nrk = mg_substeps(qR, fmax(__dsub_rn(Rs.p, fmax(plow, fmin(L.p, pac))), 0.0));
+  const double loL = fmax(plow, fmin(Rs.p, pac)), loR = fmax(plow, fmin(L.p, pac));
+  if (qL.type == M2C_EOS_MG) L.nrk = mg_substeps(qL, fmax(__dsub_rn(L.p, loL), 0.0));
+  if (qR.type == M2C_EOS_MG) Rs.nrk = mg_substeps(qR, fmax(__dsub_rn(Rs.p, loR), 0.0));
+  if (qL.type == M2C_EOS_JWL) L.nrk = jwl_substeps(L.p, loL);
+  if (qR.type == M2C_EOS_JWL) Rs.nrk = jwl_substeps(Rs.p, loR);
 }
 
 __device__ inline int wave_sg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
@@ -648,9 +723,148 @@ __device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& 
   return M2C_OK;
 }
 
+// NASG wave curves in P = p + p_c and the covolume-reduced specific volume
+// w = 1/rho - b. Shock: the Hugoniot energy equation is linear in w,
+// w = w_K (gm r + 1)/(r + gm), r = P/P_K, gm = (g - 1)/(g + 1), so
+// f = (p - p_K) sqrt(A/(P + gm P_K)) with A = 2 w_K/(g + 1). Rarefaction: the
+// isentrope P w^g = const gives rho c = sqrt(g P / w) and
+// f = 2 c_K (1 - b rho_K)/(g - 1) (r^((g-1)/(2g)) - 1).
+static __device__ __noinline__ int wave_nasg(const EosDev& q, const Side& K, double p, double& f, double& df,
+                                             double& rs, double* drs) {
+  const double g = q.g, b = q.b, P = p + q.pc, PK = K.p + q.pc, wK = 1.0 / K.rho - b;
+  if (!(P >= 0.0) || !(PK > 0.0) || !(wK > 0.0)) return M2C_ENONPHYS;
+  const double r = P / PK;
+  if (p > K.p) {
+    const double gm = (g - 1.0) / (g + 1.0), A = 2.0 * wK / (g + 1.0), D = P + gm * PK;
+    const double sq = sqrt(A / D);
+    f = (p - K.p) * sq;
+    df = sq * (1.0 - 0.5 * (p - K.p) / D);
+    const double w = wK * (gm * r + 1.0) / (r + gm);
+    rs = 1.0 / (b + w);
+    if (drs) *drs = rs * rs * wK * (1.0 - gm * gm) / ((r + gm) * (r + gm) * PK);
+  } else {
+    f = 2.0 * K.c * (1.0 - b * K.rho) / (g - 1.0) * (pow(r, (g - 1.0) / (2.0 * g)) - 1.0);
+    const double w = wK * pow(r, -1.0 / g);
+    df = sqrt(w / (g * P));
+    rs = 1.0 / (b + w);
+    if (drs) *drs = rs * rs * w / (g * P);
+  }
+  return M2C_OK;
+}
+
+// JWL Hugoniot through K at p > p_K: the root rho > rho_K of
+// H(rho) = e(rho, p) - e_K - (p + p_K)(1/rho_K - 1/rho)/2, bracketed from
+// [rho_K, rho_K (w + 2)/w] (doubling the upper end until H < 0), then Newton
+// kept inside the bracket with the tolerance and extra step of the MG root;
+// d rho/dp by implicit differentiation. de/drho|_p = -(f'(rho) + w e)/(w rho).
+__device__ inline int jwl_hugoniot(const EosDev& q, const Side& K, double p, double& rho_out, double& drdp) {
+  const double w = q.om;
+  double lo = K.rho, hi = K.rho * (w + 2.0) / w;
+  bool bracketed = false;
+  for (int k = 0; k < 60 && !bracketed; ++k) {
+    double f, df;
+    jwl_f<double>(q, hi, 1.0 / hi, f, df);
+    const double e = (p - f) / (w * hi);
+    if (e - K.e - 0.5 * (p + K.p) * (1.0 / K.rho - 1.0 / hi) < 0.0) bracketed = true;
+    else { lo = hi; hi = 2.0 * hi; }
+  }
+  if (!bracketed) return M2C_ENOCONV;
+  double rho = K.rho + (p - K.p) / (K.c * K.c);
+  if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
+  bool extra = false, done = false;
+  for (int it = 0; it < kHugCap; ++it) {
+    double f, df;
+    jwl_f<double>(q, rho, 1.0 / rho, f, df);
+    const double e = (p - f) / (w * rho);
+    const double dedr = -(df + w * e) / (w * rho);
+    const double H = e - K.e - 0.5 * (p + K.p) * (1.0 / K.rho - 1.0 / rho);
+    const double dH = dedr - 0.5 * (p + K.p) / (rho * rho);
+    if (H > 0.0) lo = rho; else hi = rho;
+    double rn = rho - H / dH;
+    if (!(rn >= lo && rn <= hi)) rn = 0.5 * (lo + hi);
+    const bool conv = fabs(rn - rho) <= kHugTol * rn;
+    rho = rn;
+    if (extra) { done = true; break; }
+    if (conv) extra = true;
+  }
+  if (!done) return M2C_ENOCONV;
+  double f, df;
+  jwl_f<double>(q, rho, 1.0 / rho, f, df);
+  const double e = (p - f) / (w * rho);
+  const double Hp = 1.0 / (w * rho) - 0.5 * (1.0 / K.rho - 1.0 / rho);
+  const double Hr = -(df + w * e) / (w * rho) - 0.5 * (p + K.p) / (rho * rho);
+  rho_out = rho;
+  drdp = -Hp / Hr;
+  return M2C_OK;
+}
+
+// JWL wave curve: shock f = sqrt((p - p_K)(1/rho_K - 1/rho_H(p))); rarefaction:
+// the isentrope d rho/dp = 1/c^2, df/dp = 1/(rho c) integrated by classical RK4
+// in s = ln p on equal substeps (fixed per problem, fix_substeps; else for
+// this span); it needs p > 0.
+static __device__ __noinline__ int wave_jwl(const EosDev& q, const Side& K, double p, double& f, double& df,
+                                            double& rs, double* drs) {
+  if (p == K.p) {
+    f = 0.0;
+    df = 1.0 / (K.rho * K.c);
+    rs = K.rho;
+    if (drs) *drs = 1.0 / (K.c * K.c);
+    return M2C_OK;
+  }
+  if (p > K.p) {
+    double rho, drdp;
+    const int st = jwl_hugoniot(q, K, p, rho, drdp);
+    if (st) return st;
+    const double dv = 1.0 / K.rho - 1.0 / rho;
+    const double fv = sqrt((p - K.p) * dv);
+    f = fv;
+    df = (dv + (p - K.p) * drdp / (rho * rho)) / (2.0 * fv);
+    rs = rho;
+    if (drs) *drs = drdp;
+    return M2C_OK;
+  }
+  if (!(p > 0.0) || !(K.p > 0.0)) return M2C_ENONPHYS;
+  const double span = log(p / K.p);
+  int ns = K.nrk;
+  if (ns <= 0) {
+    const double nd = ceil(256.0 * fabs(span));
+    ns = nd < 8.0 ? 8 : (int)nd;
+  }
+  const double hs = span / ns, s0 = log(K.p);
+  double rho = K.rho, fv = 0.0;
+  // d(rho, f)/ds at (s, rho): (p / c^2, p / (rho c)) with p = exp(s)
+  auto rhs = [&](double si, double r, double& kr, double& kf) {
+    const double pp = exp(si);
+    double e, c2;
+    if (!eos_e_c2<double, true>(q, r, 1.0 / r, pp, e, c2)) return false;
+    kr = pp / c2;
+    kf = pp / (r * sqrt(c2));
+    return true;
+  };
+  for (int i = 0; i < ns; ++i) {
+    const double si = s0 + i * hs;
+    double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
+    if (!rhs(si, rho, k1r, k1f) || !rhs(si + 0.5 * hs, rho + 0.5 * hs * k1r, k2r, k2f) ||
+        !rhs(si + 0.5 * hs, rho + 0.5 * hs * k2r, k3r, k3f) || !rhs(si + hs, rho + hs * k3r, k4r, k4f))
+      return M2C_ENONPHYS;
+    rho = rho + hs / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
+    fv = fv + hs / 6.0 * (k1f + 2.0 * k2f + 2.0 * k3f + k4f);
+  }
+  double e, c2;
+  if (!eos_e_c2<double, true>(q, rho, 1.0 / rho, p, e, c2)) return M2C_ENONPHYS;
+  f = fv;
+  df = 1.0 / (rho * sqrt(c2));
+  rs = rho;
+  if (drs) *drs = 1.0 / c2;
+  return M2C_OK;
+}
+
 __device__ inline int wave(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
                            bool want_rho = true, double* drs = nullptr) {
-  return q.type == M2C_EOS_SG ? wave_sg(q, K, p, f, df, rs, want_rho, drs) : wave_mg(q, K, p, f, df, rs, drs);
+  if (q.type == M2C_EOS_SG) return wave_sg(q, K, p, f, df, rs, want_rho, drs);
+  if (q.type == M2C_EOS_MG) return wave_mg(q, K, p, f, df, rs, drs);
+  if (q.type == M2C_EOS_NASG) return wave_nasg(q, K, p, f, df, rs, drs);
+  return wave_jwl(q, K, p, f, df, rs, drs);
 }
 
 // Both wave curves at p: f and f' of each side, and on request (wv) the star
@@ -690,7 +904,8 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
   // vacuum test (F(p_low) >= 0); both wave curves increase with p and vanish at
   // their side's pressure, so F(p_low) <= u_R - u_L and the test is only made
   // when u_R - u_L >= 0
-  if (isfinite(plow) && Rs.u - L.u >= 0.0) {
+  // no vacuum test with a JWL side (its rarefaction needs p > 0)
+  if (isfinite(plow) && Rs.u - L.u >= 0.0 && qL.type != M2C_EOS_JWL && qR.type != M2C_EOS_JWL) {
     st = riemann_F(qL, L, qR, Rs, plow, F, dF);
     if (st) return st;
     if (F >= 0.0) return M2C_EVACUUM;
@@ -919,6 +1134,9 @@ __device__ inline bool riemann_F_f(const EosP<float>& qL, const SideF& L, const 
 // or does not reach |dp| <= 1e-5 |p| in 30 steps.
 static __device__ __noinline__ bool riemann_newton_f(const EosP<float>& qL, float rl, float ul, float pl, const EosP<float>& qR,
                                         float rr, float ur, float pr, float& p_out, int& iters) {
+  // FP32 wave curves exist for the stiffened gas and Mie-Grueneisen only
+  if ((qL.type != M2C_EOS_SG && qL.type != M2C_EOS_MG) || (qR.type != M2C_EOS_SG && qR.type != M2C_EOS_MG))
+    return false;
   SideF L, Rs;
   if (!make_side_f(qL, rl, ul, pl, L) || !make_side_f(qR, rr, ur, pr, Rs)) return false;
   const float plow = fmaxf(eos_plow_f(qL), eos_plow_f(qR));

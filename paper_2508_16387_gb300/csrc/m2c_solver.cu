@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
     const EosDev& qa = G.eos[ia];
     const EosDev& qb = G.eos[ib];
     double Pa[5], Pb[5];
-    bool ok = cons_to_prim<double>(qa, qa, Ws, N, ca, Pa);
-    ok = cons_to_prim<double>(qb, qb, Ws, N, cb, Pb) && ok;
+    bool ok = cons_to_prim<double, true>(qa, qa, Ws, N, ca, Pa);
+    ok = cons_to_prim<double, true>(qb, qb, Ws, N, cb, Pb) && ok;
     double Fa[5] = {0, 0, 0, 0, 0}, Fb[5] = {0, 0, 0, 0, 0};
     RiemannOut rs;
     int its = 0;
@@ -109,10 +109,10 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
       double Sb[5] = {rs.rhoR, Pb[1], Pb[2], Pb[3], rs.p};
       Sa[1 + d] = rs.u;
       Sb[1 + d] = rs.u;
-      bool okf = make_face<double>(qa, Pa[0], Pa[1], Pa[2], Pa[3], Pa[4], A);
-      okf = make_face<double>(qa, Sa[0], Sa[1], Sa[2], Sa[3], Sa[4], SA) && okf;
-      okf = make_face<double>(qb, Sb[0], Sb[1], Sb[2], Sb[3], Sb[4], SB) && okf;
-      okf = make_face<double>(qb, Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], B) && okf;
+      bool okf = make_face<double, true>(qa, Pa[0], Pa[1], Pa[2], Pa[3], Pa[4], A);
+      okf = make_face<double, true>(qa, Sa[0], Sa[1], Sa[2], Sa[3], Sa[4], SA) && okf;
+      okf = make_face<double, true>(qb, Sb[0], Sb[1], Sb[2], Sb[3], Sb[4], SB) && okf;
+      okf = make_face<double, true>(qb, Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], B) && okf;
       if (!okf) st = M2C_ENONPHYS;
       if (d == 0) fiver_fluxes<0>(A, SA, SB, B, Fa, Fb, G.flux);
       else if (d == 1) fiver_fluxes<1>(A, SA, SB, B, Fa, Fb, G.flux);
@@ -159,6 +159,18 @@ __global__ void __launch_bounds__(128) k_finish(const Grid* __restrict__ grids, 
 #pragma unroll
     for (int v = 0; v < 5; ++v)
       res[v] = ((e.F[0][v] - e.F[1][v]) * ih + (e.F[2][v] - e.F[3][v]) * ih) + (e.F[4][v] - e.F[5][v]) * ih;
+    if (G.geom != M2C_GEOM_CARTESIAN) {
+      // spherical / cylindrical source term (Sec. 3.4), FP64, as in the bulk kernel
+      const double* __restrict__ Ws = stage_W(G, mode);
+      const int m = G.id[c] & 1;
+      double P[5];
+      if (!cons_to_prim<double, true>(G.eos[m], G.eos[m], Ws, N, c, P)) latch_error(ctrl, M2C_ENONPHYS, c);
+      const double r = G.x0 + ((double)(c % G.nx) + 0.5) * G.h;
+      const double a = (G.geom == M2C_GEOM_SPHERICAL ? 2.0 : 1.0) / r * P[1];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) res[v] = res[v] - a * Ws[v * N + c];
+      res[4] = res[4] - a * (Ws[4 * N + c] + P[4]);
+    }
     if (mode == kResidual) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) G.resR[v * N + c] = res[v];
@@ -314,6 +326,17 @@ __global__ void k_copy_phi1(const Grid* __restrict__ grids) {
     G.phi[c] = G.phi1[c];
 }
 
+// Narrow band (Sec. 4.4): after the Runge-Kutta update and the scheduled
+// reinitialisation the level set is clipped to [-gamma, gamma] (a plateau
+// beyond the tube; the signs, hence the materials, are unchanged).
+__global__ void __launch_bounds__(256) k_band_clip(const Grid* __restrict__ grids) {
+  const Grid& G = grids[blockIdx.y];
+  if (!(G.band_gamma > 0.0)) return;
+  const double gam = G.band_gamma;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < G.N; c += (long long)gridDim.x * blockDim.x)
+    G.phi[c] = fmax(-gam, fmin(gam, G.phi[c]));
+}
+
 // ---------------------------------------------------------------------------
 // Phase update (Sec. 2.3 step (6)): a cell whose material changed takes the
 // mean primitive state of its face neighbours that were and are of its new
@@ -335,28 +358,34 @@ __global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grid
     const EosDev& q = G.eos[m];
     double sum[5] = {0, 0, 0, 0, 0};
     int cnt = 0;
-    auto take = [&](long long nb) {
+    // a neighbour position across a symmetry side is the mirror image of a cell
+    // inside, its velocity component along that axis negated
+    auto take = [&](int ii, int jj, int kk) {
+      const long long nb = cell_of(G, ii, jj, kk);
       const int old_id = G.id[nb] & 1;
       const int new_id = (G.id[nb] >> 2) & 1;
       if (old_id == m && new_id == m) {
         double P[5];
-        if (!cons_to_prim<double>(q, q, G.W, N, nb, P)) latch_error(ctrl, M2C_ENONPHYS, nb);
+        if (!cons_to_prim<double, true>(q, q, G.W, N, nb, P)) latch_error(ctrl, M2C_ENONPHYS, nb);
+        if (mirrored(ii, G.nx, G.bc[0], G.bc[1])) P[1] = -P[1];
+        if (mirrored(jj, G.ny, G.bc[2], G.bc[3])) P[2] = -P[2];
+        if (mirrored(kk, G.nz, G.bc[4], G.bc[5])) P[3] = -P[3];
 #pragma unroll
         for (int v = 0; v < 5; ++v) sum[v] = sum[v] + P[v];
         ++cnt;
       }
     };
-    take(cell_of(G, i - 1, j, k));
-    take(cell_of(G, i + 1, j, k));
-    take(cell_of(G, i, j - 1, k));
-    take(cell_of(G, i, j + 1, k));
-    take(cell_of(G, i, j, k - 1));
-    take(cell_of(G, i, j, k + 1));
+    take(i - 1, j, k);
+    take(i + 1, j, k);
+    take(i, j - 1, k);
+    take(i, j + 1, k);
+    take(i, j, k - 1);
+    take(i, j, k + 1);
     if (cnt == 0) {
       for (int dk = -1; dk <= 1; ++dk)
         for (int dj = -1; dj <= 1; ++dj)
           for (int di = -1; di <= 1; ++di)
-            if (di || dj || dk) take(cell_of(G, i + di, j + dj, k + dk));
+            if (di || dj || dk) take(i + di, j + dj, k + dk);
     }
     if (cnt == 0) {
       const int old_id = 1 - m;
@@ -372,7 +401,7 @@ __global__ void __launch_bounds__(128) k_phase_fix(const Grid* __restrict__ grid
 #pragma unroll
     for (int v = 0; v < 5; ++v) P[v] = sum[v] / cnt;
     double e, c2;
-    if (!eos_e_c2<double>(q, P[0], 1.0 / P[0], P[4], e, c2)) latch_error(ctrl, M2C_ENONPHYS, c);
+    if (!eos_e_c2<double, true>(q, P[0], 1.0 / P[0], P[4], e, c2)) latch_error(ctrl, M2C_ENONPHYS, c);
     G.W[c] = P[0];
     G.W[N + c] = P[0] * P[1];
     G.W[2 * N + c] = P[0] * P[2];
@@ -429,7 +458,7 @@ __global__ void k_state_to_prims(const Grid* __restrict__ grids, double* __restr
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
     const int m = lt0(G.phi[c]) ? 1 : 0;
     double P[5];
-    if (!cons_to_prim<double>(G.eos[m], G.eos[m], G.W, N, c, P)) latch_error(G.ctrl, M2C_ENONPHYS, c);
+    if (!cons_to_prim<double, true>(G.eos[m], G.eos[m], G.W, N, c, P)) latch_error(G.ctrl, M2C_ENONPHYS, c);
 #pragma unroll
     for (int v = 0; v < 5; ++v) prims[v * N + c] = P[v];
   }
@@ -442,7 +471,7 @@ __global__ void k_prims_to_state(const Grid* __restrict__ grids, const double* _
     const int m = lt0(G.phi[c]) ? 1 : 0;
     const double rho = prims[c], u = prims[N + c], v = prims[2 * N + c], w = prims[3 * N + c], p = prims[4 * N + c];
     double e, c2;
-    if (!eos_e_c2<double>(G.eos[m], rho, 1.0 / rho, p, e, c2)) latch_error(G.ctrl, M2C_ENONPHYS, c);
+    if (!eos_e_c2<double, true>(G.eos[m], rho, 1.0 / rho, p, e, c2)) latch_error(G.ctrl, M2C_ENONPHYS, c);
     G.W[c] = rho;
     G.W[N + c] = rho * u;
     G.W[2 * N + c] = rho * v;
@@ -573,13 +602,32 @@ const char* eos_param_error(int type, const double* prm, int nparams) {
       return "MG needs rho0, c0 > 0, s > 1, Gamma0 > 0";
     return nullptr;
   }
+  if (type == M2C_EOS_NASG) {
+    if (nparams != 4) return "NASG needs 4 params";
+    if (!(prm[0] > 1.0) || !(prm[2] >= 0.0) || !std::isfinite(prm[1]) || !std::isfinite(prm[3]))
+      return "NASG needs gamma > 1, b >= 0 and finite p_c, e_c";
+    return nullptr;
+  }
+  if (type == M2C_EOS_JWL) {
+    if (nparams != 6) return "JWL needs 6 params";
+    if (!(prm[0] > 0.0) || !(prm[3] > 0.0) || !(prm[4] > 0.0) || !(prm[5] > 0.0) || !std::isfinite(prm[1]) ||
+        !std::isfinite(prm[2]))
+      return "JWL needs omega, R1, R2, rho0 > 0 and finite A1, A2";
+    return nullptr;
+  }
   return "unknown EOS type";
 }
 
-// The same for an EOS descriptor of the Riemann entry points (all six params given).
-const char* eos_desc_error(const m2c_eos_desc* e) {
-  return eos_param_error(e->type, e->params, e->type == M2C_EOS_SG ? 2 : 6);
+int eos_nparams(int type) {
+  return type == M2C_EOS_SG ? 2 : (type == M2C_EOS_NASG ? 4 : 6);
 }
+
+// The same for an EOS descriptor of the Riemann entry points (the type's params given).
+const char* eos_desc_error(const m2c_eos_desc* e) {
+  return eos_param_error(e->type, e->params, eos_nparams(e->type));
+}
+
+bool eos_extended(int type) { return type == M2C_EOS_NASG || type == M2C_EOS_JWL; }
 
 // Checks of a grid's sizes, cell edge and boundary conditions shared by
 // m2c_init_grid and m2c_residual_noalloc: nullptr when valid, else the reason.
@@ -589,14 +637,25 @@ const char* grid_args_error(int nx, int ny, int nz, double h, const int* bc) {
     return "a grid needs an axis with more than one cell";
   if ((long long)nx * ny * nz >= (1ll << 31))  // 32-bit cell indices in some kernels
     return "a grid holds fewer than 2^31 cells";
+  const int n[3] = {nx, ny, nz};
   for (int a = 0; a < 3; ++a) {
-    for (int s = 0; s < 2; ++s)
-      if (bc[2 * a + s] != M2C_BC_TRANSMISSIVE && bc[2 * a + s] != M2C_BC_PERIODIC)
+    for (int s = 0; s < 2; ++s) {
+      if (bc[2 * a + s] != M2C_BC_TRANSMISSIVE && bc[2 * a + s] != M2C_BC_PERIODIC &&
+          bc[2 * a + s] != M2C_BC_SYMMETRY)
         return "unknown boundary condition";
+      // the stencils reach two cells across a side: a mirror needs two cells inside
+      if (bc[2 * a + s] == M2C_BC_SYMMETRY && n[a] < 2) return "a symmetry side needs 2 cells along its axis";
+    }
     if ((bc[2 * a] == M2C_BC_PERIODIC) != (bc[2 * a + 1] == M2C_BC_PERIODIC))
       return "periodic on one side of an axis only";
   }
   return nullptr;
+}
+
+bool has_symmetry_side(const int* bc) {
+  for (int s = 0; s < 6; ++s)
+    if (bc[s] == M2C_BC_SYMMETRY) return true;
+  return false;
 }
 
 m2c_status cuda_check(m2c_ctx* c, cudaError_t e, const char* what) {
@@ -729,7 +788,7 @@ cudaError_t record_pair(StageEvents* pe, bool start, cudaStream_t s, int kind = 
 // bulk kernel.
 cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int ngrid, long long ntiles, int prec,
                          const LaunchPlan& lp, bool reinit, int reinit_iters, long long nmax, cudaStream_t s,
-                         StageEvents* pe = nullptr, int rk = 2, bool gen = false) {
+                         StageEvents* pe = nullptr, int rk = 2, bool gen = false, bool band = false) {
   cudaError_t e;
   const dim3 lg((unsigned)(2 * sm_count()), (unsigned)ngrid);
   const dim3 fg((unsigned)(8 * sm_count()), (unsigned)ngrid);
@@ -762,6 +821,10 @@ cudaError_t enqueue_step(const Grid* dev_grids, const long long* dev_tiles, int 
       else M2C_TIMED(kKReinit, (k_reinit<float><<<rg, 256, 0, s>>>(dev_grids, it)));
     }
     M2C_TIMED(kKReinit, (k_copy_phi1<<<rg, 256, 0, s>>>(dev_grids)));
+  }
+  if (band) {
+    const dim3 bg((unsigned)std::min<long long>((nmax + 255) / 256, 8ll * sm_count()), (unsigned)ngrid);
+    M2C_TIMED(kKReinit, (k_band_clip<<<bg, 256, 0, s>>>(dev_grids)));
   }
   M2C_TIMED(kKPhaseFix, (k_phase_fix<<<lg, 128, 0, s>>>(dev_grids)));
   M2C_TIMED(kKEndStep, (k_end_step<<<(ngrid + 63) / 64, 64, 0, s>>>(dev_grids, ngrid)));
@@ -808,6 +871,7 @@ struct m2c_batch {
   int reinit_every = 10, reinit_iters = 5, graph_steps = 0;
   int rk = 2;        // Runge-Kutta scheme of every grid
   bool gen = false;  // some grid has scheme options: the general bulk kernel
+  bool band = false; // some grid has a narrow-band level set
 };
 
 extern "C" {
@@ -878,7 +942,9 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   g.flux = M2C_FLUX_HLLC;
   g.mc_alpha = 1.2;
   g.dt_fixed = 0.0;
-  g.general = 0;
+  g.geom = M2C_GEOM_CARTESIAN;
+  g.x0 = 0.0;
+  g.general = has_symmetry_side(bc) ? 1 : 0;  // mirror loads: the general kernel
   const Layout L3 = layout_for(N, 3);
   if (ws_bytes >= L3.total) {  // room for the second stage state of TVD RK3
     g.W2 = reinterpret_cast<double*>(ws + L3.W2);
@@ -889,7 +955,7 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   c->dev_tiles = reinterpret_cast<long long*>(ws + L.tiles);
   c->stream = static_cast<cudaStream_t>(stream);
   setup_all_stage_kernels();
-  c->ty = default_rows(g);
+  c->ty = g.general ? 8 : default_rows(g);
   set_tiling(g, c->ty, default_tz(g, c->ty));
   c->reinit_every = 10;
   c->reinit_iters = 5;
@@ -916,15 +982,18 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   return M2C_OK;
 }
 
+static void update_general(m2c_ctx* c);
+
 m2c_status m2c_set_eos(m2c_ctx* c, int material, int type, const double* params, int nparams) {
   if (!c) return M2C_EINVAL;
   if (material < 0 || material > 1 || !params) return set_err(c, M2C_EINVAL, "bad material or params");
   if (const char* why = eos_param_error(type, params, nparams)) return set_err(c, M2C_EINVAL, why);
-  double prm[6] = {0, 0, 0, 0, 0, -INFINITY};
+  double prm[6] = {0, 0, 0, 0, 0, type == M2C_EOS_MG ? -INFINITY : 0.0};
   for (int i = 0; i < (type == M2C_EOS_SG ? 2 : nparams); ++i) prm[i] = params[i];
   c->host.eos[material] = make_eos<double>(type, prm);
   c->host.eosf[material] = make_eos<float>(type, prm);
   c->eos_set[material] = true;
+  update_general(c);
   return push_grid(c);
 }
 
@@ -939,6 +1008,19 @@ m2c_status m2c_set_scheme(m2c_ctx* c, double cfl, int reinit_every, int reinit_i
   return push_grid(c);
 }
 
+// The general bulk kernel serves every grid with a scheme option, a symmetry
+// side or a NASG / JWL material; it runs 8-row tiles.
+static void update_general(m2c_ctx* c) {
+  Grid& g = c->host;
+  g.general = (g.rk == 3 || g.limiter != M2C_LIM_VAN_ALBADA || g.flux != M2C_FLUX_HLLC ||
+               g.geom != M2C_GEOM_CARTESIAN || has_symmetry_side(g.bc) || eos_extended(g.eos[0].type) ||
+               eos_extended(g.eos[1].type) || g.band_gamma > 0.0) ? 1 : 0;
+  if (g.general && c->ty != 8) {
+    c->ty = 8;
+    set_tiling(g, 8, default_tz(g, 8));
+  }
+}
+
 m2c_status m2c_set_options(m2c_ctx* c, const m2c_options* o) {
   if (!c) return M2C_EINVAL;
   if (!o) return set_err(c, M2C_EINVAL, "options are NULL");
@@ -948,6 +1030,16 @@ m2c_status m2c_set_options(m2c_ctx* c, const m2c_options* o) {
   if (o->limiter == M2C_LIM_MC && !(o->mc_alpha >= 1.0 && o->mc_alpha <= 2.0))
     return set_err(c, M2C_EINVAL, "the MC limiter needs 1 <= alpha <= 2");
   if (!(o->dt_fixed >= 0.0) || !std::isfinite(o->dt_fixed)) return set_err(c, M2C_EINVAL, "dt_fixed must be >= 0");
+  if (o->geom != M2C_GEOM_CARTESIAN && o->geom != M2C_GEOM_CYLINDRICAL && o->geom != M2C_GEOM_SPHERICAL)
+    return set_err(c, M2C_EINVAL, "unknown geometry");
+  if (o->geom != M2C_GEOM_CARTESIAN && !(o->x0 >= 0.0 && std::isfinite(o->x0)))
+    return set_err(c, M2C_EINVAL, "the radius x0 of the first face must be >= 0");
+  if (o->geom == M2C_GEOM_SPHERICAL && (c->host.ny != 1 || c->host.nz != 1))
+    return set_err(c, M2C_EINVAL, "the spherical form is one-dimensional (ny = nz = 1)");
+  if (o->geom == M2C_GEOM_CYLINDRICAL && c->host.ny != 1)
+    return set_err(c, M2C_EINVAL, "the cylindrical form is (r, z): ny = 1");
+  if (!(o->band_gamma >= 0.0) || (o->band_gamma > 0.0 && !(o->band_beta > 0.0 && o->band_beta < o->band_gamma)))
+    return set_err(c, M2C_EINVAL, "a narrow band needs 0 < band_beta < band_gamma (cells)");
   if (o->rk == 3 && !c->host.W2)
     return set_err(c, M2C_ENOMEM, "TVD RK3 needs a workspace of m2c_workspace_bytes_rk(nx, ny, nz, precision, 3)");
   Grid& g = c->host;
@@ -956,12 +1048,11 @@ m2c_status m2c_set_options(m2c_ctx* c, const m2c_options* o) {
   g.flux = o->flux;
   g.mc_alpha = o->limiter == M2C_LIM_MC ? o->mc_alpha : 1.2;
   g.dt_fixed = o->dt_fixed;
-  g.general = (g.rk == 3 || g.limiter != M2C_LIM_VAN_ALBADA || g.flux != M2C_FLUX_HLLC) ? 1 : 0;
-  if (g.general && c->ty != 8) {  // the general kernel runs 8-row tiles
-    c->ty = 8;
-    set_tiling(g, 8, default_tz(g, 8));
-  }
-  c->lam_valid = false;  // a constant time step replaces the reduced one from the next step
+  g.geom = o->geom;
+  g.x0 = o->geom != M2C_GEOM_CARTESIAN ? o->x0 : 0.0;
+  g.band_beta = o->band_gamma > 0.0 ? o->band_beta * g.h : 0.0;
+  g.band_gamma = o->band_gamma > 0.0 ? o->band_gamma * g.h : 0.0;
+  update_general(c);
   return push_grid(c);
 }
 
@@ -1060,7 +1151,7 @@ m2c_status m2c_step(m2c_ctx* c, int nsteps) {
     lp.ty = c->ty;
     cudaError_t e = enqueue_step(c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), c->host.prec, lp, re,
                                  c->reinit_iters, c->host.N, c->stream, c->profiling ? &pe : nullptr, c->host.rk,
-                                 c->host.general != 0);
+                                 c->host.general != 0, c->host.band_gamma > 0.0);
     if (e != cudaSuccess) return cuda_check(c, e, "step launch");
     ++c->host_step;
   }
@@ -1120,6 +1211,7 @@ m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace
   b->prec = v[0]->host.prec;
   b->rk = v[0]->host.rk;
   b->gen = gen;
+  for (int i = 0; i < k; ++i) b->band = b->band || v[i]->host.band_gamma > 0.0;
   b->stream = v[0]->stream;
   b->step = v[0]->host_step;
   b->reinit_every = v[0]->reinit_every;
@@ -1153,7 +1245,7 @@ static m2c_status batch_enqueue(m2c_batch* b, int nsteps, cudaStream_t s) {
     // grids of a batch may be at different steps: the reinitialisation kernels
     // are enqueued every step and each grid checks its own schedule
     cudaError_t e = enqueue_step(b->dev, b->dtiles, k, b->tiles[k], b->prec, b->lp, b->reinit_iters > 0,
-                                 b->reinit_iters, b->nmax, s, nullptr, b->rk, b->gen);
+                                 b->reinit_iters, b->nmax, s, nullptr, b->rk, b->gen, b->band);
     if (e != cudaSuccess) return cuda_check(b->ctx[0], e, "batch step launch");
     ++b->step;
     for (m2c_ctx* c : b->ctx) ++c->host_step;
@@ -1448,6 +1540,10 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
     return noalloc_fail(M2C_EINVAL, std::string("m2c_residual_noalloc: ") + why);
   if (precision != M2C_FP64 && precision != M2C_MIXED)
     return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: bad precision");
+  if (has_symmetry_side(bc))
+    return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: transmissive and periodic sides only");
+  if (eos_extended(eos0->type) || eos_extended(eos1->type))
+    return noalloc_fail(M2C_EINVAL, "m2c_residual_noalloc: stiffened-gas and Mie-Grueneisen materials only");
   // the EOS rules of m2c_set_eos: an unknown type or a parameter outside its
   // range is rejected before any device work
   if (const char* why = eos_desc_error(eos0))

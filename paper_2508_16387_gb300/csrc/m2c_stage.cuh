@@ -190,11 +190,26 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     halo_base[s] = h_hx[s] < 0 ? 0
                                : (long long)map_index(y0 + h_hy[s] - 2, ny, G.bc[2], G.bc[3]) * nx +
                                      map_index(x0 + h_hx[s] - 2, nx, G.bc[0], G.bc[1]);
+  // general kernel: velocity components to negate for a position mirrored across a
+  // symmetry side (bit 0: u, bit 1: v, bit 2: w), for the own column and the halo slots
+  int own_neg = 0, halo_neg[HI];
+#pragma unroll
+  for (int s = 0; s < HI; ++s) halo_neg[s] = 0;
+  if constexpr (GEN) {
+    own_neg = mirrored(gx, nx, G.bc[0], G.bc[1]) | (mirrored(gy, ny, G.bc[2], G.bc[3]) << 1);
+#pragma unroll
+    for (int s = 0; s < HI; ++s)
+      if (h_hx[s] >= 0)
+        halo_neg[s] = mirrored(x0 + h_hx[s] - 2, nx, G.bc[0], G.bc[1]) |
+                      (mirrored(y0 + h_hy[s] - 2, ny, G.bc[2], G.bc[3]) << 1);
+  }
+  auto zneg = [&](int k) { return GEN ? (mirrored(k, nz, bcz0, bcz1) << 2) : 0; };
 
   // failures seen by this thread in this tile: non-physical state, work-list overflow
   bool bad = false, ovf = false;
   // material at the start of the step and the stage state of cell index c
-  auto load = [&](long long c, R P[5], R& ph, int& idv) {
+  // (neg: the velocity components to negate, general kernel only)
+  auto load = [&](long long c, R P[5], R& ph, int& idv, int neg) {
     const double phd = phis[c];
     if (ids_frozen) {
       idv = idg[c] & 1;
@@ -202,7 +217,12 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       idv = lt0(phd) ? 1 : 0;
     }
     ph = to_r<R>(phd);
-    if (!cons_to_prim<R>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) bad = true;
+    if (!cons_to_prim<R, GEN>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) bad = true;
+    if constexpr (GEN) {
+      if (neg & 1) P[1] = -P[1];
+      if (neg & 2) P[2] = -P[2];
+      if (neg & 4) P[3] = -P[3];
+    }
   };
   auto plane = [&](int k) { return (long long)map_index(k, nz, bcz0, bcz1) * nxy; };
 
@@ -215,10 +235,10 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   {
     R Pb[5];
     int idb;
-    load(plane(k0 - 2) + own_base, Pb, ph[0], idb);
-    load(plane(k0 - 1) + own_base, Pa, ph[1], ida);
-    load(plane(k0) + own_base, P0, ph[2], id0);
-    load(plane(k0 + 1) + own_base, P1, ph[3], id1);
+    load(plane(k0 - 2) + own_base, Pb, ph[0], idb, own_neg | zneg(k0 - 2));
+    load(plane(k0 - 1) + own_base, Pa, ph[1], ida, own_neg | zneg(k0 - 1));
+    load(plane(k0) + own_base, P0, ph[2], id0, own_neg);
+    load(plane(k0 + 1) + own_base, P1, ph[3], id1, own_neg | zneg(k0 + 1));
     FaceState<R> QaP, Q0M;
     cell_faces<R, GEN>(s_eos[ida], Pb, Pa, P0, idb == ida && id0 == ida, Qtmp, QaP, bad, lim, alpha);
     cell_faces<R, GEN>(s_eos[id0], Pa, P0, P1, ida == id0 && id1 == id0, Q0M, QzP, bad, lim, alpha);
@@ -240,7 +260,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     R* const s_phi = s_phi0 + buf * PL;
     uint8_t* const s_id = s_id0 + buf * PL;
     // ---- own column: plane k+2, z face states of cell k+1, z flux of face k+1/2
-    load(plane(k + 2) + own_base, P2, ph[4], id2);
+    load(plane(k + 2) + own_base, P2, ph[4], id2, own_neg | zneg(k + 2));
     cell_faces<R, GEN>(s_eos[id1], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad, lim, alpha);
     if (id0 == id1) {
       num_flux<2, R, GEN>(QzP, QzM1, Fzp, flx);
@@ -259,7 +279,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       const int hslot = h_hy[s] * HX + h_hx[s];
       R Ph[5], phh;
       int idh;
-      load(pk + halo_base[s], Ph, phh, idh);
+      load(pk + halo_base[s], Ph, phh, idh, halo_neg[s]);
 #pragma unroll
       for (int v = 0; v < 5; ++v) s_q[v * PL + hslot] = Ph[v];
       s_phi[hslot] = phh;
@@ -342,9 +362,28 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       else Dy = ((-prow[2 * HX] + (R)6 * prow[HX]) - (R)3 * prow[0] - (R)2 * prow[-HX]) * i6h;
       if (w >= (R)0) Dz = (((R)2 * ph[3] + (R)3 * ph[2]) - (R)6 * ph[1] + ph[0]) * i6h;
       else Dz = ((-ph[4] + (R)6 * ph[3]) - (R)3 * ph[2] - (R)2 * ph[1]) * i6h;
-      const R Lphi = -((u * Dx + vv * Dy) + w * Dz);
+      R Lphi = -((u * Dx + vv * Dy) + w * Dz);
+      if constexpr (GEN) {
+        // narrow band (Sec. 4.4): the velocity scaled by the cutoff of the cell's level set
+        if (G.band_gamma > 0.0) Lphi = band_cutoff<R>((R)G.band_beta, (R)G.band_gamma, ph[2]) * Lphi;
+      }
 
       const long long c = pk + own_base;
+      if constexpr (GEN) {
+        // spherical / cylindrical forms (Sec. 3.4): S = -(alpha/r) u_r (rho, rho u, rho v,
+        // rho w, rho E + p) at the cell centre r = x0 + (i + 1/2) h from the stage state,
+        // added after the flux sum (interface cells get it in k_finish)
+        if (G.geom != M2C_GEOM_CARTESIAN && inside && !is_if) {
+          const double r = G.x0 + ((double)gx + 0.5) * G.h;
+          const R a = to_r<R>((G.geom == M2C_GEOM_SPHERICAL ? 2.0 : 1.0) / r) * P0[1];
+          R wv[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) wv[v] = to_r<R>(Ws[v * N + c]);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) res[v] = res[v] - a * wv[v];
+          res[4] = res[4] - a * (wv[4] + P0[4]);
+        }
+      }
       bool flip = false;
       if (inside) {
         if (mode == kResidual) {
@@ -390,7 +429,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
             }
             if (!flip) {
               bool ok;
-              const R lam = wave_sum_v<R>(G, s_eos[id0], s_eosd[id0], wn, ok);
+              const R lam = wave_sum_v<R, GEN>(G, s_eos[id0], s_eosd[id0], wn, ok);
               bad = bad || !ok;
               lam_max = fmax(lam_max, lam);
             }

@@ -21,9 +21,10 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENONP
           7: "ETIMEOUT", 8: "EOVERFLOW"}
 EOS_SG, EOS_MG = 0, 1
 FP64, MIXED = 0, 1
-BC_TRANSMISSIVE, BC_PERIODIC = 0, 1
+BC_TRANSMISSIVE, BC_PERIODIC, BC_SYMMETRY = 0, 1, 2
 LIM_VAN_ALBADA, LIM_MC = 0, 1
 FLUX_HLLC, FLUX_LLF = 0, 1
+GEOM_CARTESIAN, GEOM_CYLINDRICAL, GEOM_SPHERICAL = 0, 1, 2
 
 
 class M2CError(RuntimeError):
@@ -38,7 +39,8 @@ class EosDesc(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("rk", ctypes.c_int), ("limiter", ctypes.c_int), ("flux", ctypes.c_int),
-                ("mc_alpha", ctypes.c_double), ("dt_fixed", ctypes.c_double)]
+                ("mc_alpha", ctypes.c_double), ("dt_fixed", ctypes.c_double), ("geom", ctypes.c_int),
+                ("x0", ctypes.c_double), ("band_beta", ctypes.c_double), ("band_gamma", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -244,9 +246,10 @@ class Grid:
 
     def __init__(self, n, h, bc, eos, precision=FP64, cfl=0.5, reinit_every=10, reinit_iters=5,
                  device="cuda", stream=None, options=None):
-        """options: None (TVD RK2, modified van Albada, HLLC, CFL time step) or a dict of
-        m2c_set_options fields (rk, limiter, flux, mc_alpha, dt_fixed); rk = 3 sizes the
-        workspace for the second stage state."""
+        """options: None (TVD RK2, modified van Albada, HLLC, CFL time step, Cartesian) or a
+        dict of m2c_set_options fields (rk, limiter, flux, mc_alpha, dt_fixed, geom, x0, band_beta,
+        band_gamma);
+        rk = 3 sizes the workspace for the second stage state."""
         import torch
         self.torch = torch
         self.n = tuple(n)
@@ -256,7 +259,8 @@ class Grid:
         self.precision = precision
         self.device = torch.device(device)
         self.stream = stream
-        opts = dict(rk=2, limiter=LIM_VAN_ALBADA, flux=FLUX_HLLC, mc_alpha=1.2, dt_fixed=0.0)
+        opts = dict(rk=2, limiter=LIM_VAN_ALBADA, flux=FLUX_HLLC, mc_alpha=1.2, dt_fixed=0.0,
+                    geom=GEOM_CARTESIAN, x0=0.0, band_beta=0.0, band_gamma=0.0)
         opts.update(options or {})
         wsb = m2c_workspace_bytes_rk(nx, ny, nz, precision, opts["rk"])
         self.workspace = torch.empty(wsb + 256, dtype=torch.uint8, device=self.device)
@@ -279,8 +283,9 @@ class Grid:
         if options:
             self.set_options(**opts)
 
-    def set_options(self, rk=2, limiter=LIM_VAN_ALBADA, flux=FLUX_HLLC, mc_alpha=1.2, dt_fixed=0.0):
-        o = Options(rk, limiter, flux, mc_alpha, dt_fixed)
+    def set_options(self, rk=2, limiter=LIM_VAN_ALBADA, flux=FLUX_HLLC, mc_alpha=1.2, dt_fixed=0.0,
+                    geom=GEOM_CARTESIAN, x0=0.0, band_beta=0.0, band_gamma=0.0):
+        o = Options(rk, limiter, flux, mc_alpha, dt_fixed, geom, x0, band_beta, band_gamma)
         _check(lib().m2c_set_options(self.ctx, ctypes.byref(o)), "m2c_set_options", self.ctx)
 
     def __del__(self):

@@ -41,6 +41,11 @@ SHOCKED = 2
 WATER_SG = (EOS_SG, (6.12, 3.43e8))                         # stiffened gas
 WATER_MG = (EOS_MG, (1000.0, 1483.0, 1.75, 0.28, 0.0, -math.inf))  # Mie-Grueneisen
 AIR_PG = (EOS_SG, (1.4, 0.0))                                # perfect gas
+EOS_NASG, EOS_JWL = 2, 3
+# synthetic Noble-Abel stiffened-gas liquid (gamma, p_c, b, e_c) and detonation products
+# (JWL: omega, A1, A2, R1, R2, rho0); parameter sets of the size such materials have
+LIQUID_NASG = (EOS_NASG, (1.5, 5.0e8, 5.0e-4, -1.0e6))
+PRODUCTS_JWL = (EOS_JWL, (0.3, 4.0e11, 4.0e9, 4.5, 1.0, 1600.0))
 
 
 @dataclass
@@ -205,10 +210,13 @@ def served_trace(n_jobs: int = 200, rate: float = 20.0, seed: int = 4, edge_rang
     return jobs
 
 
-def random_state(n: tuple, seed: int, eos=(WATER_SG, AIR_PG), two_phase: bool = True, amp: float = 0.05):
+def random_state(n: tuple, seed: int, eos=(WATER_SG, AIR_PG), two_phase: bool = True, amp: float = 0.05,
+                 base=None):
     """Smooth random single- or two-material test state on an (nx, ny, nz) grid with h = 1/nx:
-    primitive fields of moderate amplitude around water and air reference states, and a
-    level set that is a randomly placed sphere (two_phase) or all positive."""
+    primitive fields of moderate amplitude around reference states (density, pressure) of
+    material 0 (phi >= 0) and 1 (phi < 0), water- and air-like unless ``base`` = {0: (rho, p),
+    1: (rho, p)} gives others, and a level set that is a randomly placed sphere (two_phase) or
+    all positive."""
     rng = np.random.Generator(np.random.PCG64(seed))
     h = 1.0 / n[0]
     x, y, z = cell_centres(n, h)
@@ -220,7 +228,7 @@ def random_state(n: tuple, seed: int, eos=(WATER_SG, AIR_PG), two_phase: bool = 
     else:
         phi = np.ones(shape)
     P = np.zeros((5,) + shape)
-    base = {0: (1000.0, 1e8), 1: (1.2, 1e5)}
+    base = base or {0: (1000.0, 1e8), 1: (1.2, 1e5)}
     vel = {0: 50.0, 1: 50.0}
     for m in (0, 1):
         sel = (phi < 0.0) if m == 1 else (phi >= 0.0)

@@ -69,7 +69,8 @@ def test_riemann_entry_rejects_bad_eos_before_any_device_work(left, right, why):
 @pytest.mark.parametrize("n,bc,why", [
     ((1, 1, 1), (0,) * 6, "a grid needs an axis with more than one cell"),
     ((8, 8, 8), (1, 0, 0, 0, 0, 0), "periodic on one side of an axis only"),
-    ((8, 8, 8), (2, 2, 0, 0, 0, 0), "unknown boundary condition"),
+    ((8, 8, 8), (3, 3, 0, 0, 0, 0), "unknown boundary condition"),
+    ((1, 8, 8), (2, 0, 0, 0, 0, 0), "a symmetry side needs 2 cells along its axis"),
     ((0, 8, 8), (0,) * 6, "grid sizes >= 1"),
 ])
 def test_init_grid_rejects_bad_grids_before_any_device_work(n, bc, why):

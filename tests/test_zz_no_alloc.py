@@ -75,6 +75,7 @@ def test_noalloc_rejects_grids_above_its_maximum(m2c):
      "material 0 EOS: MG needs rho0, c0 > 0, s > 1"),
     (WL.WATER_SG, WL.AIR_PG, (0, 0, 9, 9, 0, 0), "unknown boundary condition"),
     (WL.WATER_SG, WL.AIR_PG, (1, 0, 0, 0, 0, 0), "periodic on one side of an axis only"),
+    (WL.WATER_SG, WL.AIR_PG, (2, 0, 0, 0, 0, 0), "transmissive and periodic sides only"),
 ])
 def test_noalloc_rejects_bad_eos_and_boundaries_before_any_device_work(eos0, eos1, bc, why):
     """The EOS and boundary rules of m2c_set_eos and m2c_init_grid apply to the allocation-free
