@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--jobs", type=int, default=200)
     ap.add_argument("--serial-jobs", type=int, default=16)
     ap.add_argument("--slice-steps", type=int, default=25)
+    ap.add_argument("--late-steps", type=int, default=50,
+                    help="steps timed after the untimed advance of the L1 check (late window; 0: skip)")
+    ap.add_argument("--sub-batch-steps", type=int, default=20,
+                    help="steps of the batched sub-run of the default line (0: skip)")
+    ap.add_argument("--sub-served-jobs", type=int, default=16,
+                    help="jobs of the served sub-run of the default line (0: skip)")
     return ap.parse_args()
 
 
@@ -204,17 +210,28 @@ def e2e_run(torch, M, s, g, steps):
     return dt, nbytes
 
 
-def l1_vs_fp64(torch, M, s, steps):
+def l1_vs_fp64(torch, M, s, steps, late_steps=0):
     """Mixed against FP64 on the same workload after `steps` steps from the same initial state:
     relative L1 of 4^3-block averages (n^3 -> (n/4)^3) of density and pressure, from the
-    library's own FP64 primitive fields."""
-    prims = {}
+    library's own FP64 primitive fields. With late_steps, each grid is then timed over that many
+    more steps (a late window: the shock is inside the bubble, interface work at its largest),
+    mixed and FP64 (a fifth of the steps), with CUDA events on the grid's stream."""
+    prims, late = {}, {}
     for prec in (M.MIXED, M.FP64):
         g = make_grid(M, s, prec)
         g.step(steps)
         g.sync()
         prims[prec] = g.prims()
         g.sync()
+        k = late_steps if prec == M.MIXED else max(1, late_steps // 5)
+        if late_steps > 0:
+            with ClockSampler(torch.cuda.current_device()) as clk:
+                ms, _, _ = time_steps(torch, g, k, 0, breakdown=prec == M.MIXED)
+            late["mixed" if prec == M.MIXED else "fp64"] = {
+                "value": round(s.ncells * k / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "steps": k,
+                "from_step": steps, "ms_per_step": round(ms / k, 4), "clocks": clk.summary(),
+                **({"step_breakdown_ms": {kk: round(v[0] / k, 4) for kk, v in time_steps.kernels.items()},
+                    "interface_faces": g.stats().interface_faces} if prec == M.MIXED else {})}
         del g
 
     def blocks(a):
@@ -226,7 +243,64 @@ def l1_vs_fp64(torch, M, s, steps):
         res[name] = float((a - b).abs().sum() / b.abs().sum())
     del prims
     torch.cuda.empty_cache()
+    l1_vs_fp64.late = late
     return res
+
+
+def batched_run(torch, M, instances, steps, tune=True):
+    """The batched workload: `instances` shock-bubble grids (edges from {32, 48, 64, 96, 128},
+    radius, centre and shock pressure from seed 3) stepped together `steps` steps in one captured
+    CUDA graph, mixed and FP64, after the autotuner has picked the tile shape, schedule and
+    persistent grid size; CUDA events around the graph launch."""
+    from paper_2508_16387_gb300 import autotune as AT
+    from paper_2508_16387_gb300 import workloads as WL
+    setups = WL.batched_instances(count=instances, seed=3, steps=steps)
+    N = sum(x.ncells for x in setups)
+    res = {}
+    for name, prec in (("mixed", M.MIXED), ("fp64", M.FP64)):
+        grids = [make_grid(M, x, prec) for x in setups]
+        cands = AT.DEFAULT_CANDIDATES if prec == M.MIXED else AT.FP64_CANDIDATES
+        best, trials = AT.tune_batch(grids, candidates=cands, trial_steps=2) if tune else ((8, 0, 0, 0), [])
+        bt = M.Batch(grids, best)
+        t0 = time.perf_counter()
+        bt.capture(steps)
+        cap_s = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(torch.cuda.current_stream())
+            bt.launch_graph()
+            e1.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        for g in grids:
+            g.sync()
+        res[name] = {"value": round(N * steps / (ms * 1e-3) / 1e6, 2), "unit": UNIT, "ms": round(ms, 2),
+                     "tuning": {"tile_rows": best[0], "tile_z": best[1], "schedule": ["stride", "atomic"][best[2]],
+                                "blocks_per_sm": best[3]},
+                     "autotune_trials": len(trials), "capture_s": round(cap_s, 2), "clocks": clk.summary()}
+        del bt, grids
+        torch.cuda.empty_cache()
+    return {"workload": f"batched_{instances}_grids_seed3", "cells": N, "steps": steps,
+            "edges": sorted({x.n[0] for x in setups}), "graph": True, **res}
+
+
+def served_run(M, jobs, slice_steps):
+    """Serving a trace: continuous batching in mixed precision against serving the same jobs one
+    at a time in plain FP64 (arrival times honoured); p50/p99 latency (arrival to result on the
+    host) and Mcell-updates/s over the wall time of each."""
+    from paper_2508_16387_gb300 import serve as S
+
+    def summary(st):
+        ok = sum(1 for r in st.results if r.status == 0)
+        return {"jobs": len(st.results), "ok": ok, "wall_s": round(st.wall_s, 2),
+                "value": round(st.cell_updates / st.wall_s / 1e6, 2), "unit": UNIT,
+                "p50_latency_s": round(st.percentile(50), 3), "p99_latency_s": round(st.percentile(99), 3),
+                "max_resident": st.max_resident, "slices": st.slices}
+    cont = S.Server(precision=M.MIXED, slice_steps=slice_steps).run(jobs, realtime=True)
+    ser = S.serve_serial(jobs, precision=M.FP64, realtime=True)
+    return {"continuous_mixed": summary(cont), "serial_fp64": summary(ser)}
 
 
 def peaks():
@@ -277,6 +351,23 @@ def ncu_traffic(kind, n):
     """DRAM read + write bytes per launch of the bulk stage kernel (dram__bytes_read.sum +
     dram__bytes_write.sum)."""
     return _ncu_per_launch(f"{kind}_bytes_per_launch_256", n)
+
+
+def fp64_flops_per_cell_update():
+    """FP64 operations per cell-update of the 256^3 MG shock-bubble workload, counted by the
+    op-counting build of the oracle (committed summary; None if absent)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_flops_per_cell_update.txt")) as f:
+            for line in f:
+                if line.startswith("flops_per_cell_update_256_mg_shock_bubble"):
+                    return float(line.split("=")[1])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# GB300 FP64 rate: 1.89 DFMA per clock per SM (own probe on this pool's GB300), 2 FLOPs each
+FP64_DFMA_PER_CLK_SM = 1.89
 
 
 def issue_roofline(warp_inst, kernel_ms, sms, sm_mhz):
@@ -374,21 +465,45 @@ def run_ours(args):
     if not args.no_fp64:
         g64 = make_grid(M, s, M.FP64)
         k64 = max(5, args.steps // 2)
-        ms64, kms64, kl64 = time_steps(torch, g64, k64, args.warmup, barrier, breakdown=False)
+        with ClockSampler(local) as clk64:
+            ms64, kms64, kl64 = time_steps(torch, g64, k64, args.warmup, barrier, breakdown=False)
         avg64 = kms64 / max(kl64, 1)
+        fpc = fp64_flops_per_cell_update()
+        mhz = clk64.summary()["sm_mhz"] or 2070.0
+        peak64 = FP64_DFMA_PER_CLK_SM * 2 * sms * mhz * 1e6 / 1e12
+        ach = fpc * N * k64 / (ms64 * 1e-3) / 1e12 if fpc else None
         fp64 = {"value": round(N * k64 / (ms64 * 1e-3) / 1e6, 2), "unit": UNIT, "steps": k64,
-                "ms_per_step": round(ms64 / k64, 3), "dtype": "f64",
-                "roofline": {"bound": "alu", "pipe": "fp64", "peak": 1.25, "unit": "TFLOP/s",
-                             "peak_source": "nominal GB300 FP64 rate (1.9 DFMA/clk/SM measured)",
+                "ms_per_step": round(ms64 / k64, 3), "dtype": "f64", "clocks": clk64.summary(),
+                "roofline": {"bound": "alu", "pipe": "fp64",
+                             "achieved": round(ach, 4) if ach else None, "peak": round(peak64, 4), "unit": "TFLOP/s",
+                             "frac": round(ach / peak64, 4) if ach else None,
+                             "flops_per_cell_update": fpc,
+                             "flops_source": "op-counting build of the oracle (profiles/fp64_flops_per_cell_update.txt)"
+                                             "; add, mul, div, sqrt one FLOP each; achieved over the whole step",
+                             "peak_source": "measured 1.89 DFMA/clk/SM x 2 FLOPs x SMs x median sampled SM clock",
                              "fp64_pipe_busy_ncu": 0.74, "kernel": "k_stage<double,8> (bulk stage)",
                              "kernel_ms_avg": round(avg64, 4), "traffic": ncu_traffic("fp64", args.n),
                              "hbm_frac": round(alg_bytes / (avg64 * 1e-3) / 1e9 / hbm, 4)}}
         del g64
     if rank != 0:
         return
-    l1 = None
+    l1, late = None, None
     if args.prec == "mixed" and not args.no_fp64 and args.l1_steps > 0:
-        l1 = l1_vs_fp64(torch, M, s, args.l1_steps)
+        l1 = l1_vs_fp64(torch, M, s, args.l1_steps, args.late_steps if ws == 1 else 0)
+        late = l1_vs_fp64.late or None
+    # sub-runs of the batched and served workloads (one GPU only: they are not weak-scaling runs)
+    batched, served = None, None
+    if ws == 1 and args.sub_batch_steps > 0:
+        batched = batched_run(torch, M, args.instances, args.sub_batch_steps)
+    if ws == 1 and args.sub_served_jobs > 0:
+        from paper_2508_16387_gb300 import workloads as WL
+        jobs = WL.served_trace(n_jobs=args.jobs, rate=20.0, seed=4)[:args.sub_served_jobs]
+        with ClockSampler(local) as sclk:
+            served = served_run(M, jobs, args.slice_steps)
+        served.update({"workload": f"first_{len(jobs)}_jobs_of_served_200_jobs_poisson20_seed4",
+                       "clocks": sclk.summary(),
+                       "p50_s": served["continuous_mixed"]["p50_latency_s"],
+                       "p99_s": served["continuous_mixed"]["p99_latency_s"]})
     out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -398,7 +513,8 @@ def run_ours(args):
                       "l2": f"state ({48 * N / 1e6:.0f} MB) larger than L2, no flush"
                             if 48 * N > 129e6 else f"state ({48 * N / 1e6:.0f} MB) fits in L2"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "fp64": fp64,
-           "mixed_fp32_riemann_start": fp32_start, "l1_error_vs_fp64": l1}
+           "mixed_fp32_riemann_start": fp32_start, "l1_error_vs_fp64": l1, "late_window": late,
+           "batched": batched, "served": served}
     if not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out))
@@ -438,56 +554,24 @@ def run_reference(args):
 
 
 def run_batched(args):
-    """64 shock-bubble grids with edges drawn from {32, 48, 64, 96, 128}, radius, centre and shock
-    pressure drawn from seed 3, stepped together 200 steps in one captured CUDA graph, after the
-    autotuner has picked the tile shape, schedule and persistent grid size."""
+    """The batched workload alone (--workload batched): 200 steps in one captured CUDA graph."""
     import torch
-    from paper_2508_16387_gb300 import autotune as AT
     from paper_2508_16387_gb300 import m2c as M
-    from paper_2508_16387_gb300 import workloads as WL
     torch.cuda.set_device(dist_env()[2])
     M.lib()
-    setups = WL.batched_instances(count=args.instances, seed=3, steps=args.batch_steps)
-    N = sum(s.ncells for s in setups)
-    res = {}
-    for name, prec in (("mixed", M.MIXED), ("fp64", M.FP64)):
-        grids = [make_grid(M, s, prec) for s in setups]
-        cands = AT.DEFAULT_CANDIDATES if prec == M.MIXED else AT.FP64_CANDIDATES
-        best, trials = AT.tune_batch(grids, candidates=cands, trial_steps=2)
-        bt = M.Batch(grids, best)
-        t0 = time.perf_counter()
-        bt.capture(args.batch_steps)
-        cap_s = time.perf_counter() - t0
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        with ClockSampler(dist_env()[2]) as clk:
-            e0.record(torch.cuda.current_stream())
-            bt.launch_graph()
-            e1.record(torch.cuda.current_stream())
-            torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        for g in grids:
-            g.sync()
-        res[name] = {"value": round(N * args.batch_steps / (ms * 1e-3) / 1e6, 2), "ms": round(ms, 1),
-                     "tuning": {"tile_rows": best[0], "tile_z": best[1], "schedule": ["stride", "atomic"][best[2]],
-                                "blocks_per_sm": best[3]},
-                     "autotune_trials": len(trials), "capture_s": round(cap_s, 2), "clocks": clk.summary()}
-        del bt, grids
-        torch.cuda.empty_cache()
+    res = batched_run(torch, M, args.instances, args.batch_steps)
     print(json.dumps({"metric": "Mcell-updates/s, uneven shock-bubble grids stepped in one CUDA graph",
                       "value": res["mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.batch_steps,
                       "higher_is_better": True, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-                      "config": {"workload": f"batched_{args.instances}_grids_seed3", "cells": N,
-                                 "edges": sorted({s.n[0] for s in setups})},
+                      "config": {"workload": res["workload"], "cells": res["cells"], "edges": res["edges"]},
                       "mixed": res["mixed"], "fp64": res["fp64"]}))
 
 
 def run_served(args):
     """Poisson arrivals at 20 jobs/s of shock-bubble jobs (edge log-uniform on [48, 192], 100-1000
-    steps, seed 4) served with continuous batching in mixed precision; the first `--serial-jobs`
-    jobs of the trace are also served one at a time in plain FP64 and with continuous batching,
-    for a same-trace comparison."""
+    steps, seed 4) served with continuous batching in mixed precision (--workload served); the
+    first `--serial-jobs` jobs of the trace are also served one at a time in plain FP64 and with
+    continuous batching, for a same-trace comparison."""
     import torch
     from paper_2508_16387_gb300 import m2c as M
     from paper_2508_16387_gb300 import serve as S
@@ -495,26 +579,21 @@ def run_served(args):
     torch.cuda.set_device(dist_env()[2])
     M.lib()
     jobs = WL.served_trace(n_jobs=args.jobs, rate=20.0, seed=4)
-
-    def summary(st):
-        ok = sum(1 for r in st.results if r.status == 0)
-        return {"jobs": len(st.results), "ok": ok, "wall_s": round(st.wall_s, 2),
-                "value": round(st.cell_updates / st.wall_s / 1e6, 2),
-                "p50_latency_s": round(st.percentile(50), 3), "p99_latency_s": round(st.percentile(99), 3),
-                "max_resident": st.max_resident, "slices": st.slices}
     with ClockSampler(dist_env()[2]) as clk:
         full = S.Server(precision=M.MIXED, slice_steps=args.slice_steps).run(jobs, realtime=True)
-    sub = jobs[:args.serial_jobs]
-    cont = S.Server(precision=M.MIXED, slice_steps=args.slice_steps).run(sub, realtime=True)
-    ser = S.serve_serial(sub, precision=M.FP64, realtime=True)
+    ok = sum(1 for r in full.results if r.status == 0)
+    full_s = {"jobs": len(full.results), "ok": ok, "wall_s": round(full.wall_s, 2),
+              "value": round(full.cell_updates / full.wall_s / 1e6, 2),
+              "p50_latency_s": round(full.percentile(50), 3), "p99_latency_s": round(full.percentile(99), 3),
+              "max_resident": full.max_resident, "slices": full.slices}
+    sub = served_run(M, jobs[:args.serial_jobs], args.slice_steps)
     offered = sum(j.params.edge ** 3 * j.params.steps for j in jobs) / jobs[-1].arrival
     out = {"metric": "served shock-bubble jobs: Mcell-updates/s and p50/p99 job latency",
-           "value": summary(full)["value"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+           "value": full_s["value"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
            "dtype": "f32+f64 (mixed)", "data": "synthetic",
            "config": {"workload": f"served_{args.jobs}_jobs_poisson20_seed4", "slice_steps": args.slice_steps,
                       "offered_Mcell_updates_per_s": round(offered / 1e6, 1)},
-           "served_mixed": summary(full), "clocks": clk.summary(),
-           f"first_{len(sub)}_jobs": {"continuous_mixed": summary(cont), "serial_fp64": summary(ser)}}
+           "served_mixed": full_s, "clocks": clk.summary(), f"first_{args.serial_jobs}_jobs": sub}
     print(json.dumps(out))
 
 
