@@ -106,8 +106,9 @@ typedef struct {
  * below 1). The workspace holds what one time step of Sec. 2.3 steps (1)-(6)
  * needs besides the state: the stage state W(1), phi(1) of the Runge-Kutta
  * scheme (Sec. 4.3), the reinitialisation scratch (Eq. reinit), one byte of
- * material flags per cell and the interface work lists of the FIVER flux
- * (Sec. 4.2); about 84 bytes per cell. */
+ * material flags per cell, the interface work lists of the FIVER flux
+ * (Sec. 4.2) and the star pressure of each face's last exact Riemann solve (the
+ * start of the next one); about 96 bytes per cell. */
 size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
 
 /* Creates a context on the calling thread's current CUDA device for a
@@ -210,8 +211,12 @@ m2c_status m2c_set_tiling(m2c_ctx* ctx, int tile_rows, int tile_z);
  * Eq. NSEquation_terms) and phi (N doubles, the level set of Sec. 3.5.1 whose
  * sign gives the material) as the state, and sets time t and step counter
  * step; the first time step (Sec. 4.3) is reduced at the next m2c_step. The
- * arrays stay the caller's and are updated in place by m2c_step. M2C_EINVAL if
- * an array is NULL or an EOS has not been set. */
+ * arrays stay the caller's and are updated in place by m2c_step. The FIVER
+ * solves start each face's Newton iteration from that face's star pressure of
+ * its previous solve; a new state clears those starts, so a run restarted from
+ * its (W, phi, t, step) agrees with the uninterrupted run to rounding (the same
+ * roots within the iteration's tolerance), not bit for bit. M2C_EINVAL if an
+ * array is NULL or an EOS has not been set. */
 m2c_status m2c_set_state(m2c_ctx* ctx, double* W, double* phi, double t, long step);
 
 /* Fills the borrowed W from device primitive arrays prims (5N: rho, u, v, w, p)

@@ -7,6 +7,15 @@
 
 namespace m2c {
 
+// Loads and stores of the state arrays as global-memory accesses: the pointers
+// come from the grid descriptor, so the compiler cannot tell their address space
+// and would otherwise use generic accesses. The loads go through the read-only
+// path: within a launch no thread reads an address another thread writes (a
+// stage reads one state and writes another; the last stage updates a cell in
+// place after its own thread has read it).
+__device__ __forceinline__ double gld(const double* p) { return __ldg(p); }
+__device__ __forceinline__ void gst(double* p, double v) { __stwb(p, v); }
+
 // ---------------------------------------------------------------------------
 // Conservative -> primitive
 // ---------------------------------------------------------------------------

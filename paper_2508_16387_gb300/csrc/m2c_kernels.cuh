@@ -90,6 +90,9 @@ struct Grid {
   double band_beta, band_gamma;  // narrow-band level set: tube radii (lengths); gamma = 0: full domain
   double* W2;         // TVD RK3: the second stage state (workspace)
   double* phi2;
+  // FIVER warm start: star pressure of each cell's x+, y+, z+ face from the face's
+  // last exact Riemann solve (3 per cell, FP32; NaN: none); nullptr: no warm start
+  float* pstar;
 };
 
 // Kernel modes: one Runge-Kutta stage each (the general bulk kernel only runs

@@ -226,6 +226,8 @@ __host__ __device__ __forceinline__ float d2f(double x) {
     const unsigned r = r0 + ((rem > 0x10000000u || (rem == 0x10000000u && (r0 & 1u))) ? 1u : 0u);
     return float_of(r | (hi & 0x80000000u));
   }
+  // zeros are common (momenta and residuals of a fluid at rest): kept on the inline path
+  if ((ah | lo) == 0u) return float_of(hi);
   return d2f_rare(x);
 }
 
@@ -256,6 +258,7 @@ __host__ __device__ __forceinline__ double f2d(float x) {
   const unsigned f = bits_of(x), a = f & 0x7fffffffu;
   if (a - 0x00800000u < 0x7f800000u - 0x00800000u)  // normal: rebias 127 -> 1023
     return double_of_words(((a >> 3) + (896u << 20)) | (f & 0x80000000u), a << 29);
+  if (a == 0u) return double_of_words(f, 0u);  // signed zero, inline
   return f2d_rare(x);
 }
 
@@ -891,9 +894,13 @@ struct RiemannOut {
 };
 
 // Solves the 1D problem between (rho, u, p) states; returns a status and the
-// Newton/bisection iteration count.
+// Newton/bisection iteration count. p_start: a start of the Newton iteration
+// (the FIVER kernel passes the same face's star pressure of its previous
+// solve); NaN, or a value not above the lowest admissible pressure, takes the
+// PVRS estimate. The root and the stopping rule do not depend on the start.
 static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, double ul, double pl, const EosDev& qR, double rr,
-                                    double ur, double pr, RiemannOut& out, int& iters) {
+                                    double ur, double pr, RiemannOut& out, int& iters,
+                                    double p_start = NAN) {
   Side L, Rs;
   iters = 0;
   if (!make_side(qL, rl, ul, pl, L) || !make_side(qR, rr, ur, pr, Rs)) return M2C_ENONPHYS;
@@ -911,6 +918,7 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
     if (F >= 0.0) return M2C_EVACUUM;
   }
   double p = 0.5 * (L.p + Rs.p) - 0.125 * (Rs.u - L.u) * (L.rho + Rs.rho) * (L.c + Rs.c);
+  if (p_start > plow && p_start < INFINITY) p = p_start;
   if (!(p > plow)) {
     double gap = fmin(L.p, Rs.p) - plow;
     if (!(gap > 0.0)) gap = fmax(L.p, Rs.p) - plow;
@@ -1133,7 +1141,8 @@ __device__ inline bool riemann_F_f(const EosP<float>& qL, const SideF& L, const 
 // FP32 Newton on p* from the PVRS guess; false if it fails, signals a vacuum
 // or does not reach |dp| <= 1e-5 |p| in 30 steps.
 static __device__ __noinline__ bool riemann_newton_f(const EosP<float>& qL, float rl, float ul, float pl, const EosP<float>& qR,
-                                        float rr, float ur, float pr, float& p_out, int& iters) {
+                                        float rr, float ur, float pr, float& p_out, int& iters,
+                                        float p_start) {
   // FP32 wave curves exist for the stiffened gas and Mie-Grueneisen only
   if ((qL.type != M2C_EOS_SG && qL.type != M2C_EOS_MG) || (qR.type != M2C_EOS_SG && qR.type != M2C_EOS_MG))
     return false;
@@ -1145,6 +1154,7 @@ static __device__ __noinline__ bool riemann_newton_f(const EosP<float>& qL, floa
     if (!riemann_F_f(qL, L, qR, Rs, plow, F, dF) || F >= 0.0f) return false;
   }
   float p = 0.5f * (L.p + Rs.p) - 0.125f * (Rs.u - L.u) * (L.rho + Rs.rho) * (L.c + Rs.c);
+  if (p_start > plow && p_start < INFINITY) p = p_start;
   if (!(p > plow)) {
     float gap = fminf(L.p, Rs.p) - plow;
     if (!(gap > 0.0f)) gap = fmaxf(L.p, Rs.p) - plow;
@@ -1167,11 +1177,12 @@ static __device__ __noinline__ bool riemann_newton_f(const EosP<float>& qL, floa
 
 static __device__ __noinline__ int riemann_solve_mixed(const EosP<float>& qLf, const EosDev& qL, double rl, double ul, double pl,
                                           const EosP<float>& qRf, const EosDev& qR, double rr, double ur, double pr,
-                                          RiemannOut& out, int& iters) {
+                                          RiemannOut& out, int& iters,
+                                          double p_start = NAN) {
   float p32;
   int it32 = 0;
   Side L, Rs;
-  if (riemann_newton_f(qLf, d2f(rl), d2f(ul), d2f(pl), qRf, d2f(rr), d2f(ur), d2f(pr), p32, it32) &&
+  if (riemann_newton_f(qLf, d2f(rl), d2f(ul), d2f(pl), qRf, d2f(rr), d2f(ur), d2f(pr), p32, it32, (float)p_start) &&
       make_side(qL, rl, ul, pl, L) && make_side(qR, rr, ur, pr, Rs)) {
     const double plow = fmax(eos_plow(qL), eos_plow(qR));
     fix_substeps(qL, L, qR, Rs, plow);
@@ -1197,7 +1208,7 @@ static __device__ __noinline__ int riemann_solve_mixed(const EosP<float>& qLf, c
       p += dp;
     }
   }
-  return riemann_solve(qL, rl, ul, pl, qR, rr, ur, pr, out, iters);
+  return riemann_solve(qL, rl, ul, pl, qR, rr, ur, pr, out, iters, p_start);
 }
 
 }  // namespace m2c

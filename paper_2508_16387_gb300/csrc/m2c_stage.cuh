@@ -210,14 +210,16 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   // material at the start of the step and the stage state of cell index c
   // (neg: the velocity components to negate, general kernel only)
   auto load = [&](long long c, R P[5], R& ph, int& idv, int neg) {
-    const double phd = phis[c];
+    const double phd = gld(phis + c);
     if (ids_frozen) {
-      idv = idg[c] & 1;
+      idv = __ldg(idg + c) & 1;
     } else {
       idv = lt0(phd) ? 1 : 0;
     }
     ph = to_r<R>(phd);
-    if (!cons_to_prim<R, GEN>(s_eos[idv], s_eosd[idv], Ws, N, c, P)) bad = true;
+    if (!cons_to_prim_v<R, GEN>(s_eos[idv], s_eosd[idv], gld(Ws + c), gld(Ws + N + c), gld(Ws + 2 * N + c),
+                                gld(Ws + 3 * N + c), gld(Ws + 4 * N + c), P))
+      bad = true;
     if constexpr (GEN) {
       if (neg & 1) P[1] = -P[1];
       if (neg & 2) P[2] = -P[2];
@@ -378,7 +380,7 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
           const R a = to_r<R>((G.geom == M2C_GEOM_SPHERICAL ? 2.0 : 1.0) / r) * P0[1];
           R wv[5];
 #pragma unroll
-          for (int v = 0; v < 5; ++v) wv[v] = to_r<R>(Ws[v * N + c]);
+          for (int v = 0; v < 5; ++v) wv[v] = to_r<R>(gld(Ws + v * N + c));
 #pragma unroll
           for (int v = 0; v < 4; ++v) res[v] = res[v] - a * wv[v];
           res[4] = res[4] - a * (wv[4] + P0[4]);
@@ -394,27 +396,29 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
           G.resL[c] = to_d<R>(Lphi);
           G.id[c] = (uint8_t)id0;
         } else if (mode == kStage1) {
-          G.phi1[c] = G.phi[c] + dt * to_d<R>(Lphi);
+          gst(G.phi1 + c, gld(G.phi + c) + dt * to_d<R>(Lphi));
           G.id[c] = (uint8_t)id0;
           if (!is_if) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) G.W1[v * N + c] = G.W[v * N + c] + dt * to_d<R>(res[v]);
+            for (int v = 0; v < 5; ++v) gst(G.W1 + v * N + c, gld(G.W + v * N + c) + dt * to_d<R>(res[v]));
           }
         } else if (GEN && mode == kStage2of3) {
           // TVD RK3, second stage (Sec. 4.3): W2 = (3/4 W + 1/4 W1) + 1/4 dt R(W1)
-          G.phi2[c] = (0.75 * G.phi[c] + 0.25 * G.phi1[c]) + 0.25 * dt * to_d<R>(Lphi);
+          gst(G.phi2 + c, (0.75 * gld(G.phi + c) + 0.25 * gld(G.phi1 + c)) + 0.25 * dt * to_d<R>(Lphi));
           if (!is_if) {
 #pragma unroll
             for (int v = 0; v < 5; ++v)
-              G.W2[v * N + c] = (0.75 * G.W[v * N + c] + 0.25 * G.W1[v * N + c]) + 0.25 * dt * to_d<R>(res[v]);
+              gst(G.W2 + v * N + c,
+                  (0.75 * gld(G.W + v * N + c) + 0.25 * gld(G.W1 + v * N + c)) + 0.25 * dt * to_d<R>(res[v]));
           }
         } else {
           // last stage: TVD RK2 W' = (W + (W1 + dt R(W1)))/2, or TVD RK3
           // W' = (1/3 W + 2/3 W2) + 2/3 dt R(W2)
           const bool rk3 = GEN && mode == kStage3;
-          const double pn = rk3 ? (G.phi[c] / 3.0 + 2.0 / 3.0 * G.phi2[c]) + 2.0 / 3.0 * dt * to_d<R>(Lphi)
-                                : 0.5 * (G.phi[c] + (G.phi1[c] + dt * to_d<R>(Lphi)));
-          G.phi[c] = pn;
+          const double pn = rk3 ? (gld(G.phi + c) / 3.0 + 2.0 / 3.0 * gld(G.phi2 + c)) +
+                                      2.0 / 3.0 * dt * to_d<R>(Lphi)
+                                : 0.5 * (gld(G.phi + c) + (gld(G.phi1 + c) + dt * to_d<R>(Lphi)));
+          gst(G.phi + c, pn);
           const bool neg = lt0(pn);
           flip = neg != (id0 == 1);
           // bit 2: material at the end of the step (read by the phase update)
@@ -423,9 +427,10 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
             double wn[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              wn[v] = rk3 ? (G.W[v * N + c] / 3.0 + 2.0 / 3.0 * G.W2[v * N + c]) + 2.0 / 3.0 * dt * to_d<R>(res[v])
-                          : 0.5 * (G.W[v * N + c] + (G.W1[v * N + c] + dt * to_d<R>(res[v])));
-              G.W[v * N + c] = wn[v];
+              wn[v] = rk3 ? (gld(G.W + v * N + c) / 3.0 + 2.0 / 3.0 * gld(G.W2 + v * N + c)) +
+                                2.0 / 3.0 * dt * to_d<R>(res[v])
+                          : 0.5 * (gld(G.W + v * N + c) + (gld(G.W1 + v * N + c) + dt * to_d<R>(res[v])));
+              gst(G.W + v * N + c, wn[v]);
             }
             if (!flip) {
               bool ok;
