@@ -272,6 +272,7 @@ typedef struct {
   double rho, u, p, c, e;
   int nrk; /* RK4 substeps of this side's rarefaction curve fixed for one Riemann
             * problem (Reading R6); 0: chosen per evaluation from |p - p_K| */
+  double dnode; /* MG: spacing of the fixed RK4 nodes p_K - i dnode of the problem (> 0), 0: none */
 } side_t;
 
 /* Wave curve of one side: velocity change f_K(p) across the K-wave that takes
@@ -361,9 +362,28 @@ static int rk4_substeps(const or_eos_t* q, double dp) {
   return (int)n;
 }
 
+/* One classical RK4 substep of the isentrope (rho, f) from pressure pi by hs. */
+static int mg_rk4_substep(const or_eos_t* q, double pi, double hs, double* rho, double* fv) {
+  double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
+  int st = mg_isentrope_rhs(q, pi, *rho, &k1r, &k1f);
+  if (!st) st = mg_isentrope_rhs(q, pi + 0.5 * hs, *rho + 0.5 * hs * k1r, &k2r, &k2f);
+  if (!st) st = mg_isentrope_rhs(q, pi + 0.5 * hs, *rho + 0.5 * hs * k2r, &k3r, &k3f);
+  if (!st) st = mg_isentrope_rhs(q, pi + hs, *rho + hs * k3r, &k4r, &k4f);
+  if (st) return st;
+  *rho = *rho + hs / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
+  *fv = *fv + hs / 6.0 * (k1f + 2.0 * k2f + 2.0 * k3f + k4f);
+  return OR_OK;
+}
+
 /* MG wave curve. Shock: f = sqrt((p - p_K)(1/rho_K - 1/rho_H(p))). Rarefaction:
  * f = integral from p_K to p of dp/(rho c) along the isentrope, integrated
- * together with rho by classical RK4 on equal substeps in p (Reading R6). */
+ * together with rho by classical RK4 in p (Reading R6): inside a Riemann
+ * problem, on the fixed nodes p_K - i dnode of the problem (dnode = the span
+ * bound over the substep count), full substeps down to the last node above p
+ * and a partial one to p, so that the curve is continuous and smooth in p (its
+ * slope jumps at a node only by the RK4 truncation error) and evaluations at
+ * nearby pressures share their nodes; beyond the span bound, and for a wave
+ * evaluated alone, equal substeps over p_K - p. */
 static int wave_mg(const or_eos_t* q, const side_t* K, double p, double* f, double* df, double* rs) {
   if (p == K->p) {
     *f = 0.0;
@@ -382,19 +402,29 @@ static int wave_mg(const or_eos_t* q, const side_t* K, double p, double* f, doub
     *rs = rho;
     return OR_OK;
   }
-  int ns = K->nrk > 0 ? K->nrk : rk4_substeps(q, p - K->p);
-  double hs = (p - K->p) / ns;
   double rho = K->rho, fv = 0.0;
-  for (int i = 0; i < ns; ++i) {
-    double pi = K->p + i * hs;
-    double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
-    int st = mg_isentrope_rhs(q, pi, rho, &k1r, &k1f);
-    if (!st) st = mg_isentrope_rhs(q, pi + 0.5 * hs, rho + 0.5 * hs * k1r, &k2r, &k2f);
-    if (!st) st = mg_isentrope_rhs(q, pi + 0.5 * hs, rho + 0.5 * hs * k2r, &k3r, &k3f);
-    if (!st) st = mg_isentrope_rhs(q, pi + hs, rho + hs * k3r, &k4r, &k4f);
-    if (st) return st;
-    rho = rho + hs / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
-    fv = fv + hs / 6.0 * (k1f + 2.0 * k2f + 2.0 * k3f + k4f);
+  double dp = K->p - p;
+  if (K->dnode > 0.0 && dp < K->nrk * K->dnode) {
+    /* inside the problem's span bound: m full substeps on the fixed nodes p_K - i dnode,
+     * then one partial substep from the last node to p (Reading R6) */
+    int m = (int)floor(dp / K->dnode);
+    if (m > K->nrk - 1) m = K->nrk - 1;
+    for (int i = 0; i < m; ++i) {
+      int st = mg_rk4_substep(q, K->p - i * K->dnode, -K->dnode, &rho, &fv);
+      if (st) return st;
+    }
+    double hp = dp - m * K->dnode;
+    if (hp > 0.0) {
+      int st = mg_rk4_substep(q, K->p - m * K->dnode, -hp, &rho, &fv);
+      if (st) return st;
+    }
+  } else {
+    int ns = K->nrk > 0 ? K->nrk : rk4_substeps(q, p - K->p);
+    double hs = (p - K->p) / ns;
+    for (int i = 0; i < ns; ++i) {
+      int st = mg_rk4_substep(q, K->p + i * hs, hs, &rho, &fv);
+      if (st) return st;
+    }
   }
   double c2;
   int st = eos_c2(q, rho, p, &c2);
@@ -562,6 +592,7 @@ static int make_side(const or_eos_t* q, const double w[3], side_t* K) {
   K->u = w[1];
   K->p = w[2];
   K->nrk = 0;
+  K->dnode = 0.0;
   double c2;
   int st = eos_c2(q, K->rho, K->p, &c2);
   if (st) return st;
@@ -578,16 +609,19 @@ static int make_side(const or_eos_t* q, const double w[3], side_t* K) {
  * too, each rarefaction curve lies below its acoustic tangent,
  * |f_K(p)| >= |p - p_K|/Z_K (rho c falls along an isentrope as p falls), and
  * F(p*) = 0 then gives p* >= p_ac. MG: the count of rk4_substeps for the span
- * p_K - p_lo. JWL: 256 per unit of ln(p_K/p_lo) and at least 8, with p_lo
+ * p_K - p_lo, and the node spacing span / count of the fixed RK4 nodes. JWL: 256 per unit of ln(p_K/p_lo) and at least 8, with p_lo
  * kept at or above 1e-6 p_K. Other EOS: closed forms, no substeps. */
-static int rarefaction_substeps(const or_eos_t* q, const side_t* K, double p_lo) {
-  if (q->type == EOS_MG) return rk4_substeps(q, fmax(K->p - p_lo, 0.0));
-  if (q->type == EOS_JWL) {
+static void set_rarefaction_steps(const or_eos_t* q, side_t* K, double p_lo) {
+  if (q->type == EOS_MG) {
+    double span = fmax(K->p - p_lo, 0.0);
+    K->nrk = rk4_substeps(q, span);
+    K->dnode = 0.0;
+    if (span > 0.0 && isfinite(span)) K->dnode = span / K->nrk;
+  } else if (q->type == EOS_JWL) {
     double lo = fmax(p_lo, 1e-6 * K->p);
     double nd = ceil(256.0 * log(K->p / lo));
-    return nd < 8.0 ? 8 : (int)nd;
+    K->nrk = nd < 8.0 ? 8 : (int)nd;
   }
-  return 0;
 }
 
 /* F(p) = f_L(p) + f_R(p) + (u_R - u_L), increasing in p. */
@@ -617,8 +651,8 @@ static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, c
   double plow = fmax(eos_plow(qL), eos_plow(qR));
   double ZL = L.rho * L.c, ZR = R.rho * R.c;
   double pac = (ZR * L.p + ZL * R.p - ZL * ZR * (R.u - L.u)) / (ZL + ZR);
-  L.nrk = rarefaction_substeps(qL, &L, fmax(plow, fmin(R.p, pac)));
-  R.nrk = rarefaction_substeps(qR, &R, fmax(plow, fmin(L.p, pac)));
+  set_rarefaction_steps(qL, &L, fmax(plow, fmin(R.p, pac)));
+  set_rarefaction_steps(qR, &R, fmax(plow, fmin(L.p, pac)));
   double F, dF;
   /* Reading R36: no vacuum test with a JWL side (its rarefaction needs p > 0) */
   if (isfinite(plow) && R.u - L.u >= 0.0 && qL->type != EOS_JWL && qR->type != EOS_JWL) {

@@ -542,6 +542,11 @@ constexpr int kRk4Steps = 64;
 struct Side {
   double rho, u, p, c, e;
   int nrk;  // RK4 substeps of this side's MG rarefaction curve in one problem; 0: per evaluation
+  // MG: spacing of the problem's fixed RK4 nodes p_K - i dnode (0: none), and the
+  // isentrope state (rho, f) after the first mbase full substeps, kept between the
+  // evaluations of one problem (nearby pressures share their nodes)
+  int mbase;
+  double dnode, dspan, rbase, fbase;  // dspan = nrk dnode, the span bound the nodes cover
 };
 
 __device__ inline bool make_side(const EosDev& q, double rho, double u, double p, Side& K) {
@@ -554,6 +559,11 @@ __device__ inline bool make_side(const EosDev& q, double rho, double u, double p
   K.c = sqrt(c2);
   K.e = e;
   K.nrk = 0;
+  K.mbase = 0;
+  K.dnode = 0.0;
+  K.dspan = 0.0;
+  K.rbase = rho;
+  K.fbase = 0.0;
   return true;
 }
 
@@ -596,8 +606,15 @@ __device__ inline void fix_substeps(const EosDev& qL, Side& L, const EosDev& qR,
                                __dmul_rn(__dmul_rn(ZL, ZR), __dsub_rn(Rs.u, L.u)));
   const double pac = __ddiv_rn(num, __dadd_rn(ZL, ZR));
   const double loL = fmax(plow, fmin(Rs.p, pac)), loR = fmax(plow, fmin(L.p, pac));
-  if (qL.type == M2C_EOS_MG) L.nrk = mg_substeps(qL, fmax(__dsub_rn(L.p, loL), 0.0));
-  if (qR.type == M2C_EOS_MG) Rs.nrk = mg_substeps(qR, fmax(__dsub_rn(Rs.p, loR), 0.0));
+  // MG: the count for the span bound and the spacing of the fixed nodes (span / count)
+  auto mg_nodes = [](const EosDev& q, Side& K, double lo) {
+    const double span = fmax(__dsub_rn(K.p, lo), 0.0);
+    K.nrk = mg_substeps(q, span);
+    K.dnode = (span > 0.0 && isfinite(span)) ? __ddiv_rn(span, (double)K.nrk) : 0.0;
+    K.dspan = __dmul_rn((double)K.nrk, K.dnode);
+  };
+  if (qL.type == M2C_EOS_MG) mg_nodes(qL, L, loL);
+  if (qR.type == M2C_EOS_MG) mg_nodes(qR, Rs, loR);
   if (qL.type == M2C_EOS_JWL) L.nrk = jwl_substeps(L.p, loL);
   if (qR.type == M2C_EOS_JWL) Rs.nrk = jwl_substeps(Rs.p, loR);
 }
@@ -681,7 +698,28 @@ __device__ inline int mg_rhs(const EosDev& q, double p, double rho, double& drho
   return M2C_OK;
 }
 
-__device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
+// One classical RK4 substep of the MG isentrope (rho, f) from pressure pi by hs.
+__device__ inline int mg_rk4_substep(const EosDev& q, double pi, double hs, double& rho, double& fv) {
+  double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
+  int st = mg_rhs(q, pi, rho, k1r, k1f);
+  if (!st) st = mg_rhs(q, pi + 0.5 * hs, rho + 0.5 * hs * k1r, k2r, k2f);
+  if (!st) st = mg_rhs(q, pi + 0.5 * hs, rho + 0.5 * hs * k2r, k3r, k3f);
+  if (!st) st = mg_rhs(q, pi + hs, rho + hs * k3r, k4r, k4f);
+  if (st) return st;
+  rho = rho + hs / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
+  fv = fv + hs / 6.0 * (k1f + 2.0 * k2f + 2.0 * k3f + k4f);
+  return M2C_OK;
+}
+
+// MG wave curve. Rarefaction: the isentrope integrated by classical RK4 in p;
+// inside a problem's span bound on the fixed nodes p_K - i dnode (full substeps
+// down to the last node above p, resumed from the node reached by an earlier
+// evaluation of the problem when it lies at or below, then one partial substep
+// to p): the curve is continuous and smooth in p; beyond the bound, and for a
+// wave evaluated alone, equal substeps over p_K - p. The node arithmetic is
+// written without contracted multiply-adds, so that it takes the same nodes as
+// the oracle.
+__device__ inline int wave_mg(const EosDev& q, Side& K, double p, double& f, double& df, double& rs,
                               double* drs = nullptr) {
   if (p == K.p) {
     f = 0.0;
@@ -702,20 +740,40 @@ __device__ inline int wave_mg(const EosDev& q, const Side& K, double p, double& 
     if (drs) *drs = drdp;
     return M2C_OK;
   }
-  // equal substeps: fixed for the problem (fix_substeps), else chosen for this span
-  const int ns = K.nrk > 0 ? K.nrk : mg_substeps(q, p - K.p);
-  const double hs = (p - K.p) / ns;
   double rho = K.rho, fv = 0.0;
-  for (int i = 0; i < ns; ++i) {
-    double pi = K.p + i * hs;
-    double k1r, k1f, k2r, k2f, k3r, k3f, k4r, k4f;
-    int st = mg_rhs(q, pi, rho, k1r, k1f);
-    if (!st) st = mg_rhs(q, pi + 0.5 * hs, rho + 0.5 * hs * k1r, k2r, k2f);
-    if (!st) st = mg_rhs(q, pi + 0.5 * hs, rho + 0.5 * hs * k2r, k3r, k3f);
-    if (!st) st = mg_rhs(q, pi + hs, rho + hs * k3r, k4r, k4f);
-    if (st) return st;
-    rho = rho + hs / 6.0 * (k1r + 2.0 * k2r + 2.0 * k3r + k4r);
-    fv = fv + hs / 6.0 * (k1f + 2.0 * k2f + 2.0 * k3f + k4f);
+  const double dp = __dsub_rn(K.p, p);
+  // (one node interval: the partial substep from p_K is the single equal substep
+  // over p_K - p, the same arithmetic, so that case takes the short path)
+  if (K.nrk > 1 && K.dnode > 0.0 && dp < K.dspan) {
+    int m = (int)floor(div_nr(dp, K.dnode));  // div_nr: the IEEE quotient
+    if (m > K.nrk - 1) m = K.nrk - 1;
+    if (K.mbase > m) {  // an earlier evaluation went past this node: start over from p_K
+      K.mbase = 0;
+      K.rbase = K.rho;
+      K.fbase = 0.0;
+    }
+    rho = K.rbase;
+    fv = K.fbase;
+    for (int i = K.mbase; i < m; ++i) {
+      const int st = mg_rk4_substep(q, __dsub_rn(K.p, __dmul_rn((double)i, K.dnode)), -K.dnode, rho, fv);
+      if (st) return st;
+    }
+    K.mbase = m;
+    K.rbase = rho;
+    K.fbase = fv;
+    const double hp = __dsub_rn(dp, __dmul_rn((double)m, K.dnode));
+    if (hp > 0.0) {
+      const int st = mg_rk4_substep(q, __dsub_rn(K.p, __dmul_rn((double)m, K.dnode)), -hp, rho, fv);
+      if (st) return st;
+    }
+  } else {
+    // equal substeps: the problem's count (beyond its span bound), else chosen for this span
+    const int ns = K.nrk > 0 ? K.nrk : mg_substeps(q, p - K.p);
+    const double hs = (p - K.p) / ns;
+    for (int i = 0; i < ns; ++i) {
+      const int st = mg_rk4_substep(q, K.p + i * hs, hs, rho, fv);
+      if (st) return st;
+    }
   }
   double e, c2;
   if (!eos_e_c2<double>(q, rho, 1.0 / rho, p, e, c2)) return M2C_ENONPHYS;
@@ -862,7 +920,7 @@ static __device__ __noinline__ int wave_jwl(const EosDev& q, const Side& K, doub
   return M2C_OK;
 }
 
-__device__ inline int wave(const EosDev& q, const Side& K, double p, double& f, double& df, double& rs,
+__device__ inline int wave(const EosDev& q, Side& K, double p, double& f, double& df, double& rs,
                            bool want_rho = true, double* drs = nullptr) {
   if (q.type == M2C_EOS_SG) return wave_sg(q, K, p, f, df, rs, want_rho, drs);
   if (q.type == M2C_EOS_MG) return wave_mg(q, K, p, f, df, rs, drs);
@@ -876,7 +934,7 @@ struct WaveVals {
   double fL, dfL, rL, dL, fR, dfR, rR, dR;
 };
 
-static __device__ __noinline__ int riemann_F(const EosDev& qL, const Side& L, const EosDev& qR, const Side& Rs, double p,
+static __device__ __noinline__ int riemann_F(const EosDev& qL, Side& L, const EosDev& qR, Side& Rs, double p,
                                 double& F, double& dF, WaveVals* wv = nullptr) {
   double fL, dfL, rL, fR, dfR, rR, dL = 0.0, dR = 0.0;
   const bool want = wv != nullptr;
