@@ -289,6 +289,25 @@ __device__ __forceinline__ double rcp_nr(double b) {
   if (nr_range(b)) return rcp_nr_in_range(b);
   return 1.0 / b;
 }
+// FP64 reciprocal square root 1/sqrt(x), x > 0, for the Mie-Grueneisen
+// isentrope integrand: a binary32 seed (x's leading 23 mantissa bits, then the
+// hardware's approximate binary32 reciprocal square root, relative error below
+// 2^-21), refined by two Newton-Raphson steps y <- y + y (1 - x y^2)/2 in FP64
+// (each squares the relative error up to a factor 3/2), within an ulp or two of
+// 1/sqrt(x); x outside [2^-125, 2^125) takes 1/sqrt(x) with the IEEE operations.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!nr_range(x)) return 1.0 / sqrt(x);
+  const unsigned hi = hi_of(x);
+  const float f = float_of(((hi - 0x38000000u) << 3) | (lo_of(x) >> 29));
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f));
+  const unsigned rb = bits_of(r);
+  double y = double_of_words((rb >> 3) + (896u << 20), rb << 29);
+  y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
+  y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
+  return y;
+}
+
 // The corrected quotient is the IEEE one when it is a normal number and its
 // residual a - b q does not underflow: with |b| in the seed range that holds
 // for |a| in [2^-897, 2^898). A zero a gives the signed zero a (1/b); any other
@@ -690,11 +709,16 @@ __device__ inline int mg_hugoniot(const EosDev& q, const Side& K, double p, doub
   return M2C_OK;
 }
 
+// d rho/dp = 1/c^2 and df/dp = 1/(rho c) of the isentrope from one reciprocal
+// square root of c^2 and the reciprocal of rho (each within an ulp or two of the
+// correctly rounded value).
 __device__ inline int mg_rhs(const EosDev& q, double p, double rho, double& drho, double& dfv) {
   double e, c2;
-  if (!eos_e_c2<double>(q, rho, div_nr(1.0, rho), p, e, c2)) return M2C_ENONPHYS;
-  drho = div_nr(1.0, c2);
-  dfv = div_nr(1.0, rho * sqrt(c2));
+  const double ir = rcp_nr(rho);
+  if (!eos_e_c2<double>(q, rho, ir, p, e, c2)) return M2C_ENONPHYS;
+  const double y = rsqrt_nr(c2);
+  drho = y * y;
+  dfv = y * ir;
   return M2C_OK;
 }
 

@@ -22,6 +22,16 @@ __global__ void k_div(const double* a, const double* b, double* x, double* y, do
   }
 }
 
+// rsqrt_nr against the IEEE 1/sqrt(x) for positive x (a[i] taken positive)
+__global__ void k_rsqrt(const double* a, double* r, double* s, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double x = fabs(a[i]);
+    r[i] = m2c::rsqrt_nr(x);
+    s[i] = 1.0 / sqrt(x);
+  }
+}
+
 static double ulps(double v, double r) {
   if (v == r) return 0.0;
   if (std::isnan(v) && std::isnan(r)) return 0.0;
@@ -79,6 +89,21 @@ int main() {
     const double u = ulps(hx[i], hy[i]);
     if (!(u <= worst_rcp)) worst_rcp = u;
   }
-  printf("quotient mismatches %ld\nreciprocal worst ulp %g\n", ndiv, worst_rcp);
+  k_rsqrt<<<(n + 255) / 256, 256>>>(db, dx, dy, n);  // reuses the x, y buffers
+  const cudaError_t e2 = cudaDeviceSynchronize();
+  if (e2 != cudaSuccess) {
+    printf("kernel failed: %s\n", cudaGetErrorString(e2));
+    return 1;
+  }
+  cudaMemcpy(hx, dx, bytes, cudaMemcpyDeviceToHost);
+  cudaMemcpy(hy, dy, bytes, cudaMemcpyDeviceToHost);
+  double worst_rsqrt = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (!(std::fabs(hb[i]) > 0.0) || !std::isfinite(hb[i])) continue;
+    const double u = ulps(hx[i], hy[i]);
+    if (!(u <= worst_rsqrt)) worst_rsqrt = u;
+  }
+  printf("quotient mismatches %ld\nreciprocal worst ulp %g\nrsqrt worst ulp %g\n", ndiv, worst_rcp,
+         worst_rsqrt);
   return 0;
 }

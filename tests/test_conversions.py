@@ -28,7 +28,8 @@ def test_integer_conversions_match_ieee(tmp_path):
 @pytest.mark.gpu
 def test_fp64_reciprocal_and_quotient_match_ieee(tmp_path):
     """The bulk kernels' FP64 quotient (Newton-Raphson reciprocal from a binary32 seed, then a
-    residual correction) equals IEEE a / b on the device; the reciprocal alone is within an ulp."""
+    residual correction) equals IEEE a / b on the device; the reciprocal alone is within an ulp,
+    and the reciprocal square root within two ulps of 1/sqrt(x)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
@@ -42,3 +43,6 @@ def test_fp64_reciprocal_and_quotient_match_ieee(tmp_path):
     assert "quotient mismatches 0" in r.stdout, r.stdout
     worst = float(r.stdout.split("reciprocal worst ulp")[1].split()[0])
     assert worst <= 1.0, r.stdout
+    # the reciprocal square root of the MG isentrope integrand: within two ulps of 1/sqrt(x)
+    worst_rsqrt = float(r.stdout.split("rsqrt worst ulp")[1].split()[0])
+    assert worst_rsqrt <= 2.0, r.stdout
