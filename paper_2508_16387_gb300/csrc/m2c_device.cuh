@@ -23,8 +23,34 @@ __device__ __forceinline__ void gst(double* p, double v) { __stwb(p, v); }
 // FP64 path: u = (rho u)/rho, e = (rho E - rho|V|^2/2)/rho, p = p(rho, e).
 // Mixed path: the same with FP32 velocities and kinetic energy; rho e and, for
 // the stiffened gas and NASG, the pressure (a difference of large numbers when
-// p_c is large) in FP64, then rounded to FP32. EXT: NASG and JWL materials too.
-template <typename R, bool EXT = false>
+// p_c is large) in FP64, then rounded to FP32. EXT: NASG and JWL materials too;
+// T: the material's type when fixed at compile time (-1: read from q).
+//
+// cons_to_prim_f is the mixed path after the loads: rho, rho u, rho v, rho w
+// already rounded to binary32 (rf, f1, f2, f3), rho and rho E in binary64.
+template <bool EXT = false, int T = -1>
+__device__ __forceinline__ bool cons_to_prim_f(const EosP<float>& q, const EosDev& qd, double rho, float rf, float f1,
+                                               float f2, float f3, double E, float P[5]) {
+  const float inv = rrcp<float>(rf);
+  const float u = f1 * inv, v = f2 * inv, w = f3 * inv;
+  const float ke = 0.5f * ((f1 * u + f2 * v) + f3 * w);
+  const double rhoe = E - f2d(ke);
+  float p = 0.0f;
+  bool ok = true;
+  if (eos_is<T>(q, M2C_EOS_SG)) {
+    p = d2f(qd.gm1 * rhoe - qd.gpc);
+  } else if (EXT && eos_is<T>(q, M2C_EOS_NASG)) {
+    const double d = 1.0 - rho * qd.b;
+    ok = d > 0.0;
+    p = d2f(div_nr(qd.gm1 * (rhoe - rho * qd.ec), d) - qd.gpc);
+  } else {
+    ok = eos_p<float, EXT, T>(q, rf, inv, d2f(rhoe) * inv, p);
+  }
+  P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
+  return ok && gt0(rho);
+}
+
+template <typename R, bool EXT = false, int T = -1>
 __device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& qd, double rho, double m1, double m2,
                                                double m3, double E, R P[5]) {
   if constexpr (sizeof(R) == 8) {
@@ -33,29 +59,14 @@ __device__ __forceinline__ bool cons_to_prim_v(const EosP<R>& q, const EosDev& q
     const double ke = 0.5 * ((m1 * u + m2 * v) + m3 * w);
     const double e = (E - ke) * inv;
     double p = 0.0;
-    const bool ok = eos_p<double, EXT>(q, rho, inv, e, p);
+    const bool ok = eos_p<double, EXT, T>(q, rho, inv, e, p);
     P[0] = rho; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
     return ok && rho > 0.0;
   } else {
-    const float rf = d2f(rho);
-    const float inv = rrcp<float>(rf);
-    const float f1 = d2f(m1), f2 = d2f(m2), f3 = d2f(m3);
-    const float u = f1 * inv, v = f2 * inv, w = f3 * inv;
-    const float ke = 0.5f * ((f1 * u + f2 * v) + f3 * w);
-    const double rhoe = E - f2d(ke);
-    float p = 0.0f;
-    bool ok = true;
-    if (q.type == M2C_EOS_SG) {
-      p = d2f(qd.gm1 * rhoe - qd.gpc);
-    } else if (EXT && q.type == M2C_EOS_NASG) {
-      const double d = 1.0 - rho * qd.b;
-      ok = d > 0.0;
-      p = d2f(div_nr(qd.gm1 * (rhoe - rho * qd.ec), d) - qd.gpc);
-    } else {
-      ok = eos_p<float, EXT>(q, rf, inv, d2f(rhoe) * inv, p);
-    }
-    P[0] = rf; P[1] = u; P[2] = v; P[3] = w; P[4] = p;
-    return ok && gt0(rho);
+    const double x[4] = {rho, m1, m2, m3};
+    float y[4];
+    d2f_group<4>(x, y);
+    return cons_to_prim_f<EXT, T>(q, qd, rho, y[0], y[1], y[2], y[3], E, P);
   }
 }
 
@@ -65,10 +76,10 @@ __device__ __forceinline__ bool cons_to_prim(const EosP<R>& q, const EosDev& qd,
   return cons_to_prim_v<R, EXT>(q, qd, W[c], W[N + c], W[2 * N + c], W[3 * N + c], W[4 * N + c], P);
 }
 
-template <typename R, bool EXT = false>
+template <typename R, bool EXT = false, int T = -1>
 __device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w, R p, FaceState<R>& F) {
   R e = (R)0, c2 = (R)0;
-  const bool ok = eos_e_c2<R, EXT>(q, rho, rrcp<R>(rho), p, e, c2);
+  const bool ok = eos_e_c2<R, EXT, T>(q, rho, rrcp<R>(rho), p, e, c2);
   F.rho = rho; F.u = u; F.v = v; F.w = w; F.p = p;
   F.c = ok ? rsqrt_pos<R>(c2) : (R)0;
   F.E = e + (R)0.5 * ((u * u + v * v) + w * w);
@@ -82,7 +93,7 @@ __device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w
 // not admissible.
 // The general kernels (GEN) take the limiter of the grid: lim = M2C_LIM_MC with
 // alpha, else van Albada.
-template <typename R, bool GEN = false>
+template <typename R, bool GEN = false, int T = -1>
 __device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], const R P[5], const R Pp[5], bool same,
                                            FaceState<R>& Qm, FaceState<R>& Qp, bool& bad, int lim = 0,
                                            R alpha = (R)0) {
@@ -96,25 +107,25 @@ __device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], cons
       for (int v = 0; v < 5; ++v) s[v] = va_slope<R>(P[v] - Pm[v], Pp[v] - P[v]);
     }
     const R hf = (R)0.5;
-    const bool okm = make_face<R, GEN>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2],
-                                       P[3] - hf * s[3], P[4] - hf * s[4], Qm);
-    const bool okp = make_face<R, GEN>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2],
-                                       P[3] + hf * s[3], P[4] + hf * s[4], Qp);
+    const bool okm = make_face<R, GEN, T>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2],
+                                          P[3] - hf * s[3], P[4] - hf * s[4], Qm);
+    const bool okp = make_face<R, GEN, T>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2],
+                                          P[3] + hf * s[3], P[4] + hf * s[4], Qp);
     if (okm && okp) return;
   }
-  if (!make_face<R, GEN>(q, P[0], P[1], P[2], P[3], P[4], Qm)) bad = true;
+  if (!make_face<R, GEN, T>(q, P[0], P[1], P[2], P[3], P[4], Qm)) bad = true;
   Qp = Qm;
 }
 
 // Wave-speed sum of a state, sum over the axes with more than one cell of
 // |V_d| + c (the CFL reading of the design notes), in precision R (the mixed
 // path takes the time step from FP32 wave speeds of the FP64 state).
-template <typename R, bool EXT = false>
+template <typename R, bool EXT = false, int T = -1>
 __device__ __forceinline__ R wave_sum_v(const Grid& g, const EosP<R>& q, const EosDev& qd, const double w[5], bool& ok) {
   R P[5];
-  ok = cons_to_prim_v<R, EXT>(q, qd, w[0], w[1], w[2], w[3], w[4], P);
+  ok = cons_to_prim_v<R, EXT, T>(q, qd, w[0], w[1], w[2], w[3], w[4], P);
   R e, c2;
-  ok = ok && eos_e_c2<R, EXT>(q, P[0], rrcp<R>(P[0]), P[4], e, c2);
+  ok = ok && eos_e_c2<R, EXT, T>(q, P[0], rrcp<R>(P[0]), P[4], e, c2);
   const R cs = ok ? rsqrt_pos<R>(c2) : (R)0;
   R lam = (R)0;
   if (g.active[0]) lam = lam + (fabs(P[1]) + cs);

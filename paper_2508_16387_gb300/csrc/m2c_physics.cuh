@@ -262,6 +262,31 @@ __host__ __device__ __forceinline__ double f2d(float x) {
   return f2d_rare(x);
 }
 
+// A group of d2f conversions taken on the common path (normal binary32 range
+// and zeros) with one branch, to the exact d2f of every member, when a member
+// falls outside it: the same results as d2f, and the group stays one basic
+// block in the common case.
+__host__ __device__ __forceinline__ float d2f_common(double x, bool& rare) {
+  const unsigned hi = hi_of(x), lo = lo_of(x), ah = hi & 0x7fffffffu;
+  const unsigned r0 = ((ah - 0x38000000u) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  const unsigned r = r0 + ((rem > 0x10000000u || (rem == 0x10000000u && (r0 & 1u))) ? 1u : 0u);
+  const bool zero = (ah | lo) == 0u;
+  rare = rare || !(ah - 0x38100000u < 0x47f00000u - 0x38100000u || zero);
+  return float_of((zero ? 0u : r) | (hi & 0x80000000u));
+}
+
+template <int K>
+__host__ __device__ __forceinline__ void d2f_group(const double (&x)[K], float (&y)[K]) {
+  bool rare = false;
+#pragma unroll
+  for (int i = 0; i < K; ++i) y[i] = d2f_common(x[i], rare);
+  if (rare) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) y[i] = d2f(x[i]);
+  }
+}
+
 // FP64 reciprocal and quotient for the bulk kernels: a binary32 seed of 1/b
 // (b's leading 23 mantissa bits, then the hardware's approximate binary32
 // reciprocal; relative error below 2^-21 together), refined by two
@@ -371,10 +396,18 @@ __device__ __forceinline__ void jwl_f(const EosP<R>& q, R rho, R inv_rho, R& f, 
   df = q.A1 * e1 * (-q.c1 + a1 * x1 * inv_rho) + q.A2 * e2 * (-q.c2 + a2 * x2 * inv_rho);
 }
 
+// Material type test: T >= 0 is a type fixed at compile time (the bulk kernel's
+// instantiations for one pair of SG / MG materials), T = -1 reads it from q.
+template <int T, typename R>
+__device__ __forceinline__ bool eos_is(const EosP<R>& q, int type) {
+  if constexpr (T >= 0) return T == type;
+  else return q.type == type;
+}
+
 // p(rho, e) given 1/rho; false if the state is outside the EOS domain.
-template <typename R, bool EXT = false>
+template <typename R, bool EXT = false, int T = -1>
 __device__ __forceinline__ bool eos_p(const EosP<R>& q, R rho, R inv_rho, R e, R& p) {
-  if (q.type == M2C_EOS_SG) {
+  if (eos_is<T>(q, M2C_EOS_SG)) {
     p = q.gm1 * rho * e - q.gpc;
     return true;
   }
@@ -402,10 +435,10 @@ __device__ __forceinline__ bool eos_p(const EosP<R>& q, R rho, R inv_rho, R e, R
 
 // e(rho, p) and c^2(rho, p) together (App. B.3 and App. C.2: c^2 = dp/drho|_e + p/rho^2 dp/de|_rho).
 // False if rho <= 0, c^2 <= 0 or the state is outside the EOS domain.
-template <typename R, bool EXT = false>
+template <typename R, bool EXT = false, int T = -1>
 __device__ __forceinline__ bool eos_e_c2(const EosP<R>& q, R rho, R inv_rho, R p, R& e, R& c2) {
   if (!(rho > (R)0)) return false;
-  if (q.type == M2C_EOS_SG) {
+  if (eos_is<T>(q, M2C_EOS_SG)) {
     R pb = p + q.pc;
     e = (p + q.gpc) * q.inv_gm1 * inv_rho;
     c2 = q.g * pb * inv_rho;

@@ -659,6 +659,14 @@ const char* grid_args_error(int nx, int ny, int nz, double h, const int* bc) {
   return nullptr;
 }
 
+// EOS type pair of a grid for the bulk kernel's fixed-type instantiations:
+// T0 + 4 T1 when both materials are SG or MG, else -1 (types read at run time).
+int material_pair(const Grid& g) {
+  const int a = g.eos[0].type, b = g.eos[1].type;
+  const bool fixed = (a == M2C_EOS_SG || a == M2C_EOS_MG) && (b == M2C_EOS_SG || b == M2C_EOS_MG);
+  return fixed ? a + 4 * b : -1;
+}
+
 bool has_symmetry_side(const int* bc) {
   for (int s = 0; s < 6; ++s)
     if (bc[s] == M2C_BC_SYMMETRY) return true;
@@ -1160,6 +1168,7 @@ m2c_status m2c_step(m2c_ctx* c, int nsteps) {
     StageEvents pe{&c->ev, &c->ev_kind, &c->ev_used, c->profile_bulk_only, false};
     LaunchPlan lp;
     lp.ty = c->ty;
+    lp.mats = material_pair(c->host);
     cudaError_t e = enqueue_step(c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), c->host.prec, lp, re,
                                  c->reinit_iters, c->host.N, c->stream, c->profiling ? &pe : nullptr, c->host.rk,
                                  c->host.general != 0, c->host.band_gamma > 0.0);
@@ -1219,6 +1228,9 @@ m2c_status m2c_batch_create(m2c_batch** out, m2c_ctx** v, int k, void* workspace
   b->lp.sched = sched;
   b->lp.blocks_per_sm = bpsm;
   b->lp.counter = b->counter;
+  b->lp.mats = material_pair(b->hosts[0]);
+  for (int i = 1; i < k; ++i)
+    if (material_pair(b->hosts[i]) != b->lp.mats) b->lp.mats = -1;
   b->prec = v[0]->host.prec;
   b->rk = v[0]->host.rk;
   b->gen = gen;
@@ -1321,6 +1333,7 @@ m2c_status m2c_residual(m2c_ctx* c, double* R, double* L) {
   if (st) return st;
   LaunchPlan lp;
   lp.ty = c->ty;
+  lp.mats = material_pair(c->host);
   cudaError_t e = launch_stage(c->host.prec, c->dev_grid, c->dev_tiles, 1, ntiles_of(c->host), kResidual, lp,
                                c->stream, c->host.general != 0);
   if (e == cudaSuccess) {
@@ -1605,6 +1618,7 @@ m2c_status m2c_residual_noalloc(int nx, int ny, int nz, double h, const int bc[6
   if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tiles, sizeof(tiles), cudaMemcpyHostToDevice, s);
   LaunchPlan lp;
   lp.ty = ty;
+  lp.mats = material_pair(g);
   if (e == cudaSuccess) e = launch_stage(precision, dg, dt, 1, tiles[1], kResidual, lp, s);
   if (e == cudaSuccess) {
     const dim3 lg((unsigned)(2 * sm_count()), 1);

@@ -30,10 +30,32 @@ struct StageSmem {
   static constexpr size_t fx_off = ys_off + sizeof(FaceState<R>) * (TY + 2) * TX * 2;
   static constexpr size_t fy_off = fx_off + sizeof(R) * 5 * TY * (TX + 1);
   static constexpr size_t id_off = fy_off + sizeof(R) * 5 * (TY + 1) * TX;
-  static constexpr size_t eos_off = (id_off + NB * HY * HX + 15) / 16 * 16;
-  static constexpr size_t eosd_off = eos_off + (sizeof(EosP<R>) * 2 + 15) / 16 * 16;
-  static constexpr size_t bytes = eosd_off + sizeof(EosDev) * 2;
+  static constexpr size_t bytes = (id_off + NB * HY * HX + 15) / 16 * 16;
 };
+
+// Compile-time integer for the material dispatch below (usable in device code).
+template <int V>
+struct IntC {
+  static constexpr int value = V;
+  __device__ constexpr operator int() const { return V; }
+};
+
+// Calls f(T, m) for material m of a cell: T its EOS type as a compile-time
+// constant when the instantiation fixes the pair of material types (MT = T0 +
+// 4 T1, each M2C_EOS_SG or M2C_EOS_MG), else IntC<-1> (the type is read at run
+// time); m the material index, itself a compile-time constant where the two
+// fixed types differ (f is then inlined once per material).
+template <int MT, typename F>
+__device__ __forceinline__ void by_material(int m, F&& f) {
+  if constexpr (MT < 0) {
+    f(IntC<-1>{}, m);
+  } else if constexpr ((MT & 3) == (MT >> 2)) {
+    f(IntC<(MT & 3)>{}, m);
+  } else {
+    if (m == 0) f(IntC<(MT & 3)>{}, IntC<0>{});
+    else f(IntC<(MT >> 2)>{}, IntC<1>{});
+  }
+}
 
 // FP64 tiles run one block per SM (FP64-pipe bound); the FP32 tiles of the
 // mixed path are latency bound and are compiled for 1024 resident threads per
@@ -49,7 +71,10 @@ struct StageSmem {
 // GEN = false is the default scheme (TVD RK2, modified van Albada, HLLC); GEN =
 // true is the general instantiation, which takes the grid's scheme options at
 // run time (limiter, flux, the stages of TVD RK3) at some cost in registers.
-template <typename R, int TY, bool GEN>
+// MT >= 0 fixes the EOS types of the two materials (SG or MG, MT = T0 + 4 T1)
+// for launches whose grids all have that pair, which removes the type dispatch
+// from every EOS evaluation; MT = -1 reads the types at run time.
+template <typename R, int TY, bool GEN, int MT = -1>
 __global__ void __launch_bounds__(32 * TY, (sizeof(R) == 8 ? 1 : 1024 / (32 * TY)))
 k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin, int ngrid, long long ntiles, int mode,
         int sched, unsigned long long* __restrict__ tile_counter) {
@@ -67,8 +92,14 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   R* s_fx = reinterpret_cast<R*>(smem + SM::fx_off);                       // [5][TY][TX+1]
   R* s_fy = reinterpret_cast<R*>(smem + SM::fy_off);                       // [5][TY+1][TX]
   uint8_t* const s_id0 = smem + SM::id_off;                                // [NB][HY][HX]
-  EosP<R>* s_eos = reinterpret_cast<EosP<R>*>(smem + SM::eos_off);
-  EosDev* s_eosd = reinterpret_cast<EosDev*>(smem + SM::eosd_off);
+  // the descriptor of the tile's grid, copied to shared memory for each tile
+  // (its fields and EOS parameters are read all through the plane loop)
+  __shared__ __align__(16) Grid s_G;
+  static_assert(sizeof(Grid) % 8 == 0, "grid descriptor copy");
+  const EosP<R>* s_eos;
+  if constexpr (sizeof(R) == 8) s_eos = s_G.eos;
+  else s_eos = s_G.eosf;
+  const EosDev* s_eosd = s_G.eos;
   __shared__ double s_dt;
   __shared__ double s_red[32];
   __shared__ long long s_tile;
@@ -147,7 +178,13 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   }
   if (tile >= ntiles) break;
   const int gidx = find_grid(tile_begin, ngrid, tile);
-  const Grid& G = grids[gidx];
+  {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(grids + gidx);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_G);
+    for (int i = tid; i < (int)(sizeof(Grid) / 8); i += NT) dst[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  const Grid& G = s_G;
   const int nx = G.nx, ny = G.ny, nz = G.nz;
   const long long N = G.N, nxy = (long long)nx * ny;
   const int bcz0 = G.bc[4], bcz1 = G.bc[5];
@@ -171,14 +208,10 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
   const R alpha = GEN ? (R)G.mc_alpha : (R)0;
   const long long step = ctrl->step;
 
-  if (tid < 2) {
-    if constexpr (sizeof(R) == 8) s_eos[tid] = G.eos[tid];
-    else s_eos[tid] = G.eosf[tid];
-    s_eosd[tid] = G.eos[tid];
-  }
   if (tid == 0) s_dt = mode == kResidual ? 0.0 : lam_to_dt(G, ctrl->lam[step & 1]);
   __syncthreads();
   const double dt = s_dt;
+  const R hdt = to_r<R>(0.5 * dt);
 
   const int gx = x0 + tx, gy = y0 + ty;
   const bool inside = gx < nx && gy < ny;
@@ -216,10 +249,24 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     } else {
       idv = lt0(phd) ? 1 : 0;
     }
-    ph = to_r<R>(phd);
-    if (!cons_to_prim_v<R, GEN>(s_eos[idv], s_eosd[idv], gld(Ws + c), gld(Ws + N + c), gld(Ws + 2 * N + c),
-                                gld(Ws + 3 * N + c), gld(Ws + 4 * N + c), P))
-      bad = true;
+    const double w0 = gld(Ws + c), w1 = gld(Ws + N + c), w2 = gld(Ws + 2 * N + c), w3 = gld(Ws + 3 * N + c),
+                 w4 = gld(Ws + 4 * N + c);
+    if constexpr (sizeof(R) == 8) {
+      ph = phd;
+      by_material<MT>(idv, [&](auto T, auto m) {
+        if (!cons_to_prim_v<R, GEN, decltype(T)::value>(s_eos[m], s_eosd[m], w0, w1, w2, w3, w4, P)) bad = true;
+      });
+    } else {
+      // the level set and the state's first four components: one group of conversions
+      const double x[5] = {phd, w0, w1, w2, w3};
+      float y[5];
+      d2f_group<5>(x, y);
+      ph = y[0];
+      by_material<MT>(idv, [&](auto T, auto m) {
+        if (!cons_to_prim_f<GEN, decltype(T)::value>(s_eos[m], s_eosd[m], w0, y[1], y[2], y[3], y[4], w4, P))
+          bad = true;
+      });
+    }
     if constexpr (GEN) {
       if (neg & 1) P[1] = -P[1];
       if (neg & 2) P[2] = -P[2];
@@ -242,8 +289,14 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     load(plane(k0) + own_base, P0, ph[2], id0, own_neg);
     load(plane(k0 + 1) + own_base, P1, ph[3], id1, own_neg | zneg(k0 + 1));
     FaceState<R> QaP, Q0M;
-    cell_faces<R, GEN>(s_eos[ida], Pb, Pa, P0, idb == ida && id0 == ida, Qtmp, QaP, bad, lim, alpha);
-    cell_faces<R, GEN>(s_eos[id0], Pa, P0, P1, ida == id0 && id1 == id0, Q0M, QzP, bad, lim, alpha);
+    by_material<MT>(ida, [&](auto T, auto m) {
+      cell_faces<R, GEN, decltype(T)::value>(s_eos[m], Pb, Pa, P0, idb == ida && id0 == ida, Qtmp, QaP, bad, lim,
+                                              alpha);
+    });
+    by_material<MT>(id0, [&](auto T, auto m) {
+      cell_faces<R, GEN, decltype(T)::value>(s_eos[m], Pa, P0, P1, ida == id0 && id1 == id0, Q0M, QzP, bad, lim,
+                                              alpha);
+    });
     if (ida == id0) {
       num_flux<2, R, GEN>(QaP, Q0M, Fzm, flx);
     } else {
@@ -263,7 +316,10 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
     uint8_t* const s_id = s_id0 + buf * PL;
     // ---- own column: plane k+2, z face states of cell k+1, z flux of face k+1/2
     load(plane(k + 2) + own_base, P2, ph[4], id2, own_neg | zneg(k + 2));
-    cell_faces<R, GEN>(s_eos[id1], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad, lim, alpha);
+    by_material<MT>(id1, [&](auto T, auto m) {
+      cell_faces<R, GEN, decltype(T)::value>(s_eos[m], P0, P1, P2, id0 == id1 && id2 == id1, QzM1, QzP1, bad, lim,
+                                              alpha);
+    });
     if (id0 == id1) {
       num_flux<2, R, GEN>(QzP, QzM1, Fzp, flx);
     } else {
@@ -306,7 +362,9 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
       const bool same = s_id[c0 - so] == ic && s_id[c0 + so] == ic;
       bool b = false;
       FaceState<R>* out = s_st + 2 * (tid + s * NT);
-      cell_faces<R, GEN>(s_eos[ic], Pm, P, Pp, same, out[0], out[1], b, lim, alpha);
+      by_material<MT>(ic, [&](auto T, auto m) {
+        cell_faces<R, GEN, decltype(T)::value>(s_eos[m], Pm, P, Pp, same, out[0], out[1], b, lim, alpha);
+      });
       bad = bad || b;
     }
     __syncthreads();
@@ -413,11 +471,15 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
           }
         } else {
           // last stage: TVD RK2 W' = (W + (W1 + dt R(W1)))/2, or TVD RK3
-          // W' = (1/3 W + 2/3 W2) + 2/3 dt R(W2)
+          // W' = (1/3 W + 2/3 W2) + 2/3 dt R(W2). The mixed path's TVD RK2 takes
+          // W' = (W + W1)/2 + (dt/2) R with the increment (dt/2) R in binary32 (R
+          // itself is a binary32 result) and one rounding after the FP64 sum.
           const bool rk3 = GEN && mode == kStage3;
-          const double pn = rk3 ? (gld(G.phi + c) / 3.0 + 2.0 / 3.0 * gld(G.phi2 + c)) +
+          constexpr bool f32inc = sizeof(R) == 4 && !GEN;
+          const double pn = rk3      ? (gld(G.phi + c) / 3.0 + 2.0 / 3.0 * gld(G.phi2 + c)) +
                                       2.0 / 3.0 * dt * to_d<R>(Lphi)
-                                : 0.5 * (gld(G.phi + c) + (gld(G.phi1 + c) + dt * to_d<R>(Lphi)));
+                            : f32inc ? fma(0.5, gld(G.phi + c) + gld(G.phi1 + c), to_d<R>(hdt * Lphi))
+                                     : 0.5 * (gld(G.phi + c) + (gld(G.phi1 + c) + dt * to_d<R>(Lphi)));
           gst(G.phi + c, pn);
           const bool neg = lt0(pn);
           flip = neg != (id0 == 1);
@@ -427,14 +489,18 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
             double wn[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              wn[v] = rk3 ? (gld(G.W + v * N + c) / 3.0 + 2.0 / 3.0 * gld(G.W2 + v * N + c)) +
+              wn[v] = rk3      ? (gld(G.W + v * N + c) / 3.0 + 2.0 / 3.0 * gld(G.W2 + v * N + c)) +
                                 2.0 / 3.0 * dt * to_d<R>(res[v])
-                          : 0.5 * (gld(G.W + v * N + c) + (gld(G.W1 + v * N + c) + dt * to_d<R>(res[v])));
+                      : f32inc ? fma(0.5, gld(G.W + v * N + c) + gld(G.W1 + v * N + c), to_d<R>(hdt * res[v]))
+                               : 0.5 * (gld(G.W + v * N + c) + (gld(G.W1 + v * N + c) + dt * to_d<R>(res[v])));
               gst(G.W + v * N + c, wn[v]);
             }
             if (!flip) {
               bool ok;
-              const R lam = wave_sum_v<R, GEN>(G, s_eos[id0], s_eosd[id0], wn, ok);
+              R lam = (R)0;
+              by_material<MT>(id0, [&](auto T, auto m) {
+                lam = wave_sum_v<R, GEN, decltype(T)::value>(G, s_eos[m], s_eosd[m], wn, ok);
+              });
               bad = bad || !ok;
               lam_max = fmax(lam_max, lam);
             }
@@ -540,20 +606,20 @@ k_stage(const Grid* __restrict__ grids, const long long* __restrict__ tile_begin
 
 // The shared-memory opt-in is a per-device attribute of the kernel: it is set
 // once on every device the calling threads make current.
-template <typename R, int TY, bool GEN>
+template <typename R, int TY, bool GEN, int MT = -1>
 void stage_smem_setup() {
   static bool done[kMaxDevices] = {};
   const int dev = current_device();
   if (done[dev]) return;
-  cudaFuncSetAttribute(k_stage<R, TY, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_stage<R, TY, GEN, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)StageSmem<R, TY>::bytes);
   done[dev] = true;
 }
 
-template <typename R, int TY, bool GEN>
+template <typename R, int TY, bool GEN, int MT = -1>
 cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
                            const LaunchPlan& lp, cudaStream_t s) {
-  stage_smem_setup<R, TY, GEN>();
+  stage_smem_setup<R, TY, GEN, MT>();
   long long nb = ntiles;
   if (lp.blocks_per_sm > 0) nb = std::min<long long>(ntiles, (long long)lp.blocks_per_sm * sm_count());
   if (nb < 1) nb = 1;
@@ -561,9 +627,37 @@ cudaError_t launch_stage_t(const Grid* grids, const long long* tiles, int ngrid,
     cudaError_t e = cudaMemsetAsync(lp.counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
   }
-  k_stage<R, TY, GEN><<<(unsigned)nb, 32 * TY, StageSmem<R, TY>::bytes, s>>>(grids, tiles, ngrid, ntiles, mode,
+  k_stage<R, TY, GEN, MT><<<(unsigned)nb, 32 * TY, StageSmem<R, TY>::bytes, s>>>(grids, tiles, ngrid, ntiles, mode,
                                                                               lp.sched, lp.counter);
   return cudaGetLastError();
+}
+
+// The launch for the material pair of the plan: instantiations with fixed EOS
+// types for the four SG / MG pairs, else the run-time types.
+template <typename R, int TY>
+cudaError_t launch_stage_pair(const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
+                              const LaunchPlan& lp, cudaStream_t s) {
+  switch (lp.mats) {
+    case M2C_EOS_SG + 4 * M2C_EOS_SG:
+      return launch_stage_t<R, TY, false, M2C_EOS_SG + 4 * M2C_EOS_SG>(grids, tiles, ngrid, ntiles, mode, lp, s);
+    case M2C_EOS_MG + 4 * M2C_EOS_SG:
+      return launch_stage_t<R, TY, false, M2C_EOS_MG + 4 * M2C_EOS_SG>(grids, tiles, ngrid, ntiles, mode, lp, s);
+    case M2C_EOS_SG + 4 * M2C_EOS_MG:
+      return launch_stage_t<R, TY, false, M2C_EOS_SG + 4 * M2C_EOS_MG>(grids, tiles, ngrid, ntiles, mode, lp, s);
+    case M2C_EOS_MG + 4 * M2C_EOS_MG:
+      return launch_stage_t<R, TY, false, M2C_EOS_MG + 4 * M2C_EOS_MG>(grids, tiles, ngrid, ntiles, mode, lp, s);
+    default:
+      return launch_stage_t<R, TY, false>(grids, tiles, ngrid, ntiles, mode, lp, s);
+  }
+}
+
+template <typename R, int TY>
+void stage_smem_setup_pairs() {
+  stage_smem_setup<R, TY, false, M2C_EOS_SG + 4 * M2C_EOS_SG>();
+  stage_smem_setup<R, TY, false, M2C_EOS_MG + 4 * M2C_EOS_SG>();
+  stage_smem_setup<R, TY, false, M2C_EOS_SG + 4 * M2C_EOS_MG>();
+  stage_smem_setup<R, TY, false, M2C_EOS_MG + 4 * M2C_EOS_MG>();
+  stage_smem_setup<R, TY, false>();
 }
 
 }  // namespace m2c

@@ -12,6 +12,7 @@ struct LaunchPlan {
   int sched = 0;         // 0: fixed stride over tiles, 1: atomic tile counter
   int blocks_per_sm = 0; // persistent grid of blocks_per_sm x SMs blocks; 0: one block per tile
   unsigned long long* counter = nullptr;
+  int mats = -1;         // EOS types of the two materials of every grid, T0 + 4 T1 (SG / MG); -1: mixed or other
 };
 
 // Host-side state kept per device (index of the current device, clamped to

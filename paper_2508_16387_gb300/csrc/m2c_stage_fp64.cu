@@ -5,13 +5,13 @@ namespace m2c {
 
 cudaError_t launch_stage_fp64(const Grid* grids, const long long* tiles, int ngrid, long long ntiles, int mode,
                               const LaunchPlan& lp, cudaStream_t s) {
-  if (lp.ty == 4) return launch_stage_t<double, 4, false>(grids, tiles, ngrid, ntiles, mode, lp, s);
-  return launch_stage_t<double, 8, false>(grids, tiles, ngrid, ntiles, mode, lp, s);
+  if (lp.ty == 4) return launch_stage_pair<double, 4>(grids, tiles, ngrid, ntiles, mode, lp, s);
+  return launch_stage_pair<double, 8>(grids, tiles, ngrid, ntiles, mode, lp, s);
 }
 
 void setup_stage_fp64() {
-  stage_smem_setup<double, 4, false>();
-  stage_smem_setup<double, 8, false>();
+  stage_smem_setup_pairs<double, 4>();
+  stage_smem_setup_pairs<double, 8>();
 }
 
 }  // namespace m2c

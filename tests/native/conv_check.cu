@@ -3,9 +3,9 @@
 // nearest, ties to even). f2d is checked on every binary32 value; d2f on every
 // binary32 value, the binary64 neighbours of each, the midpoints between
 // adjacent binary32 values and their neighbours (the rounding ties), and
-// random bit patterns; the bit-level sign tests lt0/gt0 against x < 0 and
-// x > 0 on the same values. Prints the number of mismatches and exits
-// non-zero on any.
+// random bit patterns (also as members of a group of conversions, d2f_group);
+// the bit-level sign tests lt0/gt0 against x < 0 and x > 0 on the same
+// values. Prints the number of mismatches and exits non-zero on any.
 #include <atomic>
 #include <cstdio>
 #include <cstdint>
@@ -14,6 +14,7 @@
 #include "m2c_physics.cuh"
 
 using m2c::d2f;
+using m2c::d2f_group;
 using m2c::f2d;
 using m2c::bits_of;
 using m2c::double_of;
@@ -35,6 +36,18 @@ static long long check_d2f(unsigned long long b) {
   if (std::isnan(want) ? !std::isnan(got) : bits_of(want) != bits_of(got)) {
     if (printed++ < 10) std::printf("d2f %016llx: got %08x want %08x\n", b, bits_of(got), bits_of(want));
     ++n;
+  }
+  // the same value in a group of conversions, beside a common-path member and beside a
+  // member that takes the group to its exact path
+  const double g1[2] = {1.5, x}, g2[2] = {x, 1e-300};
+  float h1[2], h2[2];
+  d2f_group<2>(g1, h1);
+  d2f_group<2>(g2, h2);
+  for (float h : {h1[1], h2[0]}) {
+    if (std::isnan(want) ? !std::isnan(h) : bits_of(want) != bits_of(h)) {
+      if (printed++ < 10) std::printf("d2f_group %016llx: got %08x want %08x\n", b, bits_of(h), bits_of(want));
+      ++n;
+    }
   }
   return n;
 }
