@@ -91,6 +91,8 @@ __host__ inline EosDev make_eos_dev(int type, const double* prm) { return make_e
 // FP32 rounding already accepted there.
 __device__ __forceinline__ double rcp_nr(double b);
 __device__ __forceinline__ double div_nr(double a, double b);
+__device__ __forceinline__ bool nr_range(double b);
+__device__ __forceinline__ double rcp_nr_in_range(double b);
 template <typename R>
 __device__ __forceinline__ R rdiv(R a, R b) {
   if constexpr (sizeof(R) == 8) return div_nr(a, b);
@@ -359,12 +361,20 @@ __device__ __forceinline__ double to_d(R x) {
   else return f2d(x);
 }
 
+// x > 0; FP64 values are tested on their bits (false for NaN either way), which
+// keeps the comparison off the narrow FP64 pipe.
+template <typename R>
+__device__ __forceinline__ bool pos(R x) {
+  if constexpr (sizeof(R) == 8) return gt0(x);
+  else return x > (R)0;
+}
+
 // Reference curves p_R, p_R', e_R, e_R' at strain eta (App. B.3); "p_H" in the
 // compression e_R is read as p_R.
 template <typename R>
 __device__ __forceinline__ void mg_ref(const EosP<R>& q, R eta, R& pR, R& dpR, R& eR, R& deR) {
   const R K0 = q.K0, rho0 = q.rho0, e0 = q.e0, h2 = q.inv_2rho0;
-  if (eta > (R)0) {
+  if (pos(eta)) {
     R d = (R)1 - q.s * eta;
     R id = rrcp<R>(d);
     R id2 = id * id;
@@ -437,7 +447,7 @@ __device__ __forceinline__ bool eos_p(const EosP<R>& q, R rho, R inv_rho, R e, R
 // False if rho <= 0, c^2 <= 0 or the state is outside the EOS domain.
 template <typename R, bool EXT = false, int T = -1>
 __device__ __forceinline__ bool eos_e_c2(const EosP<R>& q, R rho, R inv_rho, R p, R& e, R& c2) {
-  if (!(rho > (R)0)) return false;
+  if (!pos(rho)) return false;
   if (eos_is<T>(q, M2C_EOS_SG)) {
     R pb = p + q.pc;
     e = (p + q.gpc) * q.inv_gm1 * inv_rho;
@@ -463,7 +473,8 @@ __device__ __forceinline__ bool eos_e_c2(const EosP<R>& q, R rho, R inv_rho, R p
     R ir2 = inv_rho * inv_rho;
     c2 = ((dpR - q.rg * deR) * q.rho0 + p * q.rg) * ir2;
   }
-  return c2 > (R)0 && c2 < (R)INFINITY;
+  if constexpr (sizeof(R) == 8) return gt0(c2) && hi_of(c2) < 0x7ff00000u;
+  else return c2 > (R)0 && c2 < (R)INFINITY;
 }
 
 // ---------------------------------------------------------------------------
@@ -473,8 +484,17 @@ __device__ __forceinline__ bool eos_e_c2(const EosP<R>& q, R rho, R inv_rho, R p
 template <typename R>
 __device__ __forceinline__ R va_slope(R a, R b) {
   R ab = a * b;
-  if (!(ab > (R)0)) return (R)0;
-  return rdiv<R>(ab * (a + b), a * a + b * b);
+  if constexpr (sizeof(R) == 8) {
+    // FP64: the sign test on the bits and the quotient as the product with the
+    // Newton-Raphson reciprocal (within an ulp or two of the IEEE quotient, which
+    // is taken where the denominator is outside the reciprocal's range)
+    if (!gt0(ab)) return 0.0;
+    const double num = ab * (a + b), den = a * a + b * b;
+    return nr_range(den) ? num * rcp_nr_in_range(den) : num / den;
+  } else {
+    if (!(ab > (R)0)) return (R)0;
+    return rdiv<R>(ab * (a + b), a * a + b * b);
+  }
 }
 
 // Monotonized central slope (App. D, Eq. theta) on the uniform grid, written
