@@ -56,7 +56,7 @@ def fake_device(monkeypatch):
 
 
 def _server(free, **kw):
-    srv = S.Server(free_bytes_fn=lambda: free[0], reserve_bytes=0, **kw)
+    srv = S.Server(free_bytes_fn=lambda: free[0], reserve_bytes=0, warm=False, **kw)
     srv.torch = types.SimpleNamespace(cuda=types.SimpleNamespace(synchronize=lambda: None))
     return srv
 
@@ -84,7 +84,7 @@ def test_admission_in_arrival_order_while_memory_allows(fake_device):
     def free():
         live = [g for g in fake_device.values() if g.steps < g.job.params.steps]
         return 2 * 1000 - sum(g.N for g in live)
-    srv = S.Server(free_bytes_fn=free, reserve_bytes=0, slice_steps=100)
+    srv = S.Server(free_bytes_fn=free, reserve_bytes=0, slice_steps=100, warm=False)
     srv.torch = types.SimpleNamespace(cuda=types.SimpleNamespace(synchronize=lambda: None))
     st = srv.run(jobs, realtime=False)
     batches = [ids for ids, _ in FakeBatch.log]
