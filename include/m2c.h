@@ -108,7 +108,7 @@ typedef struct {
  * scheme (Sec. 4.3), the reinitialisation scratch (Eq. reinit), one byte of
  * material flags per cell, the interface work lists of the FIVER flux
  * (Sec. 4.2) and the star pressure of each face's last exact Riemann solve (the
- * start of the next one); about 96 bytes per cell. */
+ * start of the next one, FP64); about 120 bytes per cell. */
 size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
 
 /* Creates a context on the calling thread's current CUDA device for a

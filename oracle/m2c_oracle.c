@@ -637,7 +637,8 @@ static int riemann_F(const or_eos_t* qL, const side_t* L, const or_eos_t* qR, co
 
 /* Exact solution of the 1D two-material Riemann problem: the star pressure p*
  * solves F(p*) = 0 (Newton from the PVRS guess, kept above the lowest
- * admissible pressure; stop when |dp| <= 1e-12 |p|, then one more step; after
+ * admissible pressure; stop at the first step with |dp| <= 1e-12 |p|, whose
+ * update leaves an error of the order of that step squared (Reading R6); after
  * 50 steps, bisection). u* = (u_L + u_R)/2 + (f_R - f_L)/2; rho*_K from the
  * K-wave. Reading R7: no vacuum solution is built; if F(p_low) >= 0 the call
  * fails with OR_EVACUUM. Both wave curves increase with p and vanish at their
@@ -666,7 +667,7 @@ static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, c
     if (!(gap > 0.0)) gap = fmax(L.p, R.p) - plow;
     p = plow + 1e-3 * gap;
   }
-  int it = 0, conv = 0, extra = 0;
+  int it = 0, conv = 0;
   for (it = 1; it <= NEWTON_CAP; ++it) {
     st = riemann_F(qL, &L, qR, &R, p, &F, &dF);
     if (st) return st;
@@ -674,8 +675,7 @@ static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, c
     if (!(pn > plow)) pn = 0.5 * (p + plow);
     int small = fabs(pn - p) <= NEWTON_TOL * fabs(pn);
     p = pn;
-    if (extra) { conv = 1; break; }
-    if (small) extra = 1;
+    if (small) { conv = 1; break; }
   }
   if (!conv) {
     /* bisection on a bracket [a, b] with F(a) < 0 < F(b) */

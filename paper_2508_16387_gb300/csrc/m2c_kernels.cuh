@@ -91,8 +91,8 @@ struct Grid {
   double* W2;         // TVD RK3: the second stage state (workspace)
   double* phi2;
   // FIVER warm start: star pressure of each cell's x+, y+, z+ face from the face's
-  // last exact Riemann solve (3 per cell, FP32; NaN: none); nullptr: no warm start
-  float* pstar;
+  // last exact Riemann solve (3 per cell; NaN: none); nullptr: no warm start
+  double* pstar;
 };
 
 // Kernel modes: one Runge-Kutta stage each (the general bulk kernel only runs

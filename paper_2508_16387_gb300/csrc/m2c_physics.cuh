@@ -599,7 +599,7 @@ __device__ __forceinline__ void num_flux(const FaceState<R>& L, const FaceState<
 // ---------------------------------------------------------------------------
 // Exact two-material Riemann problem (Sec. 4.2, Eq. 1DRiemannProblem with the
 // interface conditions of Sec. 3.5.1), FP64. Newton on p* from the PVRS guess,
-// stop when |dp| <= 1e-12 |p| and take one more step; 50 steps then bisection.
+// stop at the first step with |dp| <= 1e-12 |p|; 50 steps then bisection.
 // SG wave curves in closed form; MG shock from the Hugoniot root, MG
 // rarefaction by RK4 on equal pressure substeps whose number is fixed once
 // per problem (fix_substeps) from a bound of the wave's pressure span.
@@ -1053,29 +1053,30 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
     if (F >= 0.0) return M2C_EVACUUM;
   }
   double p = 0.5 * (L.p + Rs.p) - 0.125 * (Rs.u - L.u) * (L.rho + Rs.rho) * (L.c + Rs.c);
-  if (p_start > plow && p_start < INFINITY) p = p_start;
+  const bool warm = p_start > plow && p_start < INFINITY;
+  if (warm) p = p_start;
   if (!(p > plow)) {
     double gap = fmin(L.p, Rs.p) - plow;
     if (!(gap > 0.0)) gap = fmax(L.p, Rs.p) - plow;
     p = plow + 1e-3 * gap;
   }
   int it;
-  bool conv = false, extra = false;
-  // the extra (last) Newton step also returns the star densities, so that the
-  // solution follows from it to first order in that step's (rounding-level)
-  // change of p instead of from one more evaluation
+  bool conv = false;
+  // every evaluation also returns the star densities, so that the solution
+  // follows from the last one to first order in its step (at most the
+  // tolerance: the error is of the order of its square) instead of from one
+  // more evaluation
   WaveVals wv{};
   double p_last = 0.0;
   for (it = 1; it <= kNewtonCap; ++it) {
-    st = riemann_F(qL, L, qR, Rs, p, F, dF, extra ? &wv : nullptr);
+    st = riemann_F(qL, L, qR, Rs, p, F, dF, &wv);
     if (st) return st;
     double pn = p - F / dF;
     if (!(pn > plow)) pn = 0.5 * (p + plow);
     bool small = fabs(pn - p) <= kNewtonTol * fabs(pn);
     p_last = p;
     p = pn;
-    if (extra) { conv = true; break; }
-    if (small) extra = true;
+    if (small) { conv = true; break; }
   }
   if (!conv) {
     double a = plow, b = fmax(L.p, Rs.p);

@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
     // Newton starts from this face's star pressure of its last solve (the previous
     // stage), else from the PVRS estimate; the residual alone (kResidual) always
     // starts from PVRS
-    float* pst = (mode != kResidual && G.pstar) ? G.pstar + 3 * ca + d : nullptr;
-    const double p_start = pst ? (double)*pst : (double)NAN;
+    double* pst = (mode != kResidual && G.pstar) ? G.pstar + 3 * ca + d : nullptr;
+    const double p_start = pst ? *pst : (double)NAN;
     if (ok) {
       // material 0 is put on the left of the 1D problem (the mirror image, normal
       // velocities negated, when it is on the plus side), so that every lane of a
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
                                  P1[0], sgn * P1[1 + d], P1[4], rs, its, p_start);
       else
         st = riemann_solve(q0, P0[0], sgn * P0[1 + d], P0[4], q1, P1[0], sgn * P1[1 + d], P1[4], rs, its, p_start);
-      if (pst && st == M2C_OK) *pst = (float)rs.p;
+      if (pst && st == M2C_OK) *pst = rs.p;
       if (mirror) {
         const double r = rs.rhoL;
         rs.rhoL = rs.rhoR;
@@ -575,7 +575,7 @@ Layout layout_for(long long N, int rk = 2) {
   L.faces = o; o = align_up(o + sizeof(IfFace) * (size_t)L.face_cap);
   L.cells = o; o = align_up(o + sizeof(IfCell) * (size_t)L.cell_cap);
   L.flips = o; o = align_up(o + sizeof(long long) * (size_t)L.flip_cap);
-  L.pstar = o; o = align_up(o + sizeof(float) * 3 * N);
+  L.pstar = o; o = align_up(o + sizeof(double) * 3 * N);
   L.W2 = L.phi2 = 0;
   if (rk == 3) {
     L.W2 = o; o = align_up(o + sizeof(double) * 5 * N);
@@ -952,7 +952,7 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   g.flips = reinterpret_cast<long long*>(ws + L.flips);
   g.face_cap = L.face_cap; g.cell_cap = L.cell_cap; g.flip_cap = L.flip_cap;
   g.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
-  g.pstar = reinterpret_cast<float*>(ws + L.pstar);
+  g.pstar = reinterpret_cast<double*>(ws + L.pstar);
   g.rk = 2;
   g.limiter = M2C_LIM_VAN_ALBADA;
   g.flux = M2C_FLUX_HLLC;
@@ -1106,7 +1106,7 @@ m2c_status m2c_set_state(m2c_ctx* c, double* W, double* phi, double t, long step
   cudaError_t e = cudaMemcpyAsync(c->host.ctrl, &init, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_check(c, e, "set_state");
   // a new state starts the FIVER warm-start cache empty (all bits set: NaN)
-  e = cudaMemsetAsync(c->host.pstar, 0xff, sizeof(float) * 3 * (size_t)c->host.N, c->stream);
+  e = cudaMemsetAsync(c->host.pstar, 0xff, sizeof(double) * 3 * (size_t)c->host.N, c->stream);
   if (e != cudaSuccess) return cuda_check(c, e, "set_state");
   c->host_step = step;
   c->has_state = true;
