@@ -302,15 +302,15 @@ static int wave_sg(const or_eos_t* q, const side_t* K, double p, double* f, doub
 
 /* MG shock: density on the Hugoniot through (rho_K, p_K, e_K) at pressure p,
  * H(rho) = e(rho,p) - e_K - (p + p_K)/2 (1/rho_K - 1/rho) = 0 on (rho_K, rho0 s/(s-1)),
- * by Newton's method kept inside a shrinking bracket, stopped when the step is
- * below 1e-14 rho and followed by one more step (Reading R6). */
+ * by Newton's method kept inside a shrinking bracket, stopped at the first step
+ * below 1e-14 rho (Reading R6). */
 static int mg_hugoniot_rho(const or_eos_t* q, const side_t* K, double p, double* rho_out, double* drho_dp) {
   const double rho0 = q->prm[0], s = q->prm[2], rg = q->prm[0] * q->prm[3];
   double lo = K->rho, hi = rho0 * s / (s - 1.0);
   if (!(hi > lo)) return OR_ENONPHYS;
   double rho = K->rho + (p - K->p) / (K->c * K->c);
   if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
-  int done = 0, extra = 0;
+  int done = 0;
   for (int it = 0; it < HUGONIOT_CAP; ++it) {
     double e, dedr;
     int st = eos_e(q, rho, p, &e);
@@ -323,8 +323,7 @@ static int mg_hugoniot_rho(const or_eos_t* q, const side_t* K, double p, double*
     if (!(rn >= lo && rn <= hi)) rn = 0.5 * (lo + hi);
     int conv = fabs(rn - rho) <= HUGONIOT_TOL * rn;
     rho = rn;
-    if (extra) { done = 1; break; }
-    if (conv) extra = 1;
+    if (conv) { done = 1; break; }
   }
   if (!done) return OR_ENOCONV;
   /* d rho / dp along the Hugoniot by implicit differentiation of H */
@@ -440,7 +439,7 @@ static int wave_mg(const or_eos_t* q, const side_t* K, double p, double* f, doub
  * Newton safeguarded in a bracket [rho_K, rho_hi] (H(rho_K) > 0; rho_hi starts
  * at the strong-shock compression rho_K (omega + 2)/omega of a gas with
  * Grueneisen coefficient omega and doubles until H(rho_hi) < 0), the same
- * tolerance and extra step as the MG root; d rho/dp by implicit
+ * tolerance and stopping rule as the MG root; d rho/dp by implicit
  * differentiation. de/drho|_p = -(f'(rho) + omega e)/(omega rho). */
 static int jwl_hugoniot_rho(const or_eos_t* q, const side_t* K, double p, double* rho_out, double* drho_dp) {
   double w = q->prm[0];
@@ -456,7 +455,7 @@ static int jwl_hugoniot_rho(const or_eos_t* q, const side_t* K, double p, double
   if (!bracketed) return OR_ENOCONV;
   double rho = K->rho + (p - K->p) / (K->c * K->c);
   if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
-  int done = 0, extra = 0;
+  int done = 0;
   for (int it = 0; it < HUGONIOT_CAP; ++it) {
     double e, f, df;
     int st = eos_e(q, rho, p, &e);
@@ -470,8 +469,7 @@ static int jwl_hugoniot_rho(const or_eos_t* q, const side_t* K, double p, double
     if (!(rn >= lo && rn <= hi)) rn = 0.5 * (lo + hi);
     int conv = fabs(rn - rho) <= HUGONIOT_TOL * rn;
     rho = rn;
-    if (extra) { done = 1; break; }
-    if (conv) extra = 1;
+    if (conv) { done = 1; break; }
   }
   if (!done) return OR_ENOCONV;
   double e, f, df;

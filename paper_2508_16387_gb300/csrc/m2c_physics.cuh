@@ -728,13 +728,14 @@ __device__ inline bool mg_dedr(const EosDev& q, double rho, double& dedr) {
 }
 
 // Density on the MG Hugoniot through K at pressure p (safeguarded Newton in a
-// closed bracket, one extra step after convergence) and d rho/dp along it.
+// closed bracket, stopped at the first step below the tolerance) and d rho/dp
+// along it.
 __device__ inline int mg_hugoniot(const EosDev& q, const Side& K, double p, double& rho_out, double& drdp) {
   double lo = K.rho, hi = q.rho0 * q.s / (q.s - 1.0);
   if (!(hi > lo)) return M2C_ENONPHYS;
   double rho = K.rho + div_nr(p - K.p, K.c * K.c);
   if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
-  bool extra = false, done = false;
+  bool done = false;
   for (int it = 0; it < kHugCap; ++it) {
     double eta = 1.0 - div_nr(q.rho0, rho);
     if (!(eta < q.eta_max)) return M2C_ENONPHYS;
@@ -749,8 +750,7 @@ __device__ inline int mg_hugoniot(const EosDev& q, const Side& K, double p, doub
     if (!(rn >= lo && rn <= hi)) rn = 0.5 * (lo + hi);
     bool conv = fabs(rn - rho) <= kHugTol * rn;
     rho = rn;
-    if (extra) { done = true; break; }
-    if (conv) extra = true;
+    if (conv) { done = true; break; }
   }
   if (!done) return M2C_ENOCONV;
   double dedr;
@@ -893,7 +893,7 @@ static __device__ __noinline__ int wave_nasg(const EosDev& q, const Side& K, dou
 // JWL Hugoniot through K at p > p_K: the root rho > rho_K of
 // H(rho) = e(rho, p) - e_K - (p + p_K)(1/rho_K - 1/rho)/2, bracketed from
 // [rho_K, rho_K (w + 2)/w] (doubling the upper end until H < 0), then Newton
-// kept inside the bracket with the tolerance and extra step of the MG root;
+// kept inside the bracket with the tolerance and stopping rule of the MG root;
 // d rho/dp by implicit differentiation. de/drho|_p = -(f'(rho) + w e)/(w rho).
 __device__ inline int jwl_hugoniot(const EosDev& q, const Side& K, double p, double& rho_out, double& drdp) {
   const double w = q.om;
@@ -909,7 +909,7 @@ __device__ inline int jwl_hugoniot(const EosDev& q, const Side& K, double p, dou
   if (!bracketed) return M2C_ENOCONV;
   double rho = K.rho + (p - K.p) / (K.c * K.c);
   if (!(rho > lo && rho < hi)) rho = 0.5 * (lo + hi);
-  bool extra = false, done = false;
+  bool done = false;
   for (int it = 0; it < kHugCap; ++it) {
     double f, df;
     jwl_f<double>(q, rho, 1.0 / rho, f, df);
@@ -922,8 +922,7 @@ __device__ inline int jwl_hugoniot(const EosDev& q, const Side& K, double p, dou
     if (!(rn >= lo && rn <= hi)) rn = 0.5 * (lo + hi);
     const bool conv = fabs(rn - rho) <= kHugTol * rn;
     rho = rn;
-    if (extra) { done = true; break; }
-    if (conv) extra = true;
+    if (conv) { done = true; break; }
   }
   if (!done) return M2C_ENOCONV;
   double f, df;
