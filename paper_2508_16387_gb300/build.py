@@ -8,8 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("m2c_solver.cu", "m2c_stage_fp32.cu", "m2c_stage_fp64.cu",
                                                          "m2c_stage_gen.cu")]
-HEADERS = [os.path.join(HERE, "csrc", f) for f in ("m2c_physics.cuh", "m2c_kernels.cuh", "m2c_device.cuh",
-                                                    "m2c_stage.cuh", "m2c_stage.h")] + \
+HEADERS = [os.path.join(HERE, "csrc", f) for f in ("m2c_physics.cuh", "m2c_riemann.cuh", "m2c_kernels.cuh",
+                                                    "m2c_device.cuh", "m2c_stage.cuh", "m2c_stage.h")] + \
     [os.path.join(ROOT, "include", "m2c.h")]
 LIB = os.path.join(HERE, "libm2cgpu.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"

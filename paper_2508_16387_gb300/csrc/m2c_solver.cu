@@ -28,6 +28,7 @@
 
 #include "m2c_kernels.cuh"
 #include "m2c_device.cuh"
+#include "m2c_riemann.cuh"
 #include "m2c_stage.h"
 
 namespace m2c {
