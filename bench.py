@@ -195,7 +195,8 @@ def time_steps(torch, g, steps, warmup, barrier=None, breakdown=True):
 def e2e_run(torch, M, s, g, steps):
     """End to end through the C-ABI with host buffers: every step uploads the state from
     pinned host memory, advances one time step and downloads the new state into the same
-    host buffers (the next step starts from it)."""
+    host buffers (the next step starts from it), one m2c_step_host call per step (which
+    overlaps a call's download with the next call's upload, one state component at a time)."""
     nx, ny, nz = s.n
     Wh = torch.empty((5, nz, ny, nx), dtype=torch.float64, pin_memory=True)
     ph = torch.empty((nz, ny, nx), dtype=torch.float64, pin_memory=True)
@@ -203,9 +204,8 @@ def e2e_run(torch, M, s, g, steps):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        g.upload(Wh, ph)
-        g.step(1)
-        g.download(Wh, ph)
+        g.step_host(Wh, ph, 1)
+    g.sync()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     nbytes = (Wh.numel() + ph.numel()) * 8

@@ -235,6 +235,20 @@ m2c_status m2c_state_to_prims(m2c_ctx* ctx, double* prims);
 m2c_status m2c_upload_state(m2c_ctx* ctx, const double* W_host, const double* phi_host);
 m2c_status m2c_download_state(m2c_ctx* ctx, double* W_host, double* phi_host);
 
+/* Advances nsteps time steps (m2c_step) from the state in the host arrays
+ * W_host (5N doubles) and phi_host (N doubles), the layout of m2c_set_state, and
+ * writes the new state back into them: the upload, the steps and the download
+ * of the host-resident time-stepping loop in one call, asynchronous on the
+ * context's stream (m2c_sync waits; the host arrays must not be touched before).
+ * The copies go one state component at a time: when a call uses the same host
+ * arrays as the previous call, it uploads each component on a second stream as
+ * soon as the previous call's download of that component has finished, so the
+ * two directions of the host link overlap. Host arrays in pinned memory are
+ * required for the copies to be asynchronous. The time step is recomputed from
+ * the uploaded state (as after m2c_upload_state). Errors: M2C_EINVAL (null
+ * arguments, nsteps < 0, no state), M2C_ECUDA. */
+m2c_status m2c_step_host(m2c_ctx* ctx, double* W_host, double* phi_host, int nsteps);
+
 /* Enqueues nsteps time steps on the context's stream. One step is Sec. 2.3
  * steps (1)-(6) with the fluid and level-set updates of the TVD Runge-Kutta
  * scheme (Sec. 4.3): the time step from the CFL number, two stages of the

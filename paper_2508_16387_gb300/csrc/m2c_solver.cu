@@ -544,6 +544,12 @@ struct m2c_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pairs around launches while profiling
   std::vector<int> ev_kind;
   size_t ev_used;
+  // m2c_step_host: the upload stream, one event per state component for the end
+  // of its download and of its upload, and the host arrays of the last call
+  cudaStream_t copy_in = nullptr;
+  cudaEvent_t down_ev[6] = {}, up_ev[6] = {};
+  const double* last_W_host = nullptr;
+  const double* last_phi_host = nullptr;
   std::string err;
 };
 
@@ -672,6 +678,13 @@ bool has_symmetry_side(const int* bc) {
   for (int s = 0; s < 6; ++s)
     if (bc[s] == M2C_BC_SYMMETRY) return true;
   return false;
+}
+
+// Every entry point that enqueues work on a context, except m2c_step_host itself,
+// ends the overlap of m2c_step_host's copies with the previous call's.
+inline void end_host_loop(m2c_ctx* c) {
+  c->last_W_host = nullptr;
+  c->last_phi_host = nullptr;
 }
 
 m2c_status cuda_check(m2c_ctx* c, cudaError_t e, const char* what) {
@@ -1093,6 +1106,7 @@ m2c_status m2c_set_tiling(m2c_ctx* c, int tile_rows, int tile_z) {
 
 m2c_status m2c_set_state(m2c_ctx* c, double* W, double* phi, double t, long step) {
   if (!c) return M2C_EINVAL;
+  end_host_loop(c);
   if (!W || !phi) return set_err(c, M2C_EINVAL, "null state");
   if (!c->eos_set[0] || !c->eos_set[1]) return set_err(c, M2C_EINVAL, "set both EOS first");
   c->host.W = W;
@@ -1118,6 +1132,7 @@ m2c_status m2c_set_state(m2c_ctx* c, double* W, double* phi, double t, long step
 
 m2c_status m2c_prims_to_state(m2c_ctx* c, const double* prims) {
   if (!c || !prims) return M2C_EINVAL;
+  end_host_loop(c);
   if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first (W and phi buffers)");
   const dim3 g((unsigned)std::min<long long>((c->host.N + 255) / 256, 8ll * sm_count()), 1);
   k_prims_to_state<<<g, 256, 0, c->stream>>>(c->dev_grid, prims);
@@ -1129,6 +1144,7 @@ m2c_status m2c_prims_to_state(m2c_ctx* c, const double* prims) {
 
 m2c_status m2c_state_to_prims(m2c_ctx* c, double* prims) {
   if (!c || !prims) return M2C_EINVAL;
+  end_host_loop(c);
   if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first");
   const dim3 g((unsigned)std::min<long long>((c->host.N + 255) / 256, 8ll * sm_count()), 1);
   k_state_to_prims<<<g, 256, 0, c->stream>>>(c->dev_grid, prims);
@@ -1137,6 +1153,7 @@ m2c_status m2c_state_to_prims(m2c_ctx* c, double* prims) {
 
 m2c_status m2c_upload_state(m2c_ctx* c, const double* W_host, const double* phi_host) {
   if (!c || !W_host || !phi_host) return M2C_EINVAL;
+  end_host_loop(c);
   if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first");
   const size_t N = (size_t)c->host.N;
   cudaError_t e = cudaMemcpyAsync(c->host.W, W_host, 5 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
@@ -1148,6 +1165,7 @@ m2c_status m2c_upload_state(m2c_ctx* c, const double* W_host, const double* phi_
 
 m2c_status m2c_download_state(m2c_ctx* c, double* W_host, double* phi_host) {
   if (!c || !W_host || !phi_host) return M2C_EINVAL;
+  end_host_loop(c);
   if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first");
   const size_t N = (size_t)c->host.N;
   cudaError_t e = cudaMemcpyAsync(W_host, c->host.W, 5 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -1157,8 +1175,54 @@ m2c_status m2c_download_state(m2c_ctx* c, double* W_host, double* phi_host) {
   return cuda_check(c, e, "download_state");
 }
 
+m2c_status m2c_step_host(m2c_ctx* c, double* W_host, double* phi_host, int nsteps) {
+  if (!c || !W_host || !phi_host || nsteps < 0) return M2C_EINVAL;
+  if (!c->has_state) return set_err(c, M2C_EINVAL, "set_state first");
+  cudaError_t e = cudaSuccess;
+  if (!c->copy_in) {
+    e = cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&c->down_ev[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->up_ev[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return cuda_check(c, e, "step_host set-up");
+  }
+  const size_t N = (size_t)c->host.N;
+  const bool same = W_host == c->last_W_host && phi_host == c->last_phi_host;
+  auto host_of = [&](int k) { return k < 5 ? W_host + (size_t)k * N : phi_host; };
+  auto dev_of = [&](int k) { return k < 5 ? c->host.W + (size_t)k * N : c->host.phi; };
+  // the uploads may not overwrite the state while work enqueued before this call
+  // still uses it: after a call on the same host arrays with nothing enqueued on
+  // the context since (every other entry point that enqueues work clears
+  // last_W_host), component k waits only for that call's download of it;
+  // otherwise the copy stream waits for everything enqueued on the context's stream
+  if (!same) {
+    e = cudaEventRecord(c->up_ev[0], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_in, c->up_ev[0], 0);
+  }
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+    if (same) e = cudaStreamWaitEvent(c->copy_in, c->down_ev[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dev_of(k), host_of(k), N * sizeof(double), cudaMemcpyHostToDevice, c->copy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(c->up_ev[k], c->copy_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->up_ev[k], 0);
+  }
+  if (e != cudaSuccess) return cuda_check(c, e, "step_host upload");
+  c->lam_valid = false;
+  m2c_status st = m2c_step(c, nsteps);
+  if (st) return st;
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+    e = cudaMemcpyAsync(host_of(k), dev_of(k), N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->down_ev[k], c->stream);
+  }
+  c->last_W_host = W_host;
+  c->last_phi_host = phi_host;
+  return cuda_check(c, e, "step_host download");
+}
+
 m2c_status m2c_step(m2c_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return M2C_EINVAL;
+  end_host_loop(c);
   if (!c->has_state) return set_err(c, M2C_EINVAL, "no state");
   if (!c->lam_valid && nsteps > 0) {
     cudaError_t e = ensure_lam(c);
@@ -1279,6 +1343,7 @@ static m2c_status batch_enqueue(m2c_batch* b, int nsteps, cudaStream_t s) {
 
 m2c_status m2c_batch_step(m2c_batch* b, int nsteps) {
   if (!b || nsteps < 0) return M2C_EINVAL;
+  for (m2c_ctx* c : b->ctx) end_host_loop(c);
   return batch_enqueue(b, nsteps, b->stream);
 }
 
@@ -1312,6 +1377,7 @@ m2c_status m2c_batch_capture(m2c_batch* b, int nsteps, void** graph_exec) {
 
 m2c_status m2c_batch_launch_graph(m2c_batch* b, void* graph_exec) {
   if (!b || !graph_exec) return M2C_EINVAL;
+  for (m2c_ctx* c : b->ctx) end_host_loop(c);
   cudaError_t e = cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), b->stream);
   if (e != cudaSuccess) return cuda_check(b->ctx[0], e, "graph launch");
   b->step += b->graph_steps;
@@ -1327,6 +1393,7 @@ void m2c_batch_destroy(m2c_batch* b) { delete b; }
 
 m2c_status m2c_residual(m2c_ctx* c, double* R, double* L) {
   if (!c || !R || !L) return M2C_EINVAL;
+  end_host_loop(c);
   if (!c->has_state) return set_err(c, M2C_EINVAL, "no state");
   c->host.resR = R;
   c->host.resL = L;
@@ -1680,6 +1747,14 @@ void m2c_destroy(m2c_ctx* c) {
   for (auto& p : c->ev) {
     cudaEventDestroy(p.first);
     cudaEventDestroy(p.second);
+  }
+  if (c->copy_in) {
+    cudaStreamSynchronize(c->copy_in);
+    for (int k = 0; k < 6; ++k) {
+      if (c->down_ev[k]) cudaEventDestroy(c->down_ev[k]);
+      if (c->up_ev[k]) cudaEventDestroy(c->up_ev[k]);
+    }
+    cudaStreamDestroy(c->copy_in);
   }
   delete c;
 }

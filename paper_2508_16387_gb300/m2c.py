@@ -85,6 +85,7 @@ def lib():
         L.m2c_state_to_prims.argtypes = [p, p]
         L.m2c_upload_state.argtypes = [p, p, p]
         L.m2c_download_state.argtypes = [p, p, p]
+        L.m2c_step_host.argtypes = [p, p, p, i]
         L.m2c_step.argtypes = [p, i]
         L.m2c_residual.argtypes = [p, p, p]
         L.m2c_sync.argtypes = [p, p, p, p]
@@ -334,6 +335,11 @@ class Grid:
     # -- stepping
     def step(self, nsteps=1):
         _check(lib().m2c_step(self.ctx, nsteps), "m2c_step", self.ctx)
+
+    def step_host(self, W_host, phi_host, nsteps=1):
+        """m2c_step_host: upload the state from the (pinned) host arrays, step, download it back
+        into them; asynchronous (sync() waits)."""
+        _check(lib().m2c_step_host(self.ctx, _ptr(W_host), _ptr(phi_host), nsteps), "m2c_step_host", self.ctx)
 
     def sync(self):
         t = ctypes.c_double()
