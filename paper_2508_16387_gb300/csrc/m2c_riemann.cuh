@@ -456,13 +456,12 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
   int st;
   // vacuum test (F(p_low) >= 0); both wave curves increase with p and vanish at
   // their side's pressure, so F(p_low) <= u_R - u_L and the test is only made
-  // when u_R - u_L >= 0
-  // no vacuum test with a JWL side (its rarefaction needs p > 0)
-  if (isfinite(plow) && Rs.u - L.u >= 0.0 && qL.type != M2C_EOS_JWL && qR.type != M2C_EOS_JWL) {
-    st = riemann_F(qL, L, qR, Rs, plow, F, dF);
-    if (st) return st;
-    if (F >= 0.0) return M2C_EVACUUM;
-  }
+  // when u_R - u_L >= 0; no vacuum test with a JWL side (its rarefaction needs
+  // p > 0). F increases with p, so a root above p_low found by the Newton
+  // iteration implies F(p_low) < 0: the test is made only when the iteration
+  // does not converge (before the bisection), which spares each converged
+  // problem an evaluation of its curves down to p_low
+  const bool vacuum_test = isfinite(plow) && Rs.u - L.u >= 0.0 && qL.type != M2C_EOS_JWL && qR.type != M2C_EOS_JWL;
   double p = 0.5 * (L.p + Rs.p) - 0.125 * (Rs.u - L.u) * (L.rho + Rs.rho) * (L.c + Rs.c);
   const bool warm = p_start > plow && p_start < INFINITY;
   if (warm) p = p_start;
@@ -490,6 +489,11 @@ static __device__ __noinline__ int riemann_solve(const EosDev& qL, double rl, do
     if (small) { conv = true; break; }
   }
   if (!conv) {
+    if (vacuum_test) {
+      st = riemann_F(qL, L, qR, Rs, plow, F, dF);
+      if (st) return st;
+      if (F >= 0.0) return M2C_EVACUUM;
+    }
     double a = plow, b = fmax(L.p, Rs.p);
     if (!isfinite(a)) {
       a = fmin(L.p, Rs.p);
@@ -685,8 +689,9 @@ __device__ inline bool riemann_F_f(const EosP<float>& qL, const SideF& L, const 
   return isfinite(F);
 }
 
-// FP32 Newton on p* from the PVRS guess; false if it fails, signals a vacuum
-// or does not reach |dp| <= 1e-5 |p| in 30 steps.
+// FP32 Newton on p* from the PVRS guess; false if it fails, ends within 1e-4
+// of the lowest admissible pressure (where a vacuum would take it) or does not
+// reach |dp| <= 1e-5 |p| in 30 steps.
 static __device__ __noinline__ bool riemann_newton_f(const EosP<float>& qL, float rl, float ul, float pl, const EosP<float>& qR,
                                         float rr, float ur, float pr, float& p_out, int& iters,
                                         float p_start) {
@@ -697,9 +702,9 @@ static __device__ __noinline__ bool riemann_newton_f(const EosP<float>& qL, floa
   if (!make_side_f(qL, rl, ul, pl, L) || !make_side_f(qR, rr, ur, pr, Rs)) return false;
   const float plow = fmaxf(eos_plow_f(qL), eos_plow_f(qR));
   float F, dF;
-  if (isfinite(plow)) {
-    if (!riemann_F_f(qL, L, qR, Rs, plow, F, dF) || F >= 0.0f) return false;
-  }
+  // no vacuum test here (as in the FP64 solve, a root above p_low rules a vacuum
+  // out): with a vacuum the iterates only approach p_low, so a "root" within
+  // 1e-4 of p_low is rejected and the problem left to the FP64 solve
   float p = 0.5f * (L.p + Rs.p) - 0.125f * (Rs.u - L.u) * (L.rho + Rs.rho) * (L.c + Rs.c);
   if (p_start > plow && p_start < INFINITY) p = p_start;
   if (!(p > plow)) {
@@ -714,6 +719,7 @@ static __device__ __noinline__ bool riemann_newton_f(const EosP<float>& qL, floa
     const bool small = fabsf(pn - p) <= 1e-5f * fabsf(pn);
     p = pn;
     if (small) {
+      if (isfinite(plow) && !(p - plow > 1e-4f * fabsf(p))) return false;
       p_out = p;
       iters = it;
       return true;
