@@ -41,17 +41,41 @@ namespace m2c {
 // F_ji = Phi(W*_ji, W_ji; EOS_j) (Reading R16), FP64.
 // ---------------------------------------------------------------------------
 
-template <int D>
-__device__ __forceinline__ void fiver_fluxes(const FaceState<double>& A, const FaceState<double>& SA,
-                                             const FaceState<double>& SB, const FaceState<double>& B, double Fa[5],
-                                             double Fb[5], int flux) {
+template <int D, typename R>
+__device__ __forceinline__ void fiver_fluxes(const FaceState<R>& A, const FaceState<R>& SA, const FaceState<R>& SB,
+                                             const FaceState<R>& B, R Fa[5], R Fb[5], int flux) {
   if (flux == M2C_FLUX_LLF) {
-    llf<D, double>(A, SA, Fa);
-    llf<D, double>(SB, B, Fb);
+    llf<D, R>(A, SA, Fa);
+    llf<D, R>(SB, B, Fb);
     return;
   }
-  hllc<D, double>(A, SA, Fa);
-  hllc<D, double>(SB, B, Fb);
+  hllc<D, R>(A, SA, Fa);
+  hllc<D, R>(SB, B, Fb);
+}
+
+// The two fluxes of an interface face from its cell states (Pa, Pb) and star
+// states (Sa, Sb), in the working precision R of the grid's fluxes: FP64, or
+// FP32 on the mixed path (as the bulk kernel's HLLC); false if a face state is
+// not admissible.
+template <typename R>
+__device__ __forceinline__ bool fiver_face_fluxes(const EosP<R>& qa, const EosP<R>& qb, const double Pa[5],
+                                                  const double Sa[5], const double Sb[5], const double Pb[5], int d,
+                                                  int flux, double Fa[5], double Fb[5]) {
+  FaceState<R> A, SA, SB, B;
+  bool ok = make_face<R, true>(qa, to_r<R>(Pa[0]), to_r<R>(Pa[1]), to_r<R>(Pa[2]), to_r<R>(Pa[3]), to_r<R>(Pa[4]), A);
+  ok = make_face<R, true>(qa, to_r<R>(Sa[0]), to_r<R>(Sa[1]), to_r<R>(Sa[2]), to_r<R>(Sa[3]), to_r<R>(Sa[4]), SA) && ok;
+  ok = make_face<R, true>(qb, to_r<R>(Sb[0]), to_r<R>(Sb[1]), to_r<R>(Sb[2]), to_r<R>(Sb[3]), to_r<R>(Sb[4]), SB) && ok;
+  ok = make_face<R, true>(qb, to_r<R>(Pb[0]), to_r<R>(Pb[1]), to_r<R>(Pb[2]), to_r<R>(Pb[3]), to_r<R>(Pb[4]), B) && ok;
+  R fa[5], fb[5];
+  if (d == 0) fiver_fluxes<0, R>(A, SA, SB, B, fa, fb, flux);
+  else if (d == 1) fiver_fluxes<1, R>(A, SA, SB, B, fa, fb, flux);
+  else fiver_fluxes<2, R>(A, SA, SB, B, fa, fb, flux);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    Fa[v] = to_d<R>(fa[v]);
+    Fb[v] = to_d<R>(fb[v]);
+  }
+  return ok;
 }
 
 // One warp-sized block per 32 faces, so that the few warps of a typical
@@ -111,19 +135,14 @@ __global__ void __launch_bounds__(kFiverThreads, 1) k_fiver(const Grid* __restri
       }
     }
     if (st == M2C_OK) {
-      FaceState<double> A, SA, SB, B;
       double Sa[5] = {rs.rhoL, Pa[1], Pa[2], Pa[3], rs.p};
       double Sb[5] = {rs.rhoR, Pb[1], Pb[2], Pb[3], rs.p};
       Sa[1 + d] = rs.u;
       Sb[1 + d] = rs.u;
-      bool okf = make_face<double, true>(qa, Pa[0], Pa[1], Pa[2], Pa[3], Pa[4], A);
-      okf = make_face<double, true>(qa, Sa[0], Sa[1], Sa[2], Sa[3], Sa[4], SA) && okf;
-      okf = make_face<double, true>(qb, Sb[0], Sb[1], Sb[2], Sb[3], Sb[4], SB) && okf;
-      okf = make_face<double, true>(qb, Pb[0], Pb[1], Pb[2], Pb[3], Pb[4], B) && okf;
+      const bool okf = G.prec == M2C_MIXED
+                           ? fiver_face_fluxes<float>(G.eosf[ia], G.eosf[ib], Pa, Sa, Sb, Pb, d, G.flux, Fa, Fb)
+                           : fiver_face_fluxes<double>(qa, qb, Pa, Sa, Sb, Pb, d, G.flux, Fa, Fb);
       if (!okf) st = M2C_ENONPHYS;
-      if (d == 0) fiver_fluxes<0>(A, SA, SB, B, Fa, Fb, G.flux);
-      else if (d == 1) fiver_fluxes<1>(A, SA, SB, B, Fa, Fb, G.flux);
-      else fiver_fluxes<2>(A, SA, SB, B, Fa, Fb, G.flux);
     }
     if (st != M2C_OK) {
       latch_error(ctrl, st, ca);
