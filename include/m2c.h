@@ -359,7 +359,7 @@ m2c_status m2c_shock_state(const m2c_eos_desc* eos, const double w[3], double p1
  *  - each device that calls it gets its own set-up (the array's address, the
  *    kernels' shared-memory limits); calls on several devices are allowed.
  *  - the first call on a device looks up the array's device address with that
- *    device current; make that first call before any stream capture.
+ *    device current.
  *  - every call shares the one array: calls whose work overlaps on the GPU
  *    (two streams, two host threads) race; serialise them. Each call clears
  *    the counters it needs and synchronises the stream before returning, so
