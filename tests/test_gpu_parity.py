@@ -163,6 +163,32 @@ def test_riemann_host_arrays_and_shock_state(m2c):
     assert code == 6 and st[0] == 6
 
 
+@pytest.mark.parametrize("mixed", [False, True])
+def test_riemann_near_vacuum_matches_oracle(m2c, mixed):
+    """Expansion problems on both sides of the vacuum threshold (air | air: u_R - u_L =
+    4c/(gamma - 1) = 3741.7 m/s; water | air with a stiffened and a Mie-Grueneisen water, near
+    2c_air/(gamma - 1) = 1708 m/s): the GPU
+    solver tests F(p_low) >= 0 only when its Newton iteration has not converged (a root above
+    p_low rules a vacuum out), the oracle before it; the status agrees everywhere, and so does
+    the solution where there is one."""
+    cases = []
+    for du in (1000.0, 3000.0, 3700.0, 3780.0, 3900.0, 6000.0):
+        cases.append((WL.AIR_PG, (1.0, -0.5 * du, 1e5), WL.AIR_PG, (1.0, 0.5 * du, 1e5)))
+    for water in (WL.WATER_SG, WL.WATER_MG):
+        for du in (100.0, 1000.0, 1650.0, 1750.0, 2000.0, 4500.0):
+            cases.append((water, (1000.0, -0.5 * du, 1e5), WL.AIR_PG, (1.2, 0.5 * du, 1e5)))
+    for eL, wL, eR, wR in cases:
+        code, out, it, st = m2c.m2c_solve_riemann_host(eL, np.array(wL).reshape(3, 1), eR, np.array(wR).reshape(3, 1),
+                                                       mixed=mixed)
+        ref_st = O.riemann_status(O.EOS(*eL), wL, O.EOS(*eR), wR)
+        assert st[0] == ref_st, (eL, wL, eR, wR, st[0], ref_st)
+        if ref_st == 0:
+            ref, _ = O.riemann(O.EOS(*eL), wL, O.EOS(*eR), wR)
+            assert abs(out[0, 0] - ref[0]) <= 1e-9 * abs(ref[0]) + 1e-12 * wL[2], (wL, wR, out[:, 0], ref)
+            assert abs(out[1, 0] - ref[1]) <= 1e-9 * max(abs(wL[1]), abs(wR[1]))
+            assert np.allclose(out[2:, 0], ref[2:], rtol=1e-8)
+
+
 @pytest.mark.parametrize("water", [WL.WATER_SG, WL.WATER_MG])
 def test_state_to_prims_matches_oracle(m2c, water):
     """m2c_state_to_prims against the oracle's conversion of the same conserved state, and the
