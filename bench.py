@@ -483,7 +483,7 @@ def run_ours(args):
                              "flops_source": "op-counting build of the oracle (profiles/fp64_flops_per_cell_update.txt)"
                                              "; add, mul, div, sqrt one FLOP each; achieved over the whole step",
                              "peak_source": "measured 1.89 DFMA/clk/SM x 2 FLOPs x SMs x median sampled SM clock",
-                             "fp64_pipe_busy_ncu": 0.74, "kernel": "k_stage<double,8> (bulk stage)",
+                             "fp64_pipe_busy_ncu": 0.72, "kernel": "k_stage<double,8> (bulk stage)",
                              "kernel_ms_avg": round(avg64, 4), "traffic": ncu_traffic("fp64", args.n),
                              "hbm_frac": round(alg_bytes / (avg64 * 1e-3) / 1e9 / hbm, 4)}}
         del g64
