@@ -100,3 +100,15 @@ def test_binding_raises_with_the_library_text_without_a_context():
     assert L.m2c_solve_riemann(0, ctypes.byref(eos), st(), ctypes.byref(eos), st(), out, None, None, 0, None, 0,
                                None) == 0
     assert L.m2c_last_error(None).decode() == ""
+
+
+def test_context_calls_reject_null_arguments_before_any_device_work():
+    """The context entry points return M2C_EINVAL for a null context or null host arrays without
+    touching the device (m2c_step_host among them)."""
+    from paper_2508_16387_gb300 import m2c
+    L = m2c.lib()
+    buf = ctypes.c_void_p(256)
+    assert L.m2c_step_host(None, buf, buf, 1) == m2c.M2C_EINVAL
+    assert L.m2c_step(None, 1) == m2c.M2C_EINVAL
+    assert L.m2c_upload_state(None, buf, buf) == m2c.M2C_EINVAL
+    assert L.m2c_download_state(None, buf, buf) == m2c.M2C_EINVAL
