@@ -265,10 +265,14 @@ __host__ __device__ __forceinline__ double f2d(float x) {
   return f2d_rare(x);
 }
 
-// A group of d2f conversions taken on the common path (normal binary32 range
-// and zeros) with one branch, to the exact d2f of every member, when a member
-// falls outside it: the same results as d2f, and the group stays one basic
-// block in the common case.
+// A group of binary64 -> binary32 conversions (the plane loads of the mixed
+// bulk kernel). On the device: the hardware conversion, round to nearest even,
+// one instruction each on the FP64 pipe, which has room there once the update
+// arithmetic is mostly FP32 (measured faster than the integer path for these
+// loads, slower for the other conversions of the kernel). On the host: the
+// common path of d2f (normal binary32 range and zeros) with one branch, to the
+// exact d2f of every member, when a member falls outside it. Both give the
+// IEEE result.
 __host__ __device__ __forceinline__ float d2f_common(double x, bool& rare) {
   const unsigned hi = hi_of(x), lo = lo_of(x), ah = hi & 0x7fffffffu;
   const unsigned r0 = ((ah - 0x38000000u) << 3) | (lo >> 29);
@@ -281,6 +285,10 @@ __host__ __device__ __forceinline__ float d2f_common(double x, bool& rare) {
 
 template <int K>
 __host__ __device__ __forceinline__ void d2f_group(const double (&x)[K], float (&y)[K]) {
+#ifdef __CUDA_ARCH__
+#pragma unroll
+  for (int i = 0; i < K; ++i) y[i] = __double2float_rn(x[i]);
+#else
   bool rare = false;
 #pragma unroll
   for (int i = 0; i < K; ++i) y[i] = d2f_common(x[i], rare);
@@ -288,6 +296,7 @@ __host__ __device__ __forceinline__ void d2f_group(const double (&x)[K], float (
 #pragma unroll
     for (int i = 0; i < K; ++i) y[i] = d2f(x[i]);
   }
+#endif
 }
 
 // FP64 reciprocal and quotient for the bulk kernels: a binary32 seed of 1/b
