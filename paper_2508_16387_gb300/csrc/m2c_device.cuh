@@ -86,11 +86,19 @@ __device__ __forceinline__ bool make_face(const EosP<R>& q, R rho, R u, R v, R w
   return ok;
 }
 
+// x == 0 (either sign), tested on the bits (off the FP64 pipe for FP64).
+template <typename R>
+__device__ __forceinline__ bool is_zero(R x) {
+  if constexpr (sizeof(R) == 8) return ((hi_of(x) << 1) | lo_of(x)) == 0u;
+  else return (bits_of(x) << 1) == 0u;
+}
+
 // MUSCL face states of one cell along one axis: q -+ sigma/2 with the modified
 // van Albada slope (App. D). same = both stencil neighbours have the cell's
 // material (otherwise first order, Reading R11); a non-admissible face state
 // makes the whole axis first order (Reading R12). bad: even the cell state is
-// not admissible.
+// not admissible. Where every slope vanishes (a locally uniform state) both
+// face states are the cell state, which takes one EOS evaluation instead of two.
 // The general kernels (GEN) take the limiter of the grid: lim = M2C_LIM_MC with
 // alpha, else van Albada.
 template <typename R, bool GEN = false, int T = -1>
@@ -106,12 +114,15 @@ __device__ __forceinline__ void cell_faces(const EosP<R>& q, const R Pm[5], cons
 #pragma unroll
       for (int v = 0; v < 5; ++v) s[v] = va_slope<R>(P[v] - Pm[v], Pp[v] - P[v]);
     }
-    const R hf = (R)0.5;
-    const bool okm = make_face<R, GEN, T>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2],
-                                          P[3] - hf * s[3], P[4] - hf * s[4], Qm);
-    const bool okp = make_face<R, GEN, T>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2],
-                                          P[3] + hf * s[3], P[4] + hf * s[4], Qp);
-    if (okm && okp) return;
+    const bool flat = is_zero(s[0]) && is_zero(s[1]) && is_zero(s[2]) && is_zero(s[3]) && is_zero(s[4]);
+    if (!flat) {
+      const R hf = (R)0.5;
+      const bool okm = make_face<R, GEN, T>(q, P[0] - hf * s[0], P[1] - hf * s[1], P[2] - hf * s[2],
+                                            P[3] - hf * s[3], P[4] - hf * s[4], Qm);
+      const bool okp = make_face<R, GEN, T>(q, P[0] + hf * s[0], P[1] + hf * s[1], P[2] + hf * s[2],
+                                            P[3] + hf * s[3], P[4] + hf * s[4], Qp);
+      if (okm && okp) return;
+    }
   }
   if (!make_face<R, GEN, T>(q, P[0], P[1], P[2], P[3], P[4], Qm)) bad = true;
   Qp = Qm;
