@@ -280,6 +280,42 @@ def test_riemann_matches_brute_force(wL, wR, eosL, eosR):
     assert rr == pytest.approx(brr, rel=1e-9)
 
 
+def _sg_curve(g, pc, rho, p, ps):
+    """Textbook stiffened-gas wave curve f_K(p*) in P = p + p_c (shock: Rankine-Hugoniot;
+    rarefaction: the isentrope), written here independently of the oracle."""
+    P, PK = ps + pc, p + pc
+    if ps >= p:
+        A, B = 2.0 / ((g + 1.0) * rho), (g - 1.0) / (g + 1.0) * PK
+        return (ps - p) * math.sqrt(A / (P + B))
+    c = math.sqrt(g * PK / rho)
+    return 2.0 * c / (g - 1.0) * ((P / PK) ** ((g - 1.0) / (2.0 * g)) - 1.0)
+
+
+@pytest.mark.parametrize("wL,wR,eosL,eosR", [
+    ((1000.0, 0.0, 1e9), (1.2, 0.0, 1e5), WATER, AIR),
+    ((1000.0, 300.0, 1e5), (1.2, -100.0, 1e5), WATER, AIR),
+    ((1000.0, -50.0, 1e6), (1.2, 200.0, 1e5), WATER, AIR),
+    ((1.0, 0.0, 1e5), (0.125, 0.0, 1e4), AIR, AIR),
+    ((1000.0, 5.0, 2e8), (1000.0, -5.0, 1e8), WATER, WATER),
+])
+def test_riemann_star_pressure_to_the_newton_tolerance(wL, wR, eosL, eosR):
+    """Reading R6 stops the Newton iteration at the first step with |dp| <= 1e-12 |p| and keeps
+    that step's update: on closed-form stiffened-gas curves the oracle's p* then agrees with the
+    root of the same F(p) = f_L + f_R + u_R - u_L, found by bracketing to 1e-15, within 1e-14
+    (the rounding level of F). A tolerance of 1e-6, or a stop before the last update, fails it
+    (both checked by planting them in the oracle)."""
+    from scipy.optimize import brentq
+    gL, pcL = eosL.prm[0], eosL.prm[1]
+    gR, pcR = eosR.prm[0], eosR.prm[1]
+
+    def F(ps):
+        return _sg_curve(gL, pcL, wL[0], wL[2], ps) + _sg_curve(gR, pcR, wR[0], wR[2], ps) + (wR[1] - wL[1])
+    lo = max(-pcL, -pcR) + 1e-9 * max(wL[2], wR[2])
+    root = brentq(F, lo, 1e12, xtol=1e-300, rtol=1e-15)
+    (ps, us, rl, rr), _ = O.riemann(eosL, wL, eosR, wR)
+    assert ps == pytest.approx(root, rel=1e-14)
+
+
 def test_riemann_trivial_and_symmetric_cases():
     w = (1000.0, 12.0, 3e7)
     (ps, us, rl, rr), _ = O.riemann(WATER, w, WATER, w)
