@@ -316,6 +316,25 @@ def test_riemann_star_pressure_to_the_newton_tolerance(wL, wR, eosL, eosR):
     assert ps == pytest.approx(root, rel=1e-14)
 
 
+@pytest.mark.parametrize("w,p", [((1000.0, 0.0, 1e5), 1e8), ((1000.0, 0.0, 1e5), 2e9), ((1100.0, 50.0, 3e8), 5e9),
+                                 ((1000.0, 0.0, 1e5), 1.0001e5)])
+def test_mg_shock_density_to_the_hugoniot_tolerance(w, p):
+    """The MG shock branch's density solves the Hugoniot energy equation
+    H(rho) = e(rho, p) - e_K - (p + p_K)(1/rho_K - 1/rho)/2 = 0 (Sec. 4.2, App. B.3), found by
+    Newton stopped at the first step below 1e-14 rho (Reading R6): within 1e-14 of the root found
+    by bracketing the same H (with the oracle's e(rho, p), pinned above). A Newton tolerance of
+    1e-7 planted in the oracle fails it."""
+    from scipy.optimize import brentq
+    eK = O.energy(MGW, w[0], w[2])
+
+    def H(r):
+        return O.energy(MGW, r, p) - eK - 0.5 * (p + w[2]) * (1.0 / w[0] - 1.0 / r)
+    hi = 1000.0 * 1.75 / 0.75 * (1.0 - 1e-12)
+    root = brentq(H, w[0] * (1.0 + 1e-15), hi, xtol=1e-300, rtol=1e-15)
+    _, _, rho = O.wave_curve(MGW, w, p)
+    assert rho == pytest.approx(root, rel=1e-14)
+
+
 def test_riemann_trivial_and_symmetric_cases():
     w = (1000.0, 12.0, 3e7)
     (ps, us, rl, rr), _ = O.riemann(WATER, w, WATER, w)
