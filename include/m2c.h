@@ -120,7 +120,8 @@ size_t m2c_workspace_bytes(int nx, int ny, int nz, int precision);
  * bc[6]: m2c_bc per side, workspace: device pointer of ws_bytes >=
  * m2c_workspace_bytes(), stream: a cudaStream_t (NULL = legacy default stream).
  * Defaults: CFL 0.5, reinitialisation every 10 steps with 5 iterations.
- * Argument errors return before any device work, with the reason in
+ * Argument errors return before any device work; they and a failed first
+ * device call (M2C_ECUDA, no context created) leave the reason in
  * m2c_last_error(NULL). */
 m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[3], double h, const int bc[6],
                          int precision, void* workspace, size_t ws_bytes, void* stream);

@@ -966,7 +966,7 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   const Layout L = layout_for(N);
   if (ws_bytes < L.total) return set_err(nullptr, M2C_ENOMEM, "workspace smaller than m2c_workspace_bytes()");
   m2c_ctx* c = new (std::nothrow) m2c_ctx();
-  if (!c) return M2C_ENOMEM;
+  if (!c) return set_err(nullptr, M2C_ENOMEM, "out of host memory for the context");
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   Grid& g = c->host;
   std::memset(&g, 0, sizeof(g));
@@ -1017,15 +1017,17 @@ m2c_status m2c_init_grid(m2c_ctx** out, int nx, int ny, int nz, const double lo[
   c->profiling = false;
   c->profile_bulk_only = false;
   c->ev_used = 0;
+  // a failure here leaves no context: its text goes to m2c_last_error(NULL)
   cudaError_t e = cudaMemsetAsync(g.ctrl, 0, sizeof(Ctrl), c->stream);
   if (e != cudaSuccess) {
     delete c;
-    return M2C_ECUDA;
+    return set_err(nullptr, M2C_ECUDA, std::string("control block reset: ") + cudaGetErrorString(e));
   }
   m2c_status st = push_grid(c);
   if (st != M2C_OK) {
+    const std::string why = c->err;
     delete c;
-    return st;
+    return set_err(nullptr, st, why);
   }
   *out = c;
   return M2C_OK;
