@@ -137,6 +137,20 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _buf(t, numel, name, cuda):
+    """Pointer of t after checking that it is a contiguous float64 torch tensor of numel
+    elements on the device (cuda) or on the host: the library reads or writes numel doubles
+    through the pointer and has no other way to know the buffer's extent."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: a torch tensor is required, got {type(t).__name__}")
+    where = "device" if cuda else "host"
+    if t.is_cuda != cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name}: a contiguous float64 {where} tensor of {numel} elements is required, got "
+                         f"{t.dtype} {tuple(t.shape)} on {t.device}{'' if t.is_contiguous() else ' (strided)'}")
+    return _ptr(t)
+
+
 def _stream_handle(stream):
     import torch
     if stream is None:
@@ -163,14 +177,20 @@ def m2c_solve_riemann(eosL, L, eosR, R, stream=None, mixed=False):
     Returns (out (4, n): p*, u*, rho*_L, rho*_R; iters (n,); status (n,)).
     mixed=True: the mixed path's solve (m2c_solve_riemann_mixed)."""
     import torch
+    if not (isinstance(L, torch.Tensor) and isinstance(R, torch.Tensor)) or L.dim() != 2 or L.shape[0] != 3 \
+            or tuple(R.shape) != tuple(L.shape):
+        raise ValueError(f"L and R of shape (3, n) are required, got {tuple(L.shape)} and {tuple(R.shape)}")
     n = L.shape[1]
+    # contiguous copies (if any) stay referenced until the call returns: the
+    # kernel reads them on the stream after the launch
+    Lc, Rc = L.contiguous(), R.contiguous()
     out = torch.empty((4, n), dtype=torch.float64, device=L.device)
     iters = torch.zeros(n, dtype=torch.int32, device=L.device)
     status = torch.zeros(n, dtype=torch.int32, device=L.device)
     eL, eR = eos_desc(eosL), eos_desc(eosR)
     fn = lib().m2c_solve_riemann_mixed if mixed else lib().m2c_solve_riemann
-    code = fn(n, ctypes.byref(eL), _ptr(L.contiguous()), ctypes.byref(eR), _ptr(R.contiguous()), _ptr(out),
-              _ptr(iters), _ptr(status), 1, None, 0, _stream_handle(stream))
+    code = fn(n, ctypes.byref(eL), _buf(Lc, 3 * n, "L", True), ctypes.byref(eR), _buf(Rc, 3 * n, "R", True),
+              _ptr(out), _ptr(iters), _ptr(status), 1, None, 0, _stream_handle(stream))
     _check(code, "m2c_solve_riemann_mixed" if mixed else "m2c_solve_riemann")
     return out, iters, status
 
@@ -224,10 +244,12 @@ def m2c_residual_noalloc(n, h, bc, eos, W, phi, R, L, precision=FP64, stream=Non
     """Stage residual with no context and no workspace (library-held scratch).
     W (5, nz, ny, nx), phi, R, L: float64 device tensors. Returns the status code."""
     nx, ny, nz = n
+    N = nx * ny * nz
     bcs = (ctypes.c_int * 6)(*bc)
     e0, e1 = eos_desc(eos[0]), eos_desc(eos[1])
     return lib().m2c_residual_noalloc(nx, ny, nz, h, bcs, ctypes.byref(e0), ctypes.byref(e1), precision,
-                                      _ptr(W), _ptr(phi), _ptr(R), _ptr(L), _stream_handle(stream))
+                                      _buf(W, 5 * N, "W", True), _buf(phi, N, "phi", True),
+                                      _buf(R, 5 * N, "R", True), _buf(L, N, "L", True), _stream_handle(stream))
 
 
 def m2c_residual_noalloc_scratch_bytes() -> int:
@@ -316,7 +338,8 @@ class Grid:
         self.phi.copy_(torch.as_tensor(phi, dtype=torch.float64))
         _check(lib().m2c_set_state(self.ctx, _ptr(self.W), _ptr(self.phi), t, step), "m2c_set_state", self.ctx)
         P = torch.as_tensor(prims, dtype=torch.float64).to(self.device).contiguous()
-        _check(lib().m2c_prims_to_state(self.ctx, _ptr(P)), "m2c_prims_to_state", self.ctx)
+        _check(lib().m2c_prims_to_state(self.ctx, _buf(P, 5 * self.N, "prims", True)), "m2c_prims_to_state",
+               self.ctx)
 
     def prims(self):
         """Primitive fields (5, nz, ny, nx) of the current state (device tensor, FP64)."""
@@ -326,11 +349,15 @@ class Grid:
         _check(lib().m2c_state_to_prims(self.ctx, _ptr(P)), "m2c_state_to_prims", self.ctx)
         return P
 
+    def _host_state(self, W_host, phi_host):
+        return _buf(W_host, 5 * self.N, "W_host", False), _buf(phi_host, self.N, "phi_host", False)
+
     def upload(self, W_host, phi_host):
-        _check(lib().m2c_upload_state(self.ctx, _ptr(W_host), _ptr(phi_host)), "m2c_upload_state", self.ctx)
+        _check(lib().m2c_upload_state(self.ctx, *self._host_state(W_host, phi_host)), "m2c_upload_state", self.ctx)
 
     def download(self, W_host, phi_host):
-        _check(lib().m2c_download_state(self.ctx, _ptr(W_host), _ptr(phi_host)), "m2c_download_state", self.ctx)
+        _check(lib().m2c_download_state(self.ctx, *self._host_state(W_host, phi_host)), "m2c_download_state",
+               self.ctx)
 
     # -- stepping
     def step(self, nsteps=1):
@@ -339,7 +366,7 @@ class Grid:
     def step_host(self, W_host, phi_host, nsteps=1):
         """m2c_step_host: upload the state from the (pinned) host arrays, step, download it back
         into them; asynchronous (sync() waits)."""
-        _check(lib().m2c_step_host(self.ctx, _ptr(W_host), _ptr(phi_host), nsteps), "m2c_step_host", self.ctx)
+        _check(lib().m2c_step_host(self.ctx, *self._host_state(W_host, phi_host), nsteps), "m2c_step_host", self.ctx)
 
     def sync(self):
         t = ctypes.c_double()

@@ -112,3 +112,27 @@ def test_context_calls_reject_null_arguments_before_any_device_work():
     assert L.m2c_step(None, 1) == m2c.M2C_EINVAL
     assert L.m2c_upload_state(None, buf, buf) == m2c.M2C_EINVAL
     assert L.m2c_download_state(None, buf, buf) == m2c.M2C_EINVAL
+
+
+def test_binding_checks_buffers_before_the_library_sees_them():
+    """The binding passes raw pointers, so it checks each buffer's place (host or device),
+    type, contiguity and element count first: a wrong buffer raises before any library call."""
+    import torch
+    from paper_2508_16387_gb300 import m2c
+    ok = torch.zeros((5, 2, 3, 4), dtype=torch.float64)
+    assert m2c._buf(ok, 120, "W", False).value == ok.data_ptr()
+    for bad, err in ((ok.float(), ValueError), (ok[:, :, :, :2], ValueError), (ok.transpose(0, 3), ValueError),
+                     (ok.reshape(-1)[:100], ValueError), (ok.numpy(), TypeError)):
+        with pytest.raises(err):
+            m2c._buf(bad, 120, "W", False)
+    with pytest.raises(ValueError, match="device tensor"):
+        m2c._buf(ok, 120, "W", True)  # a host tensor where a device buffer is needed
+    L = torch.zeros((3, 8), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        m2c.m2c_solve_riemann((m2c.EOS_SG, (1.4, 0.0)), L, (m2c.EOS_SG, (1.4, 0.0)), L)
+    with pytest.raises(ValueError, match=r"\(3, n\)"):
+        m2c.m2c_solve_riemann((m2c.EOS_SG, (1.4, 0.0)), L, (m2c.EOS_SG, (1.4, 0.0)), L[:, :4])
+    W = torch.zeros((5, 4, 4, 4), dtype=torch.float64)
+    phi = torch.zeros((4, 4, 4), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        m2c.m2c_residual_noalloc((4, 4, 4), 0.25, (0,) * 6, ((0, (1.4, 0.0)), (0, (1.4, 0.0))), W, phi, W, phi)

@@ -56,16 +56,19 @@ def test_noalloc_residual_matches_context_residual_twice_in_a_row(m2c):
         assert np.abs(L - L_ctx).max() <= 1e-11 * max(np.abs(L_ctx).max(), 1.0)
 
 
-@pytest.mark.gpu
-def test_noalloc_rejects_grids_above_its_maximum(m2c):
-    import torch
-    n = (128, 64, 33)   # 270336 cells > 262144
-    W = torch.zeros((5, 1), dtype=torch.float64, device="cuda")
-    phi = torch.zeros(1, dtype=torch.float64, device="cuda")
-    code = m2c.m2c_residual_noalloc(n, 1.0 / 128, (0,) * 6, (WL.WATER_SG, WL.AIR_PG), W, phi, W, phi)
-    assert code == 1
-    assert b"exceed" in m2c.lib().m2c_last_error(None)
-    assert m2c.m2c_residual_noalloc_scratch_bytes() < 16 * 2 ** 20
+def test_noalloc_rejects_grids_above_its_maximum():
+    """The size check runs on the host before any device work (the array pointers are never
+    dereferenced, so this runs without a GPU)."""
+    from paper_2508_16387_gb300 import m2c as M
+    L = M.lib()
+    e0, e1 = M.eos_desc(WL.WATER_SG), M.eos_desc(WL.AIR_PG)
+    fake = ctypes.c_void_p(256)
+    # 128 x 64 x 33 = 270336 cells > 262144
+    code = L.m2c_residual_noalloc(128, 64, 33, 1.0 / 128, (ctypes.c_int * 6)(*(0,) * 6), ctypes.byref(e0),
+                                  ctypes.byref(e1), M.FP64, fake, fake, fake, fake, None)
+    assert code == M.M2C_EINVAL
+    assert b"exceed" in L.m2c_last_error(None)
+    assert M.m2c_residual_noalloc_scratch_bytes() < 16 * 2 ** 20
 
 
 @pytest.mark.parametrize("eos0,eos1,bc,why", [
