@@ -171,10 +171,11 @@ class Server:
                 dirty = True
             st.max_resident = max(st.max_resident, len(resident))
             if not resident:
+                # with nothing resident, no eviction can free memory for the head of the queue
+                if queue:
+                    raise RuntimeError(f"job {queue[0].job_id} does not fit in device memory")
                 if pending and realtime:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now())))
-                elif queue:
-                    raise RuntimeError("a queued job does not fit in device memory")
                 continue
             if dirty:
                 batch = None

@@ -3,6 +3,7 @@ admission in arrival order while free memory allows, the resident cap, slices th
 job past its step count, failure of one job at admission isolated from the others, the
 too-large-job error, and the accounting of cell updates and times."""
 import math
+import time
 import types
 
 import pytest
@@ -117,6 +118,17 @@ def test_a_job_failing_at_admission_does_not_stop_the_others(fake_device):
 def test_a_job_that_can_never_fit_is_an_error(fake_device):
     with pytest.raises(RuntimeError):
         _server([100], slice_steps=10).run(_jobs([(10, 10)]), realtime=False)
+
+
+def test_a_job_that_can_never_fit_fails_at_once_in_real_time(fake_device):
+    """With nothing resident the error comes when the job is queued, not after the later jobs of
+    the trace have arrived (their arrival frees no memory)."""
+    jobs = _jobs([(10, 10), (4, 10)])
+    jobs[1] = WL.Job(1, 30.0, jobs[1].params)   # arrives 30 s later
+    t0 = time.perf_counter()
+    with pytest.raises(RuntimeError, match="job 0"):
+        _server([100], slice_steps=10).run(jobs, realtime=True)
+    assert time.perf_counter() - t0 < 5.0
 
 
 def test_percentiles_of_latency():
