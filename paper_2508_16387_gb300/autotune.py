@@ -2,8 +2,11 @@
 on the mixed path, 32 x 16 columns; z-length of a tile), tile schedule (fixed
 stride or atomic counter) and persistent grid size, picked by timing candidates with CUDA events on the
 actual grids. The state is saved before and restored after every trial, so
-tuning leaves the simulation where it was; results never depend on the choice
-(every cell is computed by the same arithmetic under every tiling).
+tuning leaves the simulation where it was, except that the exact Riemann
+solver's warm-start star pressures start empty again (a restored state is a
+new state), which moves later results by no more than the Newton tolerance.
+The choice itself never changes a result (every cell is computed by the same
+arithmetic under every tiling).
 """
 from __future__ import annotations
 
