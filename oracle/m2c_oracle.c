@@ -641,7 +641,12 @@ static int riemann_F(const or_eos_t* qL, const side_t* L, const or_eos_t* qR, co
  * K-wave. Reading R7: no vacuum solution is built; if F(p_low) >= 0 the call
  * fails with OR_EVACUUM. Both wave curves increase with p and vanish at their
  * side's pressure (>= p_low), so F(p_low) <= u_R - u_L: the test is only made
- * when u_R - u_L >= 0. out = {p*, u*, rho*_L, rho*_R}. */
+ * when u_R - u_L >= 0; and since F increases with p, a root above p_low found
+ * by Newton rules a vacuum out, so the test is made only when Newton has not
+ * converged (before the bisection). This also keeps a solution whose wave
+ * curves cannot be evaluated at p_low itself: the MG isentrope's sound speed
+ * vanishes at the tensile cutoff p_min = K0 eta_min. out = {p*, u*, rho*_L,
+ * rho*_R}. */
 static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, const double wR[3], double out[4], int* iters) {
   side_t L, R;
   int st = make_side(qL, wL, &L);
@@ -654,11 +659,7 @@ static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, c
   set_rarefaction_steps(qR, &R, fmax(plow, fmin(L.p, pac)));
   double F, dF;
   /* Reading R36: no vacuum test with a JWL side (its rarefaction needs p > 0) */
-  if (isfinite(plow) && R.u - L.u >= 0.0 && qL->type != EOS_JWL && qR->type != EOS_JWL) {
-    st = riemann_F(qL, &L, qR, &R, plow, &F, &dF);
-    if (st) return st;
-    if (F >= 0.0) return OR_EVACUUM;
-  }
+  const int vacuum_test = isfinite(plow) && R.u - L.u >= 0.0 && qL->type != EOS_JWL && qR->type != EOS_JWL;
   double p = 0.5 * (L.p + R.p) - 0.125 * (R.u - L.u) * (L.rho + R.rho) * (L.c + R.c);
   if (!(p > plow)) {
     double gap = fmin(L.p, R.p) - plow;
@@ -676,6 +677,11 @@ static int riemann(const or_eos_t* qL, const double wL[3], const or_eos_t* qR, c
     if (small) { conv = 1; break; }
   }
   if (!conv) {
+    if (vacuum_test) {
+      st = riemann_F(qL, &L, qR, &R, plow, &F, &dF);
+      if (st) return st;
+      if (F >= 0.0) return OR_EVACUUM;
+    }
     /* bisection on a bracket [a, b] with F(a) < 0 < F(b) */
     double a = plow, b = fmax(L.p, R.p);
     if (!isfinite(a)) {

@@ -317,13 +317,14 @@ def test_riemann_star_pressure_to_the_newton_tolerance(wL, wR, eosL, eosR):
 
 
 @pytest.mark.parametrize("w,p", [((1000.0, 0.0, 1e5), 1e8), ((1000.0, 0.0, 1e5), 2e9), ((1100.0, 50.0, 3e8), 5e9),
-                                 ((1000.0, 0.0, 1e5), 1.0001e5)])
+                                 ((1000.0, 0.0, 1e5), 1.0001e5), ((1000.0, 0.0, 1e5), 3e11)])
 def test_mg_shock_density_to_the_hugoniot_tolerance(w, p):
     """The MG shock branch's density solves the Hugoniot energy equation
     H(rho) = e(rho, p) - e_K - (p + p_K)(1/rho_K - 1/rho)/2 = 0 (Sec. 4.2, App. B.3), found by
     Newton stopped at the first step below 1e-14 rho (Reading R6): within 1e-14 of the root found
     by bracketing the same H (with the oracle's e(rho, p), pinned above). A Newton tolerance of
-    1e-7 planted in the oracle fails it."""
+    1e-7 planted in the oracle fails it. The last case (3e11 Pa, rho* above 0.9 of the maximum
+    compression rho0 s/(s - 1)) fails a bracket that stops short of that limit."""
     from scipy.optimize import brentq
     eK = O.energy(MGW, w[0], w[2])
 
@@ -388,6 +389,25 @@ def test_shock_state_satisfies_rankine_hugoniot(eos, w, p1):
         assert res < 1e-11
 
 
+@pytest.mark.parametrize("eos", [MGW, WATER, AIR])
+def test_shock_speed_is_galilean_and_carries_the_momentum_jump(eos):
+    """The shock speed returned with a post-shock state: moving the state ahead by a velocity
+    moves the shock and the state behind by the same velocity (Galilean invariance of the Euler
+    equations), and the speed carries the momentum jump rho0 (u0 - S)^2 + p0 =
+    rho1 (u1 - S)^2 + p1 (Rankine-Hugoniot)."""
+    w0 = (1000.0, 0.0, 1e5) if eos is not AIR else (1.2, 0.0, 1e5)
+    p1 = 1e9 if eos is not AIR else 5e5
+    rho_a, u_a, S_a = O.shock_state(eos, w0, p1)
+    for du in (75.0, -140.0):
+        rho_b, u_b, S_b = O.shock_state(eos, (w0[0], w0[1] + du, w0[2]), p1)
+        assert rho_b == pytest.approx(rho_a, rel=1e-13)
+        assert u_b == pytest.approx(u_a + du, rel=1e-12)
+        assert S_b == pytest.approx(S_a + du, rel=1e-12)
+        lhs = w0[0] * (w0[1] + du - S_b) ** 2 + w0[2]
+        rhs = rho_b * (u_b - S_b) ** 2 + p1
+        assert lhs == pytest.approx(rhs, rel=1e-11)
+
+
 @pytest.mark.parametrize("w,p,tol", [((1000.0, 0.0, 1e9), 1e5, 1e-8), ((1000.0, 0.0, 1e5), -5e6, 1e-8),
                                      ((1250.0, 0.0, 2e9), 1.5e9, 1e-8), ((2204.0, 0.0, 1e5), 0.03, 1e-8),
                                      ((1250.0, 0.0, 2e9), 3e8, 2e-5)])
@@ -415,6 +435,64 @@ def test_mg_rarefaction_matches_ode_integration(w, p, tol):
     assert f == pytest.approx(f_end, rel=max(tol, 1e-7), abs=1e-9)
     # derivative of the wave curve is 1/(rho c) at the end state (Sec. 4.2, isentrope)
     assert df == pytest.approx(1.0 / (rho_star * math.sqrt(O.sound_speed2(eos, rho_star, p))), rel=1e-12)
+
+
+def _isentrope_until(eos, w, stop):
+    """Integrates the isentrope through w = (rho, u, p) towards lower density with scipy's DOP853
+    on the energy form de/drho = p/rho^2, df/drho = c/rho (f = the velocity change, negative
+    below rho_K) until stop(rho, e, f) = 0; returns (rho, p, f) there."""
+    e0 = O.energy(eos, w[0], w[2])
+
+    def rhs(r, y):
+        pr = O.pressure(eos, r, y[0])
+        return [pr / r ** 2, math.sqrt(O.sound_speed2(eos, r, pr)) / r]
+
+    def ev(r, y):
+        return stop(r, y[0], y[1])
+    ev.terminal = True
+    sol = solve_ivp(rhs, (w[0], 0.5 * w[0]), [e0, 0.0], events=ev, rtol=1e-12, atol=1e-12, method="DOP853")
+    r = sol.t_events[0][0]
+    e, f = sol.y_events[0][0]
+    return r, O.pressure(eos, r, e), f
+
+
+@pytest.mark.parametrize("eos,w,u", [
+    (MGW, (1300.0, 0.0, 1e9), 100.0),       # strong rarefactions on the fixed RK4 nodes
+    (MGW, (1300.0, 0.0, 2e9), 400.0),
+    (MGW, (1000.0, 0.0, 1e5), 20.0),        # into tension, no cutoff
+    (MGW_CUT, (1000.0, 0.0, 1e5), 30.0),    # into tension above the cutoff p_min = K0 eta_min
+    (MGW_CUT, (1000.0, 0.0, 1e5), 70.0),
+])
+def test_mg_riemann_rarefactions_match_ode_integration(eos, w, u):
+    """Two MG states separating at +-u (Sec. 4.2): by symmetry u* = 0 and p* is where the
+    rarefaction's velocity change reaches -u, found here by integrating the isentrope with
+    DOP853 (the energy form, c^2 pinned above). This exercises the exact solver's rarefaction
+    curves on the problem's fixed RK4 nodes (Reading R6) far from the side state, and, with a
+    tensile cutoff, a star pressure below zero but above the cutoff's p_min = rho0 c0^2 eta_min
+    (a wrong p_min, or a node shifted by one spacing, planted in the oracle fails it)."""
+    rho_s, p_s, _ = _isentrope_until(eos, w, lambda r, e, f: f + u)
+    wl, wr = (w[0], -u, w[2]), (w[0], u, w[2])
+    (ps, us, rl, rr), _ = O.riemann(eos, wl, eos, wr)
+    K0 = eos.prm[0] * eos.prm[1] ** 2
+    assert ps == pytest.approx(p_s, rel=1e-9, abs=1e-10 * K0)
+    assert abs(us) <= 1e-9 * u
+    assert rl == pytest.approx(rho_s, rel=1e-9) and rr == pytest.approx(rho_s, rel=1e-9)
+    if eos is MGW_CUT:
+        assert K0 * eos.prm[5] < ps < 0.0
+
+
+@pytest.mark.parametrize("w,p", [((1000.0, 0.0, 1e5), 1e8), ((1000.0, 0.0, 1e5), 2e9), ((1100.0, 50.0, 3e8), 5e9),
+                                 ((1000.0, 0.0, 1e5), 3e11)])
+def test_mg_shock_curve_slope_is_the_derivative_of_the_curve(w, p):
+    """The slope the MG shock branch returns (it drives the Newton iteration of the exact
+    solver, Sec. 4.2) equals a central difference of the returned velocity change; d rho/dp on
+    the Hugoniot comes from implicit differentiation of the energy equation, whose de/drho|_p a
+    sign error planted in the oracle spoils."""
+    f, df, _ = O.wave_curve(MGW, w, p)
+    dp = 1e-5 * (p - w[2])
+    fp, _, _ = O.wave_curve(MGW, w, p + dp)
+    fm, _, _ = O.wave_curve(MGW, w, p - dp)
+    assert df == pytest.approx((fp - fm) / (2 * dp), rel=1e-6)
 
 
 # --------------------------------------------------------------------------- flow solver
@@ -496,6 +574,70 @@ def test_shock_bubble_is_mirror_symmetric():
     assert np.array_equal(r.phi < 0, (r.phi < 0)[:, ::-1, :])
 
 
+def _boundary(pred, lo, hi, iters=200):
+    """Bisection for the point where pred changes between lo (pred true) and hi (pred false)."""
+    assert pred(lo) and not pred(hi)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if pred(mid):
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("eL,wL,eR,wR,shocks", [
+    (WATER, (1000.0, 0.0, 1e9), AIR, (1.0, 0.0, 1e5), (False, True)),     # stiffened fan | shock
+    (AIR, (1.0, 0.0, 1e5), WATER, (1000.0, 0.0, 1e9), (True, False)),     # shock | stiffened fan
+    (AIR, (1.0, 200.0, 1e5), AIR, (1.0, -200.0, 1e5), (True, True)),      # two shocks
+    (AIR, (1.0, -100.0, 1e5), WATER, (1000.0, 100.0, 1e7), (False, False)),  # two fans
+])
+def test_exact_sampler_waves_satisfy_their_relations(eL, wL, eR, wR, shocks):
+    """The exact two-stiffened-gas solution that the shock-tube convergence test measures
+    against: each shock, located by bisection on xi = x/t, moves at the speed that carries the
+    mass, momentum and energy jumps between the outer and the star state; each fan starts at
+    u_K -+ c_K and ends at u* -+ c*_K, and inside it the state keeps (p + p_c)/rho^gamma and the
+    Riemann invariant u +- 2c/(gamma - 1) of its side and sits on the characteristic xi = u -+ c."""
+    def sample(xi):
+        out, _ = O.exact_sample_sg(eL.prm, wL, eR.prm, wR, np.array([xi]))
+        return out[:, 0]
+    _, (ps, us, rls, rrs) = O.exact_sample_sg(eL.prm, wL, eR.prm, wR, np.zeros(1))
+    for eos, w, rs, sgn, shock in ((eL, wL, rls, -1.0, shocks[0]), (eR, wR, rrs, 1.0, shocks[1])):
+        g, pc = eos.prm
+        assert (ps > w[2]) == shock
+        c = math.sqrt(g * (w[2] + pc) / w[0])
+        far = us + sgn * 10.0 * (abs(w[1]) + c + abs(us))
+
+        def outer(xi):
+            return np.array_equal(sample(xi), np.array(w))
+
+        def star(xi):
+            q = sample(xi)
+            return q[0] == rs and q[1] == us and q[2] == ps
+        if shock:
+            S = _boundary(outer, far, us + sgn * 1e-9)
+            assert star(S - sgn * 1e-9 * abs(S)) and outer(S + sgn * 1e-9 * abs(S))
+            for res in _rh_residuals(lambda r, p: _e_sg(eos, r, p), w, (rs, us, ps)):
+                assert res < 1e-12
+            S_rh = (rs * us - w[0] * w[1]) / (rs - w[0])   # the speed the jumps require
+            assert S == pytest.approx(S_rh, rel=1e-9)
+        else:
+            head = _boundary(outer, far, us + sgn * 1e-9)
+            tail = _boundary(star, us + sgn * 1e-9, head)
+            cs = math.sqrt(g * (ps + pc) / rs)
+            assert head == pytest.approx(w[1] + sgn * c, rel=1e-9, abs=1e-9 * c)
+            assert tail == pytest.approx(us + sgn * cs, rel=1e-9, abs=1e-9 * c)
+            ent = (w[2] + pc) / w[0] ** g
+            inv = w[1] - sgn * 2.0 * c / (g - 1.0)
+            for f in (0.1, 0.37, 0.5, 0.81, 0.95):
+                xi = tail + f * (head - tail)
+                rho, u, p = sample(xi)
+                cf = math.sqrt(g * (p + pc) / rho)
+                assert (p + pc) / rho ** g == pytest.approx(ent, rel=1e-11)
+                assert u - sgn * 2.0 * cf / (g - 1.0) == pytest.approx(inv, rel=1e-11, abs=1e-9 * c)
+                assert u + sgn * cf == pytest.approx(xi, rel=1e-11, abs=1e-9 * c)
+
+
 def test_shock_tube_converges_to_exact_solution():
     """Water | air shock tube on nx x 1 x 1 grids: L1 error of density against the exact
     two-stiffened-gas solution decreases under refinement (Sec. 5.1 verification approach)."""
@@ -569,6 +711,42 @@ def test_level_set_stencil_is_exact_for_cubics():
         assert np.allclose(L[:, :, inner], (-u * dphi)[:, :, inner], rtol=1e-11, atol=1e-9)
 
 
+@pytest.mark.parametrize("vel", [(37.0, -23.0, 11.0), (-19.0, 29.0, -13.0)])
+def test_level_set_residual_of_a_quartic_in_every_axis(vel):
+    """L = -((u phi_x + v phi_y) + w phi_z) (Eq. levelset) with the third-order upwind-biased
+    derivative of Sec. 4.4 along each axis: on phi = quartic(x) + quartic(y) + quartic(z) in a
+    uniform flow each derivative is exact up to its truncation term, which for the stencil of a
+    positive velocity is +(h^3/12) phi and for the other -(h^3/12) phi (Taylor
+    expansion), so the residual checks the sign of every velocity term and that each axis is
+    upwinded by its own velocity component."""
+    n = (12, 12, 12)
+    h = 1.0 / 12
+    s = WL.Setup("quartic", n, h, (WL.WATER_SG, WL.AIR_PG), (0,) * 6, np.ones((12, 12, 12)),
+                 np.zeros((12, 12, 12), np.uint8), {})
+    x, y, z = WL.cell_centres(n, h)
+    coef = {"x": (0.3, -0.4, 0.7, 0.2), "y": (-0.2, 0.5, -0.3, 0.1), "z": (0.25, 0.1, 0.4, -0.3)}
+
+    def q(t, c):          # c4 t^4 + c3 t^3 + c2 t^2 + c1 t, t about 0.4
+        t = t - 0.4
+        return ((c[0] * t + c[1]) * t + c[2]) * t * t + c[3] * t
+
+    def dq(t, c):
+        t = t - 0.4
+        return ((4 * c[0] * t + 3 * c[1]) * t + 2 * c[2]) * t + c[3]
+    phi = 2.0 + q(x, coef["x"]) + q(y, coef["y"]) + q(z, coef["z"])
+    P = np.zeros((5,) + phi.shape)
+    P[0], P[1], P[2], P[3], P[4] = 1000.0, vel[0], vel[1], vel[2], 1e8
+    g = _grid(s)
+    _, L, _ = O.residual(g, O.prims_to_cons(g, P, phi), phi)
+    D = [dq(t, coef[a]) + math.copysign(1.0, v) * h ** 3 / 12.0 * 24.0 * coef[a][0]
+         for t, a, v in ((x, "x", vel[0]), (y, "y", vel[1]), (z, "z", vel[2]))]
+    expect = -((vel[0] * D[0] + vel[1] * D[1]) + vel[2] * D[2])
+    inner = (slice(2, -2),) * 3
+    assert np.abs(L[inner] - expect[inner]).max() < 1e-9
+    # the truncation terms are well above that bound: the wrong upwind choice on any axis fails
+    assert min(abs(v) for v in vel) * 2 * h ** 3 / 12.0 * 24.0 * 0.2 > 1e-3
+
+
 def test_reinit_keeps_a_plane_distance_and_every_sign():
     n = (20, 6, 6)
     g = O.Grid(n=n, h=1.0 / 20, eos=(O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)), bc=(0,) * 6)
@@ -589,6 +767,43 @@ def test_reinit_keeps_a_plane_distance_and_every_sign():
     away[[0, 1, 9, grad.shape[2] - 2, grad.shape[2] - 1]] = False   # boundary faces and the frozen pair
     assert np.abs(grad[:, :, away] - 1.0).max() < 1e-6
     assert np.array_equal(out3 < 0, phi3 < 0)
+
+
+def test_reinit_keeps_a_distance_with_ridges():
+    """The signed distance to two parallel planes on a periodic domain has a ridge (a kink of
+    |grad phi| = 1 with the two one-sided slopes of opposite sign) in the middle of each phase,
+    here on cell centres. It is a fixed point of the reinitialisation (Eq. reinit): the
+    Godunov upwind norm of Sec. 4.4 takes the larger of the two admissible one-sided slopes
+    along an axis, not their sum, so at a ridge it is still 1 (a sum planted in the oracle
+    moves both ridges)."""
+    n, h = (32, 4, 4), 1.0 / 32
+    g = O.Grid(n=n, h=h, eos=(O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)), bc=(1, 1, 0, 0, 0, 0))
+    x, _, _ = WL.cell_centres(n, h)
+    a, b = 9.2 * h, 23.8 * h      # ridges at x = 16.5 h (inside) and 0.5 h (outside, periodic)
+
+    def dper(t):
+        d = np.abs(x - t)
+        return np.minimum(d, 1.0 - d)
+    phi = np.where((x > a) & (x < b), -np.minimum(x - a, b - x), np.minimum(dper(a), dper(b)))
+    out = O.reinit(g, phi, 5)
+    assert np.abs(out - phi).max() < 1e-13
+
+
+def test_one_reinit_iteration_in_closed_form():
+    """One pseudo-time iteration of Eq. reinit on phi = 2 (x - 0.43) (|grad phi| = 2): away from
+    the frozen first layer every cell moves by dtau S(phi0) (G - 1) with G = 2 (the upwind
+    one-sided slopes), dtau = h/2 and S = phi0 / sqrt(phi0^2 + h^2) (Reading R24), all values
+    read from the previous iterate (Jacobi)."""
+    n, h = (20, 4, 4), 1.0 / 20
+    g = O.Grid(n=n, h=h, eos=(O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)), bc=(0,) * 6)
+    x, _, _ = WL.cell_centres(n, h)
+    phi = 2.0 * (x - 0.43)
+    out = O.reinit(g, phi, 1)
+    expect = phi - 0.5 * h * phi / np.sqrt(phi * phi + h * h) * (2.0 - 1.0)
+    moving = np.ones(n[0], bool)
+    moving[[8, 9]] = False        # the first layer: cells 8 (phi < 0) and 9 (phi > 0)
+    assert np.abs(out[..., moving] - expect[..., moving]).max() < 1e-14
+    assert np.array_equal(out[..., ~moving], phi[..., ~moving])
 
 
 def test_phase_update_follows_translating_interface():

@@ -111,11 +111,9 @@ def test_spherical_rest_state_stays_at_rest():
     assert np.array_equal(O.run(g, W, phi, 5).W, W)
 
 
-def test_mirror_side_equals_the_symmetric_full_domain():
-    """A water/air problem symmetric about the plane x = 1/2 (an air bubble centred on it, a
-    pressure step along y): the half domain x > 1/2 with a mirror side at x = 1/2 reproduces the
-    full domain's right half, FIVER faces on the mirror plane included."""
-    n = 16
+def _mirror_problem(n):
+    """A water/air problem symmetric about the planes x = 1/2 and z = 1/2 (an air bubble centred
+    on both, a pressure step along y)."""
     h = 1.0 / n
     c = (np.arange(n) + 0.5) * h
     z, y, x = np.meshgrid(c, c, c, indexing="ij")
@@ -124,15 +122,83 @@ def test_mirror_side_equals_the_symmetric_full_domain():
     P[0] = np.where(phi < 0, 1.2, 1000.0)
     P[2] = np.where(y < 0.25, 40.0, 0.0)
     P[4] = np.where(y < 0.25, 5e8, 1e5)
+    return h, P, phi
+
+
+@pytest.fixture(scope="module")
+def mirror_full_run():
+    n = 16
+    h, P, phi = _mirror_problem(n)
     full = O.Grid(n=(n, n, n), h=h, eos=(WATER, AIR), bc=(0,) * 6, reinit_every=3, reinit_iters=2)
-    half = O.Grid(n=(n // 2, n, n), h=h, eos=(WATER, AIR), bc=(O.BC_SYMMETRY, 0, 0, 0, 0, 0),
-                  reinit_every=3, reinit_iters=2)
-    rf = O.run(full, O.prims_to_cons(full, P, phi), phi, 8)
-    Ph, phih = P[..., n // 2:].copy(), phi[..., n // 2:].copy()
+    return n, h, P, phi, O.run(full, O.prims_to_cons(full, P, phi), phi, 8)
+
+
+@pytest.mark.parametrize("axis,side", [("x", "lo"), ("x", "hi"), ("z", "lo"), ("z", "hi")])
+def test_mirror_side_equals_the_symmetric_full_domain(mirror_full_run, axis, side):
+    """The half domain on one side of a symmetry plane, with a mirror side on that plane (its
+    lower side for the upper half, its upper side for the lower half, along x or z), reproduces
+    the full domain's half, FIVER faces on the mirror plane included."""
+    n, h, P, phi, rf = mirror_full_run
+    m = n // 2
+    half_sel = slice(m, None) if side == "lo" else slice(None, m)
+    if axis == "x":
+        sel = (Ellipsis, half_sel)
+        shape = (m, n, n)
+        bc = [0] * 6
+        bc[0 if side == "lo" else 1] = O.BC_SYMMETRY
+    else:
+        sel = (Ellipsis, half_sel, slice(None), slice(None))
+        shape = (n, n, m)
+        bc = [0] * 6
+        bc[4 if side == "lo" else 5] = O.BC_SYMMETRY
+    half = O.Grid(n=shape, h=h, eos=(WATER, AIR), bc=tuple(bc), reinit_every=3, reinit_iters=2)
+    Ph, phih = P[sel].copy(), phi[sel].copy()
     rh = O.run(half, O.prims_to_cons(half, Ph, phih), phih, 8)
     assert rf.stats["interface_faces"] > 0
     assert rh.t == pytest.approx(rf.t, rel=1e-13)
     for v in range(5):
-        a, b = rh.W[v], rf.W[v][..., n // 2:]
+        a, b = rh.W[v], rf.W[v][sel]
         assert np.abs(a - b).max() <= 1e-12 * np.abs(rf.W[v]).max(), v
-    assert np.array_equal(rh.phi < 0, rf.phi[..., n // 2:] < 0)
+    assert np.array_equal(rh.phi < 0, rf.phi[sel] < 0)
+
+
+def _steady_radial_flow(r, alpha, gamma=1.4):
+    """Isentropic steady radial flow of a perfect gas through (rho, u, p) = (1, 50, 1e5) at
+    r = 1 (subsonic branch): rho u r^alpha = m, p = K rho^gamma and the Bernoulli sum
+    gamma/(gamma - 1) p/rho + u^2/2 = H, each density by scipy's brentq. It is a steady solution
+    of the spherical (alpha = 2) or cylindrical (alpha = 1) Euler equations of Sec. 3.4."""
+    from scipy.optimize import brentq
+    m, K = 50.0, 1e5
+    H = gamma / (gamma - 1.0) * 1e5 + 0.5 * 50.0 ** 2
+    out = []
+    for ri in r:
+        def bern(rho):
+            return gamma / (gamma - 1.0) * K * rho ** (gamma - 1.0) + 0.5 * (m / (rho * ri ** alpha)) ** 2 - H
+        rho_sonic = (m ** 2 / (gamma * K * ri ** (2 * alpha))) ** (1.0 / (gamma + 1.0))
+        rho = brentq(bern, rho_sonic * (1.0 + 1e-9), 10.0, xtol=1e-15, rtol=1e-15)
+        out.append((rho, m / (rho * ri ** alpha), K * rho ** gamma))
+    return np.array(out).T
+
+
+@pytest.mark.parametrize("geom,alpha", [(O.GEOM_SPHERICAL, 2), (O.GEOM_CYLINDRICAL, 1)])
+def test_steady_radial_flow_residual_vanishes_at_second_order(geom, alpha):
+    """The stage residual of the exact steady radial flow on r in [1, 1.5] falls at second order
+    under refinement (away from the ends): the flux differences and the geometric source
+    -(alpha/r) u_r (rho, rho u, rho v, rho w, rho E + p) of Sec. 3.4, taken at the cell centre
+    r = x0 + (i + 1/2) h (Reading R37), balance to O(h^2). A source taken half a cell off the
+    centre, planted in the oracle, leaves an O(h) residual and fails it."""
+    errs = []
+    for nr in (32, 64, 128):
+        h = 0.5 / nr
+        g = O.Grid(n=(nr, 1, 1), h=h, eos=(AIR, AIR), geom=geom, x0=1.0, reinit_every=10 ** 9)
+        r = 1.0 + (np.arange(nr) + 0.5) * h
+        rho, u, p = _steady_radial_flow(r, alpha)
+        P = np.zeros((5, 1, 1, nr))
+        P[0, 0, 0], P[1, 0, 0], P[4, 0, 0] = rho, u, p
+        phi = np.ones((1, 1, nr))
+        R, _, _ = O.residual(g, O.prims_to_cons(g, P, phi), phi)
+        inner = slice(3, nr - 3)
+        errs.append([np.abs(R[v, 0, 0, inner]).max() for v in (0, 1, 4)])
+    errs = np.array(errs)
+    orders = np.log2(errs[:-1] / errs[1:])   # rows: refinements; columns: mass, momentum, energy
+    assert orders.min() > 1.7 and orders[-1].min() > 1.85, orders
