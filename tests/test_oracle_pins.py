@@ -51,6 +51,17 @@ def test_energy_inverts_pressure(eos, rho, p):
     assert O.pressure(eos, rho, e) == pytest.approx(p, rel=1e-13, abs=1e-6)
 
 
+def test_a_state_without_sound_speed_is_not_admissible():
+    """c^2 > 0 is required of every state (the wave speeds u -+ c of App. C.4 and the 1/(rho c)
+    of the wave curves, Sec. 4.2): a stiffened gas at p = -p_c has c = 0 and is rejected, as is
+    one below it; one just above it is admitted."""
+    g, pc = WATER.prm
+    for p in (-pc, -pc * (1.0 + 1e-12)):
+        with pytest.raises(O.OracleError):
+            O.sound_speed2(WATER, 1000.0, p)
+    assert O.sound_speed2(WATER, 1000.0, -pc * (1.0 - 1e-9)) > 0.0
+
+
 def test_perfect_gas_and_stiffened_gas_closed_forms():
     # NASG with b = e_c = 0 (Sec. 3.3): p = (gamma - 1) rho e - gamma p_c
     assert O.pressure(AIR, 1.3, 2.0e5) == pytest.approx(0.4 * 1.3 * 2.0e5, rel=1e-15)
@@ -297,6 +308,10 @@ def _sg_curve(g, pc, rho, p, ps):
     ((1000.0, -50.0, 1e6), (1.2, 200.0, 1e5), WATER, AIR),
     ((1.0, 0.0, 1e5), (0.125, 0.0, 1e4), AIR, AIR),
     ((1000.0, 5.0, 2e8), (1000.0, -5.0, 1e8), WATER, WATER),
+    # two strong water rarefactions whose Newton iteration does not converge within its 50
+    # steps: p* comes from the bracketing bisection of Reading R6 (stopped at a bracket of
+    # 1e-14 of its ends)
+    ((956.875186, -1351.01462, 6.87618598e7), (1211.34497, -1272.28087, 5.27972620e7), WATER, WATER),
 ])
 def test_riemann_star_pressure_to_the_newton_tolerance(wL, wR, eosL, eosR):
     """Reading R6 stops the Newton iteration at the first step with |dp| <= 1e-12 |p| and keeps
@@ -312,8 +327,9 @@ def test_riemann_star_pressure_to_the_newton_tolerance(wL, wR, eosL, eosR):
         return _sg_curve(gL, pcL, wL[0], wL[2], ps) + _sg_curve(gR, pcR, wR[0], wR[2], ps) + (wR[1] - wL[1])
     lo = max(-pcL, -pcR) + 1e-9 * max(wL[2], wR[2])
     root = brentq(F, lo, 1e12, xtol=1e-300, rtol=1e-15)
-    (ps, us, rl, rr), _ = O.riemann(eosL, wL, eosR, wR)
+    (ps, us, rl, rr), iters = O.riemann(eosL, wL, eosR, wR)
     assert ps == pytest.approx(root, rel=1e-14)
+    assert (iters > 50) == (wL[1] < -1000.0)   # only the last case reaches the bisection
 
 
 @pytest.mark.parametrize("w,p", [((1000.0, 0.0, 1e5), 1e8), ((1000.0, 0.0, 1e5), 2e9), ((1100.0, 50.0, 3e8), 5e9),
@@ -493,6 +509,20 @@ def test_mg_shock_curve_slope_is_the_derivative_of_the_curve(w, p):
     fp, _, _ = O.wave_curve(MGW, w, p + dp)
     fm, _, _ = O.wave_curve(MGW, w, p - dp)
     assert df == pytest.approx((fp - fm) / (2 * dp), rel=1e-6)
+
+
+@pytest.mark.parametrize("w", [(1000.0, 0.0, 1e5), (1243.0, 30.0, 1e9)])
+def test_mg_wave_curve_slope_at_the_side_pressure(w):
+    """At p = p_K the two branches of the MG wave curve meet with the acoustic slope 1/(rho c),
+    which the curve returns there: a central difference across p_K (shock above, rarefaction
+    below) gives the same slope."""
+    f, df, rho = O.wave_curve(MGW, w, w[2])
+    assert f == 0.0 and rho == w[0]
+    dp = 1e-6 * w[2]
+    fp, _, _ = O.wave_curve(MGW, w, w[2] + dp)
+    fm, _, _ = O.wave_curve(MGW, w, w[2] - dp)
+    assert df == pytest.approx((fp - fm) / (2 * dp), rel=1e-6)
+    assert df == pytest.approx(1.0 / (w[0] * math.sqrt(O.sound_speed2(MGW, w[0], w[2]))), rel=1e-14)
 
 
 # --------------------------------------------------------------------------- flow solver

@@ -58,6 +58,35 @@ def test_time_integrators_reach_their_order(rk, lo, hi):
         assert all(lo < o < hi for o in orders), orders
 
 
+def test_forward_euler_converges_to_the_exact_translation():
+    """Forward Euler (Sec. 4.3) with a CFL time step on the smooth translating wave: the density
+    and the level set approach their exactly translated profiles at first order in h (the time
+    error, dt ~ h, dominates), which a self-convergence test in dt alone cannot show (a wrong
+    coefficient of the level-set update, planted in the oracle, converges there too)."""
+    air = O.EOS(O.EOS_SG, (1.4, 0.0))
+    u, T = 1.0, 0.25
+    err_rho, err_phi = [], []
+    for nx in (32, 64, 128):
+        h = 1.0 / nx
+        g = O.Grid(n=(nx, 1, 1), h=h, eos=(air, air), bc=(1, 1, 0, 0, 0, 0), reinit_every=10 ** 9, rk=1, cfl=0.2)
+        x = (np.arange(nx) + 0.5) * h
+        P = np.zeros((5, 1, 1, nx))
+        P[0, 0, 0] = 1.0 + 0.2 * np.sin(2 * np.pi * x)
+        P[1] = u
+        P[4] = 1.0
+        phi = (0.5 + 0.3 * np.sin(2 * np.pi * x))[None, None, :]
+        W = O.prims_to_cons(g, P, phi)
+        n = int(np.ceil(T / O.time_step(g, W, phi)))
+        r = O.run(g, W, phi, n)
+        Pn = O.cons_to_prims(g, r.W, r.phi)
+        xs = x - u * r.t
+        err_rho.append(np.abs(Pn[0, 0, 0] - (1.0 + 0.2 * np.sin(2 * np.pi * xs))).mean())
+        err_phi.append(np.abs(r.phi[0, 0] - (0.5 + 0.3 * np.sin(2 * np.pi * xs))).mean())
+    for errs in (err_rho, err_phi):
+        orders = _orders(errs)
+        assert min(orders) > 0.8, (orders, errs)
+
+
 def test_constant_time_step_rejects_negative_values():
     g, _, P, phi = _smooth_wave(16, dt_fixed=-1.0)
     with pytest.raises(O.OracleError):
