@@ -57,6 +57,21 @@ def test_nasg_without_covolume_is_the_stiffened_gas(wL, wR):
         assert np.allclose(a, b, rtol=1e-13, atol=1e-12)
 
 
+@pytest.mark.parametrize("u", [50.0, 100.0, 300.0])
+def test_nasg_without_covolume_is_the_stiffened_gas_in_tension(u):
+    """Two liquid states separating at +-u: with b = 0 the star pressure falls below zero (into
+    tension, above the lowest admissible pressure -p_c of both EOS) and is the stiffened gas's,
+    whatever e_c; a lower bound of 0 for NASG, planted in the oracle, fails it."""
+    sg = O.EOS(O.EOS_SG, (1.5, 5.0e8))
+    wl, wr = (1000.0, -u, 1e5), (1000.0, u, 1e5)
+    b, _ = O.riemann(sg, wl, sg, wr)
+    assert -5.0e8 < b[0] < 0.0
+    for ec in (0.0, -1.0e6):
+        nasg = O.EOS(O.EOS_NASG, (1.5, 5.0e8, 0.0, ec))
+        a, _ = O.riemann(nasg, wl, nasg, wr)
+        assert np.allclose(a, b, rtol=1e-13, atol=1e-12)
+
+
 def _rh(eos, ahead, behind):
     r0, u0, p0 = ahead
     r1, u1, p1 = behind

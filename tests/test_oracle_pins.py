@@ -62,6 +62,24 @@ def test_a_state_without_sound_speed_is_not_admissible():
     assert O.sound_speed2(WATER, 1000.0, -pc * (1.0 - 1e-9)) > 0.0
 
 
+def test_primitive_conversion_rejects_a_state_without_sound_speed():
+    """The conserved -> primitive conversion of a cell (the first step of each stage) rejects a
+    stiffened-gas state whose internal energy puts its pressure below -p_c (no real sound
+    speed), reporting the cell, rather than passing it on."""
+    g = O.Grid(n=(4, 1, 1), h=0.25, eos=(WATER, AIR), bc=(0,) * 6)
+    P = np.zeros((5, 1, 1, 4))
+    P[0], P[4] = 1000.0, 1e5
+    phi = np.ones((1, 1, 4))
+    W = O.prims_to_cons(g, P, phi)
+    gam, pc = WATER.prm
+    e_bad = (-1.5 * pc + gam * pc) / ((gam - 1.0) * 1000.0)   # p = -1.5 p_c
+    W[4, 0, 0, 2] = 1000.0 * e_bad
+    with pytest.raises(O.OracleError):
+        O.cons_to_prims(g, W, phi)
+    code, cell = O.run_status(g, W, phi, 1)
+    assert code == 5 and cell == 2    # ENONPHYS at that cell
+
+
 def test_perfect_gas_and_stiffened_gas_closed_forms():
     # NASG with b = e_c = 0 (Sec. 3.3): p = (gamma - 1) rho e - gamma p_c
     assert O.pressure(AIR, 1.3, 2.0e5) == pytest.approx(0.4 * 1.3 * 2.0e5, rel=1e-15)
@@ -797,6 +815,33 @@ def test_reinit_keeps_a_plane_distance_and_every_sign():
     away[[0, 1, 9, grad.shape[2] - 2, grad.shape[2] - 1]] = False   # boundary faces and the frozen pair
     assert np.abs(grad[:, :, away] - 1.0).max() < 1e-6
     assert np.array_equal(out3 < 0, phi3 < 0)
+
+
+def test_two_reinit_iterations_in_closed_form():
+    """Two iterations of Eq. reinit on phi0 = 2 (x - 0.43) evaluated by hand: the first moves
+    each cell by (h/2) s_i with s_i = S(phi0_i) = phi0_i/sqrt(phi0_i^2 + h^2); the second takes
+    the upwind one-sided slope of that iterate (the left one where phi0 >= 0, the right one
+    where phi0 < 0; both positive here) as |grad phi|, and the same s_i: the smoothed sign
+    stays that of phi0, not of the iterate."""
+    n, h = (20, 4, 4), 1.0 / 20
+    g = O.Grid(n=n, h=h, eos=(O.EOS(*WL.WATER_SG), O.EOS(*WL.AIR_PG)), bc=(0,) * 6)
+    x, _, _ = WL.cell_centres(n, h)
+    phi0 = 2.0 * (x[0, 0] - 0.43)
+    s = phi0 / np.sqrt(phi0 * phi0 + h * h)
+    frozen = np.zeros(20, bool)
+    frozen[[8, 9]] = True
+    phi1 = np.where(frozen, phi0, phi0 - 0.5 * h * s)
+    left = np.empty(20)
+    left[1:] = (phi1[1:] - phi1[:-1]) / h
+    right = np.empty(20)
+    right[:-1] = (phi1[1:] - phi1[:-1]) / h
+    G = np.where(phi0 >= 0.0, left, right)
+    cells = np.arange(1, 19)
+    cells = cells[~frozen[cells]]
+    expect = phi1[cells] - 0.5 * h * s[cells] * (G[cells] - 1.0)
+    out = O.reinit(g, 2.0 * (x - 0.43), 2)
+    assert np.abs(out[..., cells] - expect).max() < 1e-14
+    assert np.array_equal(out[..., frozen], (2.0 * (x - 0.43))[..., frozen])
 
 
 def test_reinit_keeps_a_distance_with_ridges():
