@@ -20,6 +20,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "m2c_oracle.c")
 LIB = os.path.join(HERE, "libm2c_oracle.so")
+# a prebuilt copy of the oracle to load instead (the mutation test builds copies with a planted
+# mistake and runs pins against them); unset: the library built from SRC above
+MUTANT_LIB = os.environ.get("M2C_ORACLE_MUTANT_LIB", "")
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC"]
 
 EOS_SG = 0
 EOS_MG = 1
@@ -38,9 +42,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 4: "ENOCONV", 5: "ENONPHYS", 6: "EV
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, OpenMP over cells)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
-               "-o", LIB, SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        subprocess.run(["gcc", *CFLAGS, "-o", LIB, SRC, "-lm"], check=True)
     return LIB
 
 
@@ -50,8 +52,11 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        build()
-        _lib = ctypes.CDLL(LIB)
+        if MUTANT_LIB:
+            _lib = ctypes.CDLL(MUTANT_LIB)
+        else:
+            build()
+            _lib = ctypes.CDLL(LIB)
         d = ctypes.c_double
         p = ctypes.c_void_p
         i = ctypes.c_int
