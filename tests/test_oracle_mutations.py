@@ -79,6 +79,20 @@ MUTANTS = [
     ("nasg_lower_bound", "if (q->type == EOS_SG || q->type == EOS_NASG) return -q->prm[1];",
      "if (q->type == EOS_SG) return -q->prm[1];\n  if (q->type == EOS_NASG) return 0.0;",
      "tests/test_oracle_nasg.py::test_nasg_without_covolume_is_the_stiffened_gas_in_tension"),
+    ("jwl_first_exponential_sign", "double x = R * rho0 / rho, ex = exp(-x)",
+     "double x = R * rho0 / rho, ex = i == 0 ? exp(x) : exp(-x)",
+     "tests/test_oracle_jwl.py::test_jwl_is_an_ideal_gas_at_low_density"),
+    ("radial_source_energy_without_p", "acc[4] = acc[4] - a * (W[4 * N + c] + P[4 * N + c]);",
+     "acc[4] = acc[4] - a * (W[4 * N + c]);",
+     "tests/test_oracle_symmetry.py::test_steady_radial_flow_residual_vanishes_at_second_order"),
+    ("phase_update_mirror_image_velocity", "                  prim_at(g, P, i + di, j + dj, k + dk, q);",
+     "                  { long nb2 = cell_index(g, i + di, j + dj, k + dk);\n"
+     "                    for (int v = 0; v < 5; ++v) q[v] = P[v * N + nb2]; }",
+     "tests/test_oracle_symmetry.py::test_phase_update_across_a_mirror_side"),
+    ("band_cutoff_coefficient", "(2.0 * a + gamma - 3.0 * beta)", "(2.0 * a + gamma - 2.0 * beta)",
+     "tests/test_oracle_narrow_band.py::test_cutoff_closed_form"),
+    ("band_clip_skipped", "  band_clip(g, phi); /* narrow band (Reading R38) */", "",
+     "tests/test_oracle_narrow_band.py::test_values_beyond_the_outer_tube_are_clipped_and_held"),
 ]
 
 

@@ -202,3 +202,30 @@ def test_steady_radial_flow_residual_vanishes_at_second_order(geom, alpha):
     errs = np.array(errs)
     orders = np.log2(errs[:-1] / errs[1:])   # rows: refinements; columns: mass, momentum, energy
     assert orders.min() > 1.7 and orders[-1].min() > 1.85, orders
+
+
+@pytest.mark.parametrize("mirror", [True, False])
+def test_phase_update_across_a_mirror_side(mirror):
+    """A cell on the x- side that becomes water with no water face neighbour takes the mean of
+    its 26-neighbourhood's water cells (Reading R17). Its only water neighbour, an edge neighbour
+    in the plane of the side, appears twice: itself, and its image across the side. With a
+    mirror side the image's normal velocity is negated, so the mean has u = 0, as the symmetry
+    demands; with a transmissive side the image is an unchanged copy and u stays."""
+    n = (4, 4, 4)
+    bc = (O.BC_SYMMETRY if mirror else 0, 0, 0, 0, 0, 0)
+    g = O.Grid(n=n, h=0.25, eos=(WATER, AIR), bc=bc)
+    P = np.zeros((5, 4, 4, 4))
+    P[0], P[4] = 1.2, 1e5                     # air everywhere ...
+    phi = -np.ones((4, 4, 4))
+    P[:, 2, 2, 0] = (1000.0, 30.0, 5.0, -7.0, 2e5)  # ... but one water cell at (i, j, k) = (0, 2, 2)
+    phi[2, 2, 0] = 1.0
+    W = O.prims_to_cons(g, P, phi)
+    id_old = (phi < 0).astype(np.uint8)
+    phi_new = phi.copy()
+    phi_new[1, 1, 0] = 0.5                    # cell (0, 1, 1) becomes water
+    W2, phi2, nflip = O.phase_fix(g, W, phi_new, id_old)
+    assert nflip == 1
+    q = O.cons_to_prims(g, W2, phi2)[:, 1, 1, 0]
+    assert q[0] == pytest.approx(1000.0, rel=1e-14) and q[4] == pytest.approx(2e5, rel=1e-12)
+    assert q[2] == pytest.approx(5.0, rel=1e-12) and q[3] == pytest.approx(-7.0, rel=1e-12)
+    assert abs(q[1] - (0.0 if mirror else 30.0)) <= 1e-12 * 30.0
